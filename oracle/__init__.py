@@ -1,0 +1,15 @@
+"""Plain, slow FP64 CPU oracle of GMRES-SDR (Burke, Guettel, Soodhalter).
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call or
+execute anything in this package: only the tests, ``__graft_entry__.smoke()``
+and the CPU-baseline / reference leg of ``bench.py`` use it.  It shares no code
+with the CUDA path (the two sides only share the seeded input generators in
+``workloads``); each function cites the part of the paper it follows.
+
+Modules:
+  sketch   -- the hash-defined sparse-sign embedding S (Section 3, eq. (sketch))
+  sdr      -- one cycle of Algorithm 1, the restart driver and the sequence
+              driver of Section 3.5 (exact and inexact recycling)
+  adjoint  -- gradients of L = ||x(theta) - x_t||^2 through A(theta) x = b
+"""
+from . import sketch, sdr  # noqa: F401
