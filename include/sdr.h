@@ -1,0 +1,186 @@
+/*
+ * sdr.h -- C ABI of the GB300 GMRES-SDR solver.
+ *
+ * GMRES-SDR (GMRES with sketching and deflated restarting; Burke, Guettel,
+ * Soodhalter) solves A x = b and sequences of slowly changing systems
+ * A^(i) x^(i) = b^(i) (Introduction, eq. (sequence_of_linear_systems)).  Each
+ * restart cycle is Algorithm 1: a truncated Arnoldi process, a sparse
+ * subspace embedding S applied to the new basis vectors, a sketched least
+ * squares problem solved through an updated QR factorisation, residual
+ * control with a safety factor (Section 3.3), and a sketched harmonic-Ritz
+ * update of the recycle space U (Section 3.4).  Section 3.5 defines how U, SU
+ * and SAU are carried from one system to the next.
+ *
+ * Conventions for every entry point:
+ *  - Device pointers are CUDA device addresses on the handle's device; host
+ *    pointers are ordinary process memory.  Each argument below says which.
+ *  - The caller owns A, b and x.  The handle owns all workspace (the Krylov
+ *    basis V, SV, SAV, U, SU, SAU, the QR factors and the small dense
+ *    buffers); it is allocated once in sdr_create for n <= n_max.
+ *  - All work is issued on the stream given to sdr_create.  sdr_solve and
+ *    sdr_recycle return after that stream has finished the call's work.
+ *  - Nothing throws across the ABI.  Every call returns an sdr_status; after
+ *    any status other than SDR_ERR_CUDA the handle stays usable.
+ *  - Matrices are square CSR with int32 row pointers and column indices,
+ *    0-based; a row's columns need not be sorted.  Values are float64.
+ *  - Vectors are contiguous float64 arrays of length n.
+ *  - Multi-column arrays are column-major with leading dimension n (tall
+ *    N x k arrays) or s (sketches, s x k).
+ */
+#ifndef SDR_H
+#define SDR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SDR_ABI_VERSION 1
+
+typedef struct sdr_handle sdr_handle; /* opaque */
+
+typedef enum {
+  SDR_OK = 0,
+  SDR_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range */
+  SDR_ERR_CUDA = 2,          /* a CUDA call failed; the handle must be destroyed */
+  SDR_ERR_OOM = 3,           /* device allocation failed in sdr_create */
+  SDR_ERR_NOT_CONVERGED = 4, /* max_cycles reached; x holds the last iterate */
+  SDR_ERR_BREAKDOWN = 5,     /* H(j+1,j) = 0 or a non-finite value with res >= tol */
+  SDR_ERR_RANK = 6,          /* the sketched least-squares matrix lost full rank */
+  SDR_ERR_NOT_IMPLEMENTED = 7
+} sdr_status;
+
+/* Solver parameters (Algorithm 1 inputs m, t, k, S and safety; the stopping
+ * rule of Section 3.3).
+ *   m          Krylov columns per cycle (V has m+1 columns), 1 <= m <= 128.
+ *   k          recycle dimension; up to k+1 columns are kept when the k-th and
+ *              (k+1)-th harmonic Ritz values form a conjugate pair. 0 <= k <= 31.
+ *   t          truncation window of the Arnoldi process, 1 <= t <= 4.
+ *   s, zeta    sketch rows and nonzeros per sketch column; needs
+ *              m + k + 2 <= s <= 512 and 1 <= zeta <= min(s, 32).
+ *   seed       seed of the hash that defines S (fixed for the handle's life,
+ *              so that SU and SAU remain valid from one system to the next).
+ *   rel_tol    stop when ||b - A x|| < rel_tol * ||b||.
+ *   safety0    initial safety factor (>= 1; the paper's default is 1.4).
+ *   max_cycles restart cycles per sdr_solve call (>= 1).
+ *   persist_safety 0: safety restarts from safety0 every cycle;
+ *                  1: it carries over within one sdr_solve call.
+ */
+typedef struct {
+  int32_t m, k, t, s, zeta;
+  uint64_t seed;
+  double rel_tol;
+  double safety0;
+  int32_t max_cycles;
+  int32_t persist_safety;
+  int32_t reserved[6]; /* must be zero */
+} sdr_params;
+
+/* Square CSR matrix; all pointers are device pointers owned by the caller. */
+typedef struct {
+  int64_t n, nnz;
+  const int32_t* rowptr; /* n + 1 entries */
+  const int32_t* col;    /* nnz entries */
+  const double* val;     /* nnz entries */
+} sdr_csr;
+
+/* Statistics of the last sdr_solve (host struct filled by the library). */
+typedef struct {
+  int32_t cycles;          /* restart cycles run */
+  int32_t converged;       /* 1 if ||b - A x|| < tol at return */
+  int32_t matvecs;         /* products with A, including true-residual checks */
+  int32_t sketches;        /* applications of S to a length-n vector */
+  int32_t true_res_evals;  /* true-residual checks (Algorithm 1, residual control) */
+  int32_t arnoldi_steps;   /* truncated Arnoldi steps over all cycles */
+  int32_t recycle_dim;     /* columns of U after the solve */
+  int32_t full_svd_cycles; /* cycles that needed the truncated-SVD path */
+  double final_res;        /* last true residual norm */
+  double tol;              /* rel_tol * ||b|| */
+  double final_rel_res;    /* final_res / ||b|| */
+  double bnorm;
+} sdr_stats;
+
+/* Per-cycle log entry (host struct). */
+typedef struct {
+  int32_t steps;       /* Krylov columns built in the cycle (j_f) */
+  int32_t checks;      /* true-residual evaluations in the cycle */
+  int32_t converged;
+  int32_t ell;         /* numerical rank of SAW at the cycle's end */
+  int32_t kprime;      /* recycle columns produced */
+  int32_t kh;          /* recycle columns used by the cycle */
+  int32_t flags;       /* bit 0: truncated-SVD path taken; bit 1: breakdown */
+  int32_t pad;
+  double res;          /* true residual at the cycle's last check */
+  double sres;         /* sketched residual at the cycle's last step */
+  double safety;       /* safety factor after the cycle */
+} sdr_cycle_log;
+
+/* Create a handle.  p: host pointer to parameters.  n_max: largest n any
+ * later call uses.  stream: a cudaStream_t (NULL = legacy default stream).
+ * out: host pointer receiving the handle.  Allocates all device workspace
+ * on the current device and builds the sketch's per-tile index tables.
+ * Errors: INVALID_ARG (parameter out of range), OOM, CUDA. */
+sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_handle** out);
+
+/* Solve A x = b by restarted GMRES-SDR (Algorithm 1 repeated on the current
+ * residual), starting from the iterate in x and from the handle's current
+ * recycle space U, SU, SAU (empty for a fresh handle).
+ *   A: host pointer to a CSR descriptor of device arrays, A->n <= n_max.
+ *   b: device pointer, n entries.   x: device pointer, n entries, in: x0,
+ *   out: solution.   stats: host pointer or NULL.
+ * On return U, SU, SAU describe the recycle space for the next system.
+ * Returns OK, NOT_CONVERGED (x holds the last iterate), BREAKDOWN, RANK,
+ * INVALID_ARG or CUDA. */
+sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x, sdr_stats* stats);
+
+/* Prepare the recycle space for the next system in a sequence (Section 3.5).
+ *   mode 0 (exact): keep U and SU, recompute SAU = S A_next U with k products
+ *          with A_next and k sketches (A_next: host pointer to a CSR
+ *          descriptor of device arrays).
+ *   mode 1 (inexact): keep SAU as it is (A_next unused, may be NULL).
+ *   mode 2: drop the recycle space.
+ * A system sequence with a fixed matrix needs no call at all. */
+sdr_status sdr_recycle(sdr_handle* h, const sdr_csr* A_next, int32_t mode);
+
+/* Release all device memory of the handle.  h may be NULL. */
+sdr_status sdr_destroy(sdr_handle* h);
+
+/* ---- inspection and state transfer ---------------------------------- */
+
+/* y = S x: apply the handle's sketch to a length-n vector.
+ *   x: device pointer (n entries).  y: device pointer (s entries). */
+sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y);
+
+/* Sketched residual norms of every Arnoldi step of the last sdr_solve, in
+ * order, and the per-cycle log.  sres: host pointer with room for cap_steps
+ * doubles (may be NULL).  log: host pointer with room for cap_cycles entries
+ * (may be NULL).  n_steps / n_cycles: host pointers receiving the counts. */
+sdr_status sdr_get_history(sdr_handle* h, double* sres, int32_t cap_steps, int32_t* n_steps,
+                           sdr_cycle_log* log, int32_t cap_cycles, int32_t* n_cycles);
+
+/* Current number of recycle columns (0 for a fresh handle). */
+sdr_status sdr_recycle_dim(sdr_handle* h, int32_t* kdim);
+
+/* Copy the recycle state out: U (device, n x kdim, ld n), SU and SAU
+ * (device, s x kdim each, ld s).  Any pointer may be NULL to skip it. */
+sdr_status sdr_recycle_export(sdr_handle* h, int64_t n, double* U, double* SU, double* SAU);
+
+/* Replace the recycle state: U (device, n x kdim, ld n); SU and SAU (device,
+ * s x kdim) or NULL, in which case the missing sketches are computed from U
+ * with A (host pointer to a CSR descriptor; needed only when SAU is NULL).
+ * kdim <= k + 1. */
+sdr_status sdr_recycle_import(sdr_handle* h, const sdr_csr* A, int64_t n, int32_t kdim,
+                              const double* U, const double* SU, const double* SAU);
+
+/* Human-readable text of a status (static storage). */
+const char* sdr_status_string(sdr_status st);
+
+/* SDR_ABI_VERSION of the library. */
+int32_t sdr_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDR_H */

@@ -1,0 +1,23 @@
+"""GB300-native GMRES-SDR: C-ABI library libsdr.so plus a thin ctypes binding.
+
+GMRES with randomized sketching and deflated restarting (Burke, Guettel,
+Soodhalter): truncated Arnoldi, a hash-defined sparse-sign embedding, a
+sketched least-squares solve and sketched harmonic-Ritz recycling, each step
+a hand-written sm_103a kernel.
+"""
+from .sdr import (  # noqa: F401
+    CSRDevice,
+    Solver,
+    SdrError,
+    load_library,
+    make_params,
+    sdr_create,
+    sdr_destroy,
+    sdr_get_history,
+    sdr_recycle,
+    sdr_recycle_dim,
+    sdr_recycle_export,
+    sdr_recycle_import,
+    sdr_sketch,
+    sdr_solve,
+)

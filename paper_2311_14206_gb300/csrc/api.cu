@@ -1,0 +1,406 @@
+// C ABI of the GMRES-SDR solver (include/sdr.h): handle, workspace and the
+// host-side driver that issues one restart cycle after another.
+//
+// Control decisions inside a cycle (when to evaluate the true residual, when
+// the cycle stops) are taken on the device from the control block; the host
+// launches the m steps of a cycle back to back and synchronises once per
+// cycle to read the outcome (converged, recycle dimension).
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <cstddef>
+#include <vector>
+
+#include "../../include/sdr.h"
+#include "launch.cuh"
+
+namespace sdr {
+size_t ce_scratch_doubles();
+}
+
+using namespace sdr;
+
+struct sdr_handle {
+  sdr_params p;
+  int64_t n_max;
+  cudaStream_t st;
+  int device;
+  WS ws;
+  std::vector<void*> allocs;
+  uint16_t* sk_ent = nullptr;
+  uint16_t* sk_ptr = nullptr;
+  int cu = 0;  // current recycle buffer
+  int kh = 0;  // current recycle dimension
+  std::vector<double> hist;
+  std::vector<CycleLog> log;
+  double* d_tmp = nullptr;  // n_max scratch vector (A u)
+};
+
+namespace {
+
+sdr_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return SDR_OK;
+  if (e == cudaErrorMemoryAllocation) return SDR_ERR_OOM;
+  return SDR_ERR_CUDA;
+}
+
+#define SDR_CK(x)                                   \
+  do {                                              \
+    cudaError_t e_ = (x);                           \
+    if (e_ != cudaSuccess) return cuda_status(e_);  \
+  } while (0)
+
+template <typename T>
+cudaError_t halloc(sdr_handle* h, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back(q);
+  *p = (T*)q;
+  return cudaSuccess;
+}
+
+int ceil_log2(int64_t v) {
+  int b = 0;
+  while (((int64_t)1 << b) < v) ++b;
+  return b;
+}
+
+bool csr_ok(const sdr_handle* h, const sdr_csr* A) {
+  return A && A->n > 0 && A->n <= h->n_max && A->nnz >= 0 && A->rowptr && A->col && A->val &&
+         A->nnz < ((int64_t)1 << 31);
+}
+
+CsrDev to_dev(const sdr_csr* A) { return CsrDev{A->n, A->nnz, A->rowptr, A->col, A->val}; }
+
+int* ctl_int_field(Ctl* c, size_t off) { return (int*)((char*)c + off); }
+
+}  // namespace
+
+extern "C" {
+
+int32_t sdr_abi_version(void) { return SDR_ABI_VERSION; }
+
+const char* sdr_status_string(sdr_status st) {
+  switch (st) {
+    case SDR_OK: return "ok";
+    case SDR_ERR_INVALID_ARG: return "invalid argument";
+    case SDR_ERR_CUDA: return "CUDA error";
+    case SDR_ERR_OOM: return "out of device memory";
+    case SDR_ERR_NOT_CONVERGED: return "not converged within max_cycles";
+    case SDR_ERR_BREAKDOWN: return "Arnoldi breakdown without convergence";
+    case SDR_ERR_RANK: return "sketched least-squares matrix lost rank";
+    case SDR_ERR_NOT_IMPLEMENTED: return "not implemented";
+  }
+  return "unknown status";
+}
+
+sdr_status sdr_destroy(sdr_handle* h) {
+  if (!h) return SDR_OK;
+  for (void* q : h->allocs) cudaFree(q);
+  delete h;
+  return SDR_OK;
+}
+
+sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_handle** out) {
+  if (!p || !out || n_max <= 0) return SDR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (p->m < 1 || p->m > M_MAX || p->k < 0 || p->k > K_MAX - 1 || p->t < 1 || p->t > T_MAX) return SDR_ERR_INVALID_ARG;
+  if (p->s > S_MAX || p->s < p->m + p->k + 2 || p->zeta < 1 || p->zeta > p->s || p->zeta > ZETA_MAX)
+    return SDR_ERR_INVALID_ARG;
+  if (!(p->rel_tol > 0.0) || !(p->safety0 >= 1.0) || p->max_cycles < 1) return SDR_ERR_INVALID_ARG;
+  if (n_max >= ((int64_t)1 << 31)) return SDR_ERR_INVALID_ARG;
+  sdr_handle* h = new sdr_handle();
+  h->p = *p;
+  h->n_max = n_max;
+  h->st = (cudaStream_t)stream;
+  cudaGetDevice(&h->device);
+  WS& ws = h->ws;
+  ws.n = n_max;
+  ws.ldv = n_max;
+  ws.m = p->m;
+  ws.k = p->k;
+  ws.t = p->t;
+  ws.s = p->s;
+  ws.zeta = p->zeta;
+  ws.kmax = p->k + 1;
+  ws.dmax = D_MAX;
+  ws.seed = p->seed;
+  ws.inv_sqrt_zeta = 1.0 / std::sqrt((double)p->zeta);
+  ws.win_bits = ceil_log2(n_max) + 1;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  ws.grid_max = (nsm > 0 ? nsm : 148) * 4;
+  const int64_t N = n_max;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  chk(halloc(h, &ws.Vs, (size_t)N * p->m));
+  chk(halloc(h, &ws.R[0], (size_t)N));
+  chk(halloc(h, &ws.R[1], (size_t)N));
+  chk(halloc(h, &ws.Wv, (size_t)N));
+  chk(halloc(h, &ws.Xw, (size_t)N));
+  chk(halloc(h, &ws.U[0], (size_t)N * ws.kmax));
+  chk(halloc(h, &ws.U[1], (size_t)N * ws.kmax));
+  chk(halloc(h, &h->d_tmp, (size_t)N));
+  const int tileR = sketch_tile_rows(p->zeta);
+  const int64_t ntiles = (N + tileR - 1) / tileR;
+  ws.ntiles = (int)ntiles;
+  chk(halloc(h, &h->sk_ent, (size_t)ntiles * tileR * p->zeta));
+  chk(halloc(h, &h->sk_ptr, (size_t)ntiles * (S_MAX + 1)));
+  ws.sk_ent = h->sk_ent;
+  ws.sk_ptr = h->sk_ptr;
+  chk(halloc(h, &ws.part, (size_t)ws.grid_max * 2 * NPART));
+  chk(halloc(h, &ws.acc, (size_t)6 * S_MAX + 16));
+  const int s = p->s;
+  chk(halloc(h, &ws.SV, (size_t)s * (M_MAX + 1)));
+  chk(halloc(h, &ws.SAV, (size_t)s * M_MAX));
+  for (int i = 0; i < 2; ++i) {
+    chk(halloc(h, &ws.SU[i], (size_t)s * K_MAX));
+    chk(halloc(h, &ws.SAU[i], (size_t)s * K_MAX));
+  }
+  chk(halloc(h, &ws.Y, (size_t)s * D_MAX));
+  chk(halloc(h, &ws.T, (size_t)D_MAX * D_MAX));
+  chk(halloc(h, &ws.Rf, (size_t)D_MAX * D_MAX));
+  chk(halloc(h, &ws.tau, (size_t)D_MAX));
+  chk(halloc(h, &ws.z, (size_t)S_MAX));
+  chk(halloc(h, &ws.Sr0, (size_t)S_MAX));
+  chk(halloc(h, &ws.ytil, (size_t)D_MAX));
+  chk(halloc(h, &ws.P, (size_t)D_MAX * K_MAX));
+  chk(halloc(h, &ws.dscr, ce_scratch_doubles()));
+  chk(halloc(h, &ws.hist, (size_t)HIST_MAX));
+  chk(halloc(h, &ws.log, (size_t)LOG_MAX));
+  chk(halloc(h, &ws.ctl, (size_t)1));
+  if (e != cudaSuccess) {
+    sdr_status st = cuda_status(e);
+    sdr_destroy(h);
+    return st;
+  }
+  chk(cudaMemsetAsync(ws.acc, 0, (6 * S_MAX + 16) * sizeof(unsigned long long), h->st));
+  chk(cudaMemsetAsync(ws.ctl, 0, sizeof(Ctl), h->st));
+  chk(cudaMemsetAsync(ws.T, 0, (size_t)D_MAX * D_MAX * sizeof(double), h->st));
+  chk(cudaMemsetAsync(ws.Rf, 0, (size_t)D_MAX * D_MAX * sizeof(double), h->st));
+  chk(cudaMemsetAsync(ws.P, 0, (size_t)D_MAX * K_MAX * sizeof(double), h->st));
+  {
+    Ctl init;
+    std::memset(&init, 0, sizeof(init));
+    init.safety0 = p->safety0;
+    init.safety = p->safety0;
+    init.persist_safety = p->persist_safety;
+    init.force_svd = p->reserved[0] == 1 ? 1 : 0;
+    chk(cudaMemcpyAsync(ws.ctl, &init, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
+  }
+  chk(launch_sketch_build(ws, N, h->sk_ent, h->sk_ptr, h->st));
+  chk(cudaStreamSynchronize(h->st));
+  if (e != cudaSuccess) {
+    sdr_status st = cuda_status(e);
+    sdr_destroy(h);
+    return st;
+  }
+  *out = h;
+  return SDR_OK;
+}
+
+sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x, sdr_stats* stats) {
+  if (!h || !csr_ok(h, A) || !b || !x) return SDR_ERR_INVALID_ARG;
+  WS ws = h->ws;
+  ws.n = A->n;
+  const CsrDev Ad = to_dev(A);
+  cudaStream_t st = h->st;
+  const int m = ws.m;
+  unsigned long long* accR = ws.acc + 2 * S_MAX;
+  SDR_CK(launch_solve_init_x(ws, Ad, b, x, h->p.rel_tol, st));
+  double* xcur = x;
+  double* xoth = ws.Xw;
+  int rb = 0;
+  SDR_CK(launch_residual(ws, Ad, b, xcur, ws.R[rb], accR, -1, 0, st));
+  Ctl hc;
+  SDR_CK(cudaMemcpyAsync(&hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  SDR_CK(cudaStreamSynchronize(st));
+  std::vector<const double*> vcol(m + 1);
+  int cycles = 0;
+  sdr_status status = SDR_OK;
+  int full_svd = 0;
+  bool converged = hc.converged != 0;
+  while (!converged && cycles < h->p.max_cycles) {
+    vcol[0] = ws.R[rb];
+    for (int c = 1; c <= m; ++c) vcol[c] = ws.Vs + (int64_t)(c - 1) * ws.ldv;
+    const int cu = h->cu, kh = h->kh;
+    SDR_CK(launch_cycle_init(ws, ws.SAU[cu], kh, accR, h->p.persist_safety, st));
+    for (int j = 0; j < m; ++j) {
+      SDR_CK(launch_spmv_dots(ws, Ad, vcol.data(), j, st));
+      SDR_CK(launch_update_sketch(ws, vcol.data(), (double*)vcol[j + 1], j, st));
+      SDR_CK(launch_step_dense(ws, j, kh, accR, st));
+      SDR_CK(launch_check_gemv(ws, ws.U[cu], vcol.data(), xcur, xoth, kh, j, st));
+      SDR_CK(launch_residual(ws, Ad, b, xoth, ws.R[1 - rb], accR, j, 1, st));
+    }
+    SDR_CK(launch_cycle_end(ws, kh, ws.SU[cu], ws.SAU[cu], ws.SU[1 - cu], ws.SAU[1 - cu], st));
+    SDR_CK(launch_recycle_gemm(ws, ws.U[cu], vcol.data(), ws.U[1 - cu], kh, st));
+    SDR_CK(cudaMemcpyAsync(&hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    SDR_CK(cudaStreamSynchronize(st));
+    ++cycles;
+    if (hc.jf > 0) {
+      h->cu = 1 - cu;
+      h->kh = hc.kprime;
+      double* t = xcur;
+      xcur = xoth;
+      xoth = t;
+      rb = 1 - rb;
+      if (hc.svd_path) ++full_svd;
+    }
+    converged = hc.converged != 0;
+    if (!converged && hc.breakdown) {
+      status = SDR_ERR_BREAKDOWN;
+      break;
+    }
+    if (!converged && !std::isfinite(hc.res)) {
+      status = SDR_ERR_BREAKDOWN;
+      break;
+    }
+  }
+  if (xcur != x) SDR_CK(cudaMemcpyAsync(x, xcur, (size_t)A->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const int nh = hc.hist_n < HIST_MAX ? hc.hist_n : HIST_MAX;
+  const int nl = hc.log_n < LOG_MAX ? hc.log_n : LOG_MAX;
+  h->hist.assign(nh, 0.0);
+  h->log.assign(nl, CycleLog());
+  if (nh) SDR_CK(cudaMemcpyAsync(h->hist.data(), ws.hist, nh * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (nl) SDR_CK(cudaMemcpyAsync(h->log.data(), ws.log, nl * sizeof(CycleLog), cudaMemcpyDeviceToHost, st));
+  SDR_CK(cudaStreamSynchronize(st));
+  if (status == SDR_OK && !converged) status = SDR_ERR_NOT_CONVERGED;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->cycles = cycles;
+    stats->converged = converged ? 1 : 0;
+    stats->matvecs = hc.matvecs;
+    stats->sketches = hc.sketches;
+    int checks = 0;
+    for (auto& g : h->log) checks += g.checks;
+    stats->true_res_evals = checks;
+    stats->arnoldi_steps = hc.hist_n;
+    stats->recycle_dim = h->kh;
+    stats->full_svd_cycles = full_svd;
+    stats->final_res = hc.res;
+    stats->tol = hc.tol;
+    stats->bnorm = hc.bnorm;
+    stats->final_rel_res = hc.bnorm > 0.0 ? hc.res / hc.bnorm : hc.res;
+  }
+  return status;
+}
+
+// Recompute SAU = S A U column by column (exact variant, Section 3.5).
+static sdr_status recompute_sau(sdr_handle* h, const sdr_csr* A, int64_t n) {
+  WS ws = h->ws;
+  ws.n = n;
+  const CsrDev Ad = to_dev(A);
+  unsigned long long* accG = ws.acc + 4 * S_MAX;
+  int* topG = ctl_int_field(ws.ctl, offsetof(Ctl, accG_top));
+  for (int c = 0; c < h->kh; ++c) {
+    const double* u = ws.U[h->cu] + (int64_t)c * ws.ldv;
+    SDR_CK(launch_spmv(Ad, u, h->d_tmp, h->st));
+    SDR_CK(launch_maxabs_top(ws, h->d_tmp, n, topG, h->st));
+    SDR_CK(launch_sketch_vec(ws, h->d_tmp, n, accG, topG, h->st));
+    SDR_CK(launch_sketch_finish(ws, accG, topG, ws.SAU[h->cu] + (int64_t)c * ws.s, h->st));
+  }
+  SDR_CK(cudaStreamSynchronize(h->st));
+  return SDR_OK;
+}
+
+static sdr_status recompute_su(sdr_handle* h, int64_t n) {
+  WS ws = h->ws;
+  ws.n = n;
+  unsigned long long* accG = ws.acc + 4 * S_MAX;
+  int* topG = ctl_int_field(ws.ctl, offsetof(Ctl, accG_top));
+  for (int c = 0; c < h->kh; ++c) {
+    const double* u = ws.U[h->cu] + (int64_t)c * ws.ldv;
+    SDR_CK(launch_maxabs_top(ws, u, n, topG, h->st));
+    SDR_CK(launch_sketch_vec(ws, u, n, accG, topG, h->st));
+    SDR_CK(launch_sketch_finish(ws, accG, topG, ws.SU[h->cu] + (int64_t)c * ws.s, h->st));
+  }
+  SDR_CK(cudaStreamSynchronize(h->st));
+  return SDR_OK;
+}
+
+sdr_status sdr_recycle(sdr_handle* h, const sdr_csr* A_next, int32_t mode) {
+  if (!h) return SDR_ERR_INVALID_ARG;
+  if (mode == 2) {
+    h->kh = 0;
+    return SDR_OK;
+  }
+  if (mode == 1) return SDR_OK;
+  if (mode != 0) return SDR_ERR_INVALID_ARG;
+  if (h->kh == 0) return SDR_OK;
+  if (!csr_ok(h, A_next)) return SDR_ERR_INVALID_ARG;
+  return recompute_sau(h, A_next, A_next->n);
+}
+
+sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y) {
+  if (!h || !x || !y || n <= 0 || n > h->n_max) return SDR_ERR_INVALID_ARG;
+  WS ws = h->ws;
+  ws.n = n;
+  unsigned long long* accG = ws.acc + 4 * S_MAX;
+  int* topG = ctl_int_field(ws.ctl, offsetof(Ctl, accG_top));
+  SDR_CK(launch_maxabs_top(ws, x, n, topG, h->st));
+  SDR_CK(launch_sketch_vec(ws, x, n, accG, topG, h->st));
+  SDR_CK(launch_sketch_finish(ws, accG, topG, y, h->st));
+  SDR_CK(cudaStreamSynchronize(h->st));
+  return SDR_OK;
+}
+
+sdr_status sdr_get_history(sdr_handle* h, double* sres, int32_t cap_steps, int32_t* n_steps, sdr_cycle_log* log,
+                           int32_t cap_cycles, int32_t* n_cycles) {
+  if (!h) return SDR_ERR_INVALID_ARG;
+  static_assert(sizeof(sdr_cycle_log) == sizeof(CycleLog), "cycle log layout");
+  const int nh = (int)h->hist.size(), nl = (int)h->log.size();
+  if (n_steps) *n_steps = nh;
+  if (n_cycles) *n_cycles = nl;
+  if (sres && cap_steps > 0) std::memcpy(sres, h->hist.data(), sizeof(double) * (nh < cap_steps ? nh : cap_steps));
+  if (log && cap_cycles > 0) std::memcpy(log, h->log.data(), sizeof(CycleLog) * (nl < cap_cycles ? nl : cap_cycles));
+  return SDR_OK;
+}
+
+sdr_status sdr_recycle_dim(sdr_handle* h, int32_t* kdim) {
+  if (!h || !kdim) return SDR_ERR_INVALID_ARG;
+  *kdim = h->kh;
+  return SDR_OK;
+}
+
+sdr_status sdr_recycle_export(sdr_handle* h, int64_t n, double* U, double* SU, double* SAU) {
+  if (!h || n <= 0 || n > h->n_max) return SDR_ERR_INVALID_ARG;
+  const WS& ws = h->ws;
+  const int kh = h->kh;
+  if (kh == 0) return SDR_OK;
+  if (U)
+    SDR_CK(cudaMemcpy2DAsync(U, n * sizeof(double), ws.U[h->cu], ws.ldv * sizeof(double), n * sizeof(double), kh,
+                             cudaMemcpyDeviceToDevice, h->st));
+  if (SU)
+    SDR_CK(cudaMemcpyAsync(SU, ws.SU[h->cu], (size_t)ws.s * kh * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  if (SAU)
+    SDR_CK(cudaMemcpyAsync(SAU, ws.SAU[h->cu], (size_t)ws.s * kh * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  SDR_CK(cudaStreamSynchronize(h->st));
+  return SDR_OK;
+}
+
+sdr_status sdr_recycle_import(sdr_handle* h, const sdr_csr* A, int64_t n, int32_t kdim, const double* U,
+                              const double* SU, const double* SAU) {
+  if (!h || n <= 0 || n > h->n_max || kdim < 0 || kdim > h->ws.kmax) return SDR_ERR_INVALID_ARG;
+  if (kdim > 0 && !U) return SDR_ERR_INVALID_ARG;
+  if (kdim > 0 && !SAU && !csr_ok(h, A)) return SDR_ERR_INVALID_ARG;
+  const WS& ws = h->ws;
+  h->kh = kdim;
+  if (kdim == 0) return SDR_OK;
+  SDR_CK(cudaMemcpy2DAsync(ws.U[h->cu], ws.ldv * sizeof(double), U, n * sizeof(double), n * sizeof(double), kdim,
+                           cudaMemcpyDeviceToDevice, h->st));
+  if (SU)
+    SDR_CK(cudaMemcpyAsync(ws.SU[h->cu], SU, (size_t)ws.s * kdim * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  if (SAU)
+    SDR_CK(cudaMemcpyAsync(ws.SAU[h->cu], SAU, (size_t)ws.s * kdim * sizeof(double), cudaMemcpyDeviceToDevice,
+                           h->st));
+  SDR_CK(cudaStreamSynchronize(h->st));
+  if (!SU) {
+    sdr_status s = recompute_su(h, n);
+    if (s != SDR_OK) return s;
+  }
+  if (!SAU) return recompute_sau(h, A, n);
+  return SDR_OK;
+}
+
+}  // extern "C"

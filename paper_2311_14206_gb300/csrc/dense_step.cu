@@ -1,0 +1,288 @@
+// Small dense part of each GMRES-SDR step (Algorithm 1, sketched least squares
+// and residual control), FP64, one CTA.
+//
+// The economic QR of SAW = [SAU, SAV(:, 1:j)] is updated one column at a time
+// with Householder reflectors held in compact WY form Q = I - Y T Y^T
+// (Schreiber & Van Loan): the new column c becomes Q^T c = c - Y (T^T (Y^T c))
+// through two matrix-vector products, so the work spreads over all threads
+// instead of one reflector at a time.  z = Q^T S r0 is kept up to date as
+// reflectors are added; the sketched residual ||S r0 - SAW y|| equals the norm
+// of z below the current column.
+#include "launch.cuh"
+
+namespace sdr {
+
+constexpr int DT = 512;  // threads of the dense-step CTA
+
+struct QrSmem {
+  double c[S_MAX];
+  double z[S_MAX];
+  double u[D_MAX];
+  double u2[D_MAX];
+  double red[32];
+};
+
+// y_l = sum_{i >= rowstart(l)} Y(i, l) x_i for l < ncols, warp per column.
+__device__ inline void gemv_yt(const double* __restrict__ Y, int ldy, int s, int ncols, int minrow,
+                               const double* __restrict__ x, double* __restrict__ y) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = wid; l < ncols; l += nw) {
+    const int r0 = l > minrow ? l : minrow;
+    const double* col = Y + (int64_t)l * ldy;
+    double acc = 0.0;
+    for (int i = r0 + lane; i < s; i += 32) acc = fma(col[i], x[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) y[l] = acc;
+  }
+}
+
+// Add column c (in sm.c, length s) as column p of SAW's QR.  Updates Y, T, Rf,
+// tau (global) and sm.z.  Returns the sketched residual ||z(p+1:s)||.
+__device__ double qr_add_column(const WS& ws, int p, QrSmem& sm, int* rank_flag) {
+  const int s = ws.s, ld = ws.dmax;
+  double* __restrict__ Y = ws.Y;
+  double* __restrict__ T = ws.T;
+  // u = Y(:, 0:p)^T c
+  gemv_yt(Y, s, s, p, 0, sm.c, sm.u);
+  __syncthreads();
+  // u2 = T(0:p, 0:p)^T u
+  for (int l = threadIdx.x; l < p; l += blockDim.x) {
+    const double* tc = T + (int64_t)l * ld;
+    double a = 0.0;
+    for (int m = 0; m <= l; ++m) a = fma(tc[m], sm.u[m], a);
+    sm.u2[l] = a;
+  }
+  __syncthreads();
+  // c = c - Y u2   (Y(i, l) = 0 for i < l)
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    double a = sm.c[i];
+    const int lmax = i < p - 1 ? i : p - 1;
+    for (int l = 0; l <= lmax; ++l) a = fma(-Y[i + (int64_t)l * s], sm.u2[l], a);
+    sm.c[i] = a;
+  }
+  __syncthreads();
+  // Householder reflector for c(p:s): H c(p:s) = beta e_1, H = I - tau v v^T, v_0 = 1
+  double xs = 0.0;
+  for (int i = p + 1 + threadIdx.x; i < s; i += blockDim.x) xs = fma(sm.c[i], sm.c[i], xs);
+  xs = block_sum(xs, sm.red);
+  const double alpha = sm.c[p];
+  double beta, tau, scale;
+  if (xs == 0.0) {
+    beta = alpha;
+    tau = 0.0;
+    scale = 0.0;
+  } else {
+    beta = -copysign(sqrt(alpha * alpha + xs), alpha);
+    tau = (beta - alpha) / beta;
+    scale = 1.0 / (alpha - beta);
+  }
+  if (beta == 0.0 && threadIdx.x == 0) *rank_flag = 1;
+  // R(0:p, p) = c(0:p), R(p, p) = beta; Y(:, p) = v
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    if (i < p) ws.Rf[i + (int64_t)p * ld] = sm.c[i];
+    if (i == p) ws.Rf[i + (int64_t)p * ld] = beta;
+    const double v = i < p ? 0.0 : (i == p ? 1.0 : sm.c[i] * scale);
+    Y[i + (int64_t)p * s] = v;
+    sm.c[i] = v;  // c now holds v
+  }
+  if (threadIdx.x == 0) ws.tau[p] = tau;
+  __syncthreads();
+  // T(0:p, p) = -tau T(0:p, 0:p) (Y(:, 0:p)^T v),  T(p, p) = tau
+  gemv_yt(Y, s, s, p, p, sm.c, sm.u);
+  __syncthreads();
+  for (int l = threadIdx.x; l <= p; l += blockDim.x) {
+    double a = 0.0;
+    if (l < p) {
+      for (int m = l; m < p; ++m) a = fma(T[l + (int64_t)m * ld], sm.u[m], a);
+      a = -tau * a;
+    } else {
+      a = tau;
+    }
+    T[l + (int64_t)p * ld] = a;
+  }
+  // z(p:s) -= tau v (v^T z(p:s))
+  double dz = 0.0;
+  for (int i = p + threadIdx.x; i < s; i += blockDim.x) dz = fma(sm.c[i], sm.z[i], dz);
+  dz = block_sum(dz, sm.red);
+  for (int i = p + threadIdx.x; i < s; i += blockDim.x) sm.z[i] = fma(-tau * dz, sm.c[i], sm.z[i]);
+  __syncthreads();
+  double rr = 0.0;
+  for (int i = p + 1 + threadIdx.x; i < s; i += blockDim.x) rr = fma(sm.z[i], sm.z[i], rr);
+  rr = block_sum(rr, sm.red);
+  return sqrt(rr);
+}
+
+// ---------------------------------------------------------------------------
+// Cycle start (Algorithm 1, before the Arnoldi loop): S r0 from the residual
+// accumulators, beta = ||r0||, V(:,1) and SV(:,1) scales, z = S r0, and the QR
+// of the kh recycled columns SAU.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DT) k_cycle_init(WS ws, const double* __restrict__ SAU, int kh,
+                                                   unsigned long long* accR, int persist_safety) {
+  __shared__ QrSmem sm;
+  __shared__ int rank_flag;
+  Ctl* c = ws.ctl;
+  const int s = ws.s;
+  const double beta = c->res;
+  const int top = c->accR_top;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    double v = int128_to_double(accR[2 * i], accR[2 * i + 1], top - 126) * ws.inv_sqrt_zeta;
+    accR[2 * i] = 0ull;
+    accR[2 * i + 1] = 0ull;
+    ws.Sr0[i] = v;
+    sm.z[i] = v;
+    ws.SV[i] = beta > 0.0 ? v / beta : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    rank_flag = 0;
+    c->alpha[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+    c->vmax[0] = c->rmax;
+    c->beta = beta;
+    c->kh = kh;
+    c->check = 0;
+    c->jf = 0;
+    c->step = 0;
+    c->nchecks = 0;
+    c->breakdown = 0;
+    c->rankfail = 0;
+    c->kprime = 0;
+    c->ell = 0;
+    c->svd_path = 0;
+    if (!persist_safety) c->safety = c->safety0;
+    c->converged = beta < c->tol ? 1 : 0;
+    c->done = c->converged;
+  }
+  __syncthreads();
+  double sres = 0.0;
+  {
+    double rr = 0.0;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) rr = fma(sm.z[i], sm.z[i], rr);
+    sres = sqrt(block_sum(rr, sm.red));
+  }
+  for (int p = 0; p < kh; ++p) {
+    for (int i = threadIdx.x; i < s; i += blockDim.x) sm.c[i] = SAU[i + (int64_t)p * s];
+    __syncthreads();
+    sres = qr_add_column(ws, p, sm, &rank_flag);
+  }
+  for (int i = threadIdx.x; i < s; i += blockDim.x) ws.z[i] = sm.z[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c->sres = sres;
+    if (rank_flag) c->rankfail = 1;
+  }
+}
+
+cudaError_t launch_cycle_init(const WS& ws, const double* SAU, int kh, unsigned long long* accR,
+                              int persist_safety, cudaStream_t st) {
+  k_cycle_init<<<1, DT, 0, st>>>(ws, SAU, kh, accR, persist_safety);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Arnoldi step j, dense part.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DT) k_step_dense(WS ws, int j, int kh, int grid2, unsigned long long* accR) {
+  Ctl* c = ws.ctl;
+  if (c->done) return;
+  __shared__ QrSmem sm;
+  __shared__ double hcol[T_MAX + 1];
+  __shared__ double sh_alpha;
+  __shared__ int rank_flag;
+  __shared__ unsigned long long redu[32];
+  const int s = ws.s, t = ws.t;
+  const int p = kh + j;
+  const int lo = j - t + 1 > 0 ? j - t + 1 : 0;
+  // 1. reduce the update kernel's partials
+  double nrm = 0.0;
+  for (int b = threadIdx.x; b < grid2; b += blockDim.x) nrm += ws.part[b * NPART + 0];
+  nrm = block_sum(nrm, sm.red);
+  double cross[T_MAX];
+  for (int d = 0; d < T_MAX; ++d) {
+    double v = 0.0;
+    if (d < t - 1) {
+      for (int b = threadIdx.x; b < grid2; b += blockDim.x) v += ws.part[b * NPART + 1 + d];
+      v = block_sum(v, sm.red);
+    }
+    cross[d] = v;
+  }
+  unsigned long long vm = 0ull;
+  for (int b = threadIdx.x; b < grid2; b += blockDim.x) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(ws.part[b * NPART + T_MAX]);
+    vm = u > vm ? u : vm;
+  }
+  vm = block_max_u64(vm, redu);
+  const double h = sqrt(nrm);
+  const bool breakdown = !(h > 0.0) || !isfinite(h);
+  if (threadIdx.x == 0) {
+    rank_flag = 0;
+    const double a = breakdown ? 0.0 : 1.0 / h;
+    sh_alpha = a;
+    c->alpha[j + 1] = a;
+    c->vmax[j + 1] = vm;
+    for (int d = 0; d < t - 1; ++d) c->gram[j + 1][d] = cross[d];
+    c->hband[j][t] = breakdown ? 0.0 : h;
+    if (breakdown) c->breakdown = 1;
+    for (int o = 0; o <= T_MAX; ++o) hcol[o] = o < t ? c->hband[j][o] : 0.0;
+    hcol[t] = breakdown ? 0.0 : h;
+  }
+  __syncthreads();
+  // 2. S v_hat_{j+1} from the accumulators; SV(:, j+1); 3. SAV(:, j)
+  const int top = c->acc_top;
+  const double a1 = sh_alpha;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    double raw = int128_to_double(ws.acc[2 * i], ws.acc[2 * i + 1], top - 126) * ws.inv_sqrt_zeta;
+    ws.acc[2 * i] = 0ull;
+    ws.acc[2 * i + 1] = 0ull;
+    if (breakdown) raw = 0.0;
+    ws.SV[i + (int64_t)(j + 1) * s] = raw * a1;
+    // SAV(:, j) = SV(:, 1:j+1) H(1:j+1, j) over the band; H(j+1,j) SV(:,j+1) = raw
+    double v = raw;
+    for (int ii = lo; ii <= j; ++ii) v = fma(hcol[ii - j + t - 1], ws.SV[i + (int64_t)ii * s], v);
+    ws.SAV[i + (int64_t)j * s] = v;
+    sm.c[i] = v;
+    sm.z[i] = ws.z[i];
+  }
+  __syncthreads();
+  // 4. QR update
+  const double sres = qr_add_column(ws, p, sm, &rank_flag);
+  for (int i = threadIdx.x; i < s; i += blockDim.x) ws.z[i] = sm.z[i];
+  // 5. residual control (Algorithm 1): check the true residual when
+  //    sres < tol / safety, at the last step, or after a breakdown.
+  __shared__ int do_check;
+  if (threadIdx.x == 0) {
+    if (c->hist_n < HIST_MAX) ws.hist[c->hist_n] = sres;
+    c->hist_n += 1;
+    c->sres = sres;
+    c->step = j + 1;
+    c->sketches += 1;
+    if (rank_flag) c->rankfail = 1;
+    do_check = (sres < c->tol / c->safety) || (j == ws.m - 1) || breakdown;
+    c->check = do_check;
+    if (do_check) c->xmax = 0ull;
+  }
+  __syncthreads();
+  if (!do_check) return;
+  for (int i = threadIdx.x; i < 2 * s; i += blockDim.x) accR[i] = 0ull;
+  // y_tilde = R(0:p+1, 0:p+1)^{-1} z(0:p+1) by column-oriented back substitution
+  __shared__ double yv;
+  for (int i = p; i >= 0; --i) {
+    if (threadIdx.x == 0) {
+      const double rii = ws.Rf[i + (int64_t)i * ws.dmax];
+      double y = (rii != 0.0 && isfinite(rii)) ? sm.z[i] / rii : 0.0;
+      if (!(rii != 0.0)) c->rankfail = 1;
+      ws.ytil[i] = y;
+      yv = y;
+    }
+    __syncthreads();
+    const double y = yv;
+    for (int l = threadIdx.x; l < i; l += blockDim.x) sm.z[l] = fma(-ws.Rf[l + (int64_t)i * ws.dmax], y, sm.z[l]);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_step_dense(const WS& ws, int j, int kh, unsigned long long* accR, cudaStream_t st) {
+  k_step_dense<<<1, DT, 0, st>>>(ws, j, kh, update_grid(ws), accR);
+  return cudaGetLastError();
+}
+
+}  // namespace sdr

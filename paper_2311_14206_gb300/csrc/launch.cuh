@@ -1,0 +1,62 @@
+// Host-side launchers of the GMRES-SDR kernels (one translation unit each).
+#pragma once
+#include "sdr_common.cuh"
+
+namespace sdr {
+
+struct CsrDev {
+  int64_t n, nnz;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+};
+
+// ---- sketch.cu ----
+cudaError_t launch_sketch_build(const WS& ws, int64_t n, uint16_t* ent, uint16_t* ptr, cudaStream_t st);
+// acc (+=) S_raw x for a vector whose entries are bounded by ctl->... ; the
+// window top is read from *top_dev (device int) so producers can set it.
+cudaError_t launch_sketch_vec(const WS& ws, const double* x, int64_t n, unsigned long long* acc,
+                              const int* top_dev, cudaStream_t st);
+// y = scale * acc * 2^(top-126) / sqrt(zeta) for s rows; zeroes acc.
+cudaError_t launch_sketch_finish(const WS& ws, unsigned long long* acc, const int* top_dev, double* y,
+                                 cudaStream_t st);
+// *top_dev = window for max|x| (reduction over x).
+cudaError_t launch_maxabs_top(const WS& ws, const double* x, int64_t n, int* top_dev, cudaStream_t st);
+
+// ---- arnoldi.cu ----
+// Solve start: ||b||, max|b|, ||A||_inf, tol into ctl.
+cudaError_t launch_solve_init_x(const WS& ws, CsrDev A, const double* b, const double* x, double rel_tol,
+                                cudaStream_t st);
+// r = b - A x into rout; ||r||, max|r| into ctl (res, rmax); S r into accR (window from
+// ctl bmax + anorm_inf * xmax_bits).  mode 0: unconditional (solve start, x = x0);
+// mode 1: only when ctl->check, and the last CTA applies the residual control.
+cudaError_t launch_residual(const WS& ws, CsrDev A, const double* b, const double* x, double* rout,
+                            unsigned long long* accR, int j, int mode, cudaStream_t st);
+// Arnoldi step j: w = A v_j with window dots; coefficients into ctl.
+cudaError_t launch_spmv_dots(const WS& ws, CsrDev A, const double* const* vcol, int j, cudaStream_t st);
+// v_hat_{j+1} = a0 w - sum a_i v_i, with norms, cross dots and the sketch into ws.acc.
+cudaError_t launch_update_sketch(const WS& ws, const double* const* vcol, double* vnext, int j,
+                                 cudaStream_t st);
+// x_trial = x_cur + [U V(:,0:j+1)] (scaled ytil) when ctl->check.
+cudaError_t launch_check_gemv(const WS& ws, const double* U, const double* const* vcol, const double* xcur,
+                              double* xtrial, int kh, int j, cudaStream_t st);
+// U_new = [U V(:,0:jf)] P' (kprime columns from ctl).
+cudaError_t launch_recycle_gemm(const WS& ws, const double* U, const double* const* vcol, double* Unew,
+                                int kh, cudaStream_t st);
+// y = A x (plain SpMV, used for A U in the exact recycling variant).
+cudaError_t launch_spmv(CsrDev A, const double* x, double* y, cudaStream_t st);
+int update_grid(const WS& ws);
+
+// ---- dense_step.cu ----
+// Cycle start: Sr0, beta, SV(:,0), QR of SAU (kh columns).
+cudaError_t launch_cycle_init(const WS& ws, const double* SAU, int kh, unsigned long long* accR,
+                              int persist_safety, cudaStream_t st);
+// Arnoldi step j, small dense part: h(j+1,j), SV(:,j+1), SAV(:,j), QR update, sres, control.
+cudaError_t launch_step_dense(const WS& ws, int j, int kh, unsigned long long* accR, cudaStream_t st);
+
+// ---- dense_cycle.cu ----
+// Cycle end: harmonic-Ritz recycling (Section 3.4); P' into ws.P, SU/SAU for the next cycle.
+cudaError_t launch_cycle_end(const WS& ws, int kh, const double* SU, const double* SAU, double* SUn,
+                             double* SAUn, cudaStream_t st);
+
+}  // namespace sdr

@@ -1,0 +1,314 @@
+// Internal definitions shared by the GMRES-SDR kernels and the host driver.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sdr {
+
+constexpr int M_MAX = 128;   // Krylov columns per cycle
+constexpr int K_MAX = 32;    // recycle columns (k + 1)
+constexpr int D_MAX = M_MAX + K_MAX;  // columns of SAW
+constexpr int S_MAX = 512;   // sketch rows
+constexpr int T_MAX = 4;     // Arnoldi truncation window
+constexpr int ZETA_MAX = 32;
+constexpr int TILE_R = 2048; // rows per sketch tile (zeta*TILE_R < 65536 for uint16 offsets)
+constexpr int NPART = 8;     // doubles of per-CTA partial results
+constexpr int HIST_MAX = 1 << 15;  // logged Arnoldi steps per solve
+constexpr int LOG_MAX = 512;       // logged cycles per solve
+
+// Control block in device memory: the state that decides the cycle's control
+// flow (Algorithm 1 residual control) without a host round trip per step.
+struct Ctl {
+  double tol, bnorm, bmax, anorm_inf;
+  double safety, safety0, res, beta, sres;
+  int kh;         // recycle columns used by the current cycle
+  int done;       // current cycle finished (converged or forced end)
+  int converged;  // true residual below tol
+  int check;      // a true-residual check is due at the current step
+  int jf;         // Krylov columns built when the cycle stopped
+  int breakdown;
+  int rankfail;
+  int nchecks;
+  int step;       // steps completed in the current cycle
+  int acc_top;    // window top of the Arnoldi-vector sketch accumulators
+  int accR_top;   // window top of the residual sketch accumulators
+  int accG_top;   // window top of the general-purpose sketch accumulators
+  int force_svd;  // test switch: always take the truncated-SVD path
+  int ell, kprime, svd_path;
+  int hist_n;     // logged steps so far in this solve
+  int log_n;      // logged cycles so far in this solve
+  int matvecs, sketches;
+  int persist_safety;
+  unsigned int counter;   // last-CTA counter for grid reductions
+  unsigned int counter2;
+  double alpha[M_MAX + 2];                // 1 / ||v_hat_c||
+  unsigned long long vmax[M_MAX + 2];     // bits of max |v_hat_c|
+  unsigned long long wmax, xmax, rmax;    // bits of max |w|, |x_trial|, |r|
+  double hband[M_MAX][T_MAX + 1];         // H(i, j), i = j-t+1 .. j+1 at index i-(j-t+1)
+  double gram[M_MAX + 2][T_MAX];          // v_hat_c . v_hat_{c-1-d}, d = 0..t-2
+  double coef[T_MAX + 1];                 // a_0 (w) and a_1.. (window) for the update
+  double hnext_sq;                        // ||v_hat_{j+1}||^2 (reduced in the dense step)
+};
+
+// Per-cycle log entry kept on the device, mirrored by sdr_cycle_log.
+struct CycleLog {
+  int steps, checks, converged, ell, kprime, kh, flags, pad;
+  double res, sres, safety;
+};
+
+// Device workspace: pointers and sizes, passed by value to kernels.
+struct WS {
+  int64_t n;        // current system size
+  int64_t ldv;      // leading dimension of tall arrays (n_max)
+  int m, k, t, s, zeta, kmax, dmax;
+  uint64_t seed;
+  double inv_sqrt_zeta;
+  int win_bits;     // log2 bound on terms per sketch row (window headroom)
+  // tall arrays (n_max rows)
+  double* Vs;       // columns 1..m of V (column c at Vs + (c-1)*ldv); column 0 is the residual
+  double* R[2];     // residual buffers
+  double* Wv;       // SpMV output w
+  double* Xw;       // workspace iterate
+  double* U[2];     // recycle bases, kmax columns each
+  // sketch tables
+  const uint16_t* sk_ent;  // per tile: zeta*TILE_R entries (offset | sign<<15)
+  const uint16_t* sk_ptr;  // per tile: s+1 row pointers
+  int ntiles;
+  // reductions
+  double* part;             // [grid_max][NPART]
+  unsigned long long* acc;  // 128-bit accumulators, acc[2*i] = lo, acc[2*i+1] = hi
+  int grid_max;
+  // small dense (column-major)
+  double* SV;    // s x (m+1)
+  double* SAV;   // s x m
+  double* SU[2]; // s x kmax
+  double* SAU[2];
+  double* Y;     // s x dmax Householder vectors
+  double* T;     // dmax x dmax
+  double* Rf;    // dmax x dmax
+  double* tau;   // dmax
+  double* z;     // s: Q^T S r0 as reflectors are added
+  double* Sr0;   // s
+  double* ytil;  // dmax
+  double* P;     // dmax x kmax: recycle coefficients (V rows scaled by alpha)
+  double* dscr;  // dense scratch for the cycle-end kernel
+  double* hist;  // HIST_MAX sres values
+  CycleLog* log; // LOG_MAX entries
+  Ctl* ctl;
+};
+
+// ---------------------------------------------------------------------------
+// Hash-defined sparse-sign embedding (same definition as the oracle, written
+// independently): word(c, q) = SplitMix64 output number c*zeta + q for the
+// seed; rows by Floyd's sampling; sign from bit 0.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ inline uint64_t splitmix_word(uint64_t seed, uint64_t counter) {
+  return mix64(seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull);
+}
+
+// Rows (distinct, in [0, s)) and signs (+1/-1) of sketch column c.
+__host__ __device__ inline void sketch_column(uint64_t seed, int s, int zeta, uint64_t c,
+                                              int* rows, int* signs) {
+  for (int q = 0; q < zeta; ++q) {
+    uint64_t w = splitmix_word(seed, c * (uint64_t)zeta + (uint64_t)q);
+    uint32_t j = (uint32_t)(s - zeta + q);
+    uint32_t hi = (uint32_t)(w >> 32);
+    uint32_t t = (uint32_t)(((uint64_t)hi * (uint64_t)(j + 1)) >> 32);
+    bool taken = false;
+    for (int p = 0; p < q; ++p) taken |= (rows[p] == (int)t);
+    rows[q] = taken ? (int)j : (int)t;
+    signs[q] = (w & 1ull) ? -1 : 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-point helpers for the exact sketch accumulation.
+// ---------------------------------------------------------------------------
+// Bits of |x| (sign cleared); unsigned order of these bits is the order of |x|.
+__device__ inline unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Biased exponent field of a non-negative double given by its bits.
+__host__ __device__ inline int bexp_of_bits(unsigned long long b) { return (int)((b >> 52) & 0x7FF); }
+
+// Quantise x to round(x * 2^(51 - e)) where 2^(e-1) <= maxabs < 2^e has biased
+// exponent field emax (so e = emax - 1022).  |result| <= 2^51.  Integer-only.
+__device__ inline long long quantize_fixed(double x, int emax) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;  // zero or subnormal: below the quantum
+  unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  // x = mant * 2^(ex - 1075); q = x * 2^(51 - (emax - 1022)) = mant * 2^(ex - emax - 2)
+  int sh = emax + 2 - ex;  // >= 2 because ex <= emax
+  if (sh >= 63) return 0;
+  unsigned long long q = (mant + (1ull << (sh - 1))) >> sh;
+  return (b >> 63) ? -(long long)q : (long long)q;
+}
+
+// 128-bit two's-complement add of a sign-extended 64-bit value shifted left by sh.
+__device__ inline void add_shifted128(unsigned long long& lo, unsigned long long& hi, long long v, int sh) {
+  if (v == 0) return;
+  unsigned long long vlo, vhi;
+  if (sh >= 64) {
+    vlo = 0ull;
+    vhi = (unsigned long long)(v << (sh - 64));
+  } else if (sh > 0) {
+    vlo = (unsigned long long)v << sh;
+    vhi = (unsigned long long)(v >> (64 - sh));
+  } else if (sh == 0) {
+    vlo = (unsigned long long)v;
+    vhi = (unsigned long long)(v >> 63);
+  } else {
+    int r = -sh;
+    if (r >= 63) return;
+    long long rv = (v + (1ll << (r - 1))) >> r;  // round to nearest
+    vlo = (unsigned long long)rv;
+    vhi = (unsigned long long)(rv >> 63);
+  }
+  unsigned long long nlo = lo + vlo;
+  hi += vhi + (nlo < lo ? 1ull : 0ull);
+  lo = nlo;
+}
+
+// Atomically add a 128-bit value into acc[0] (lo), acc[1] (hi).  Integer
+// addition is associative, so the final sum does not depend on the order.
+__device__ inline void atomic_add128(unsigned long long* acc, unsigned long long lo, unsigned long long hi) {
+  if (lo == 0ull && hi == 0ull) return;
+  unsigned long long old = atomicAdd(acc, lo);
+  unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  if (hi + carry) atomicAdd(acc + 1, hi + carry);
+}
+
+// Signed 128-bit (hi:lo) times 2^scale_exp, rounded to double.
+__device__ inline double int128_to_double(unsigned long long lo, unsigned long long hi, int scale_exp) {
+  bool neg = (long long)hi < 0;
+  if (neg) {  // negate
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  double d = (double)hi * 18446744073709551616.0 + (double)lo;
+  d = ldexp(d, scale_exp);
+  return neg ? -d : d;
+}
+
+// Window for a sketch of a vector whose entries are bounded by `bound`: the
+// 128-bit accumulator counts in units of 2^(top - 126), top = exponent of
+// bound + log2(number of summed terms) + 2.
+__host__ __device__ inline int window_top(double bound, int win_bits) {
+  int e;
+  frexp(bound > 0.0 ? bound : 1e-300, &e);
+  return e + win_bits + 2;
+}
+
+// ---------------------------------------------------------------------------
+// Sketch tiles.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int sketch_tile_rows(int zeta) {
+  int r = 32768 / (zeta > 0 ? zeta : 1);
+  if (r > TILE_R) r = TILE_R;
+  r = (r / 512) * 512;
+  return r < 512 ? 512 : r;
+}
+inline size_t sketch_smem_bytes(int zeta) {
+  int tileR = sketch_tile_rows(zeta);
+  return (size_t)tileR * 8 + (size_t)tileR * zeta * 2 + (S_MAX + 8) * 2;
+}
+
+// ---------------------------------------------------------------------------
+// Block-level helpers.
+// ---------------------------------------------------------------------------
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ inline unsigned long long warp_max_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+
+// Sum over the block in a fixed order (deterministic).  `red` needs
+// blockDim.x/32 doubles of shared memory.  All threads receive the result.
+__device__ inline double block_sum(double v, double* red) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = lane < nw ? red[lane] : 0.0;
+    r = warp_sum(r);
+    if (lane == 0) red[0] = r;
+  }
+  __syncthreads();
+  r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ inline unsigned long long block_max_u64(unsigned long long v, unsigned long long* red) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_max_u64(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long r = lane < nw ? red[lane] : 0ull;
+    r = warp_max_u64(r);
+    if (lane == 0) red[0] = r;
+  }
+  __syncthreads();
+  unsigned long long r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Add the tile's contribution S_tile x_tile to the 128-bit accumulator of
+// sketch row threadIdx.x (threads >= s do nothing).  vals holds the tile's
+// values (tileR doubles, zero beyond ncols) and is overwritten.  All threads
+// of the block must call it.
+__device__ inline void tile_sketch_accumulate(const WS& ws, int tileR, int tile, int ncols, double* vals,
+                                              uint16_t* ent_s, uint16_t* ptr_s, unsigned long long* red,
+                                              int top, unsigned long long& lo, unsigned long long& hi) {
+  const uint4* src = (const uint4*)(ws.sk_ent + (int64_t)tile * tileR * ws.zeta);
+  uint4* dst = (uint4*)ent_s;
+  const int nvec = (tileR * ws.zeta) / 8;
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = src[i];
+  const uint16_t* psrc = ws.sk_ptr + (int64_t)tile * (S_MAX + 1);
+  for (int i = threadIdx.x; i <= ws.s; i += blockDim.x) ptr_s[i] = psrc[i];
+  unsigned long long mb = 0ull;
+  for (int i = threadIdx.x; i < ncols; i += blockDim.x) {
+    unsigned long long b = abs_bits(vals[i]);
+    mb = b > mb ? b : mb;
+  }
+  mb = block_max_u64(mb, red);  // synchronises the block
+  const int emax = bexp_of_bits(mb);
+  if (emax == 0 || emax == 0x7FF) return;  // all zero, or non-finite (caught through the norms)
+  long long* q = (long long*)vals;
+  for (int i = threadIdx.x; i < ncols; i += blockDim.x) q[i] = quantize_fixed(vals[i], emax);
+  __syncthreads();
+  if (threadIdx.x < ws.s) {
+    long long a = 0;
+    const int e0 = ptr_s[threadIdx.x], e1 = ptr_s[threadIdx.x + 1];
+    for (int e = e0; e < e1; ++e) {
+      const uint16_t c = ent_s[e];
+      const long long v = q[c & 0x7FFF];
+      a += (c & 0x8000) ? -v : v;
+    }
+    // tile value = a * 2^(e_t - 51) with e_t = emax - 1022; window unit 2^(top - 126)
+    add_shifted128(lo, hi, a, (emax - 1022) - 51 - (top - 126));
+  }
+  __syncthreads();
+}
+
+}  // namespace sdr

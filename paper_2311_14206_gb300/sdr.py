@@ -1,0 +1,242 @@
+"""Python binding of libsdr.so (include/sdr.h): argument marshalling only.
+
+The functions carry the C names (sdr_create, sdr_solve, sdr_recycle,
+sdr_destroy, ...).  Device arrays are torch CUDA tensors; their data pointers
+and the current torch stream are handed to the library, which does all the
+work in its own kernels.  There is no fallback: if the library is missing or
+no GPU is present the calls raise.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+SDR_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory", 4: "not converged",
+          5: "breakdown", 6: "rank", 7: "not implemented"}
+
+
+class sdr_params(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("k", ctypes.c_int32), ("t", ctypes.c_int32), ("s", ctypes.c_int32),
+                ("zeta", ctypes.c_int32), ("seed", ctypes.c_uint64), ("rel_tol", ctypes.c_double),
+                ("safety0", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("persist_safety", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class sdr_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class sdr_stats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int32), ("converged", ctypes.c_int32), ("matvecs", ctypes.c_int32),
+                ("sketches", ctypes.c_int32), ("true_res_evals", ctypes.c_int32), ("arnoldi_steps", ctypes.c_int32),
+                ("recycle_dim", ctypes.c_int32), ("full_svd_cycles", ctypes.c_int32), ("final_res", ctypes.c_double),
+                ("tol", ctypes.c_double), ("final_rel_res", ctypes.c_double), ("bnorm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class sdr_cycle_log(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("checks", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("ell", ctypes.c_int32), ("kprime", ctypes.c_int32), ("kh", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("pad", ctypes.c_int32), ("res", ctypes.c_double),
+                ("sres", ctypes.c_double), ("safety", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libsdr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2311_14206_gb300._build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "sdr_create": ([P(sdr_params), i64, vp, P(vp)], i32),
+        "sdr_solve": ([vp, P(sdr_csr), vp, vp, P(sdr_stats)], i32),
+        "sdr_recycle": ([vp, P(sdr_csr), i32], i32),
+        "sdr_destroy": ([vp], i32),
+        "sdr_sketch": ([vp, vp, i64, vp], i32),
+        "sdr_get_history": ([vp, P(ctypes.c_double), i32, P(i32), P(sdr_cycle_log), i32, P(i32)], i32),
+        "sdr_recycle_dim": ([vp, P(i32)], i32),
+        "sdr_recycle_export": ([vp, i64, vp, vp, vp], i32),
+        "sdr_recycle_import": ([vp, P(sdr_csr), i64, i32, vp, vp, vp], i32),
+        "sdr_status_string": ([i32], ctypes.c_char_p),
+        "sdr_abi_version": ([], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+class SdrError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+def _check(st, where, ok=(SDR_OK,)):
+    if st not in ok:
+        raise SdrError(st, where)
+    return st
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass
+class CSRDevice:
+    """Square CSR matrix held in torch CUDA tensors (int32 / int32 / float64)."""
+
+    n: int
+    rowptr: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor
+
+    @classmethod
+    def from_numpy(cls, A, device="cuda"):
+        return cls(A.n, torch.as_tensor(A.rowptr, dtype=torch.int32).to(device),
+                   torch.as_tensor(A.col, dtype=torch.int32).to(device),
+                   torch.as_tensor(A.val, dtype=torch.float64).to(device))
+
+    def c_struct(self) -> sdr_csr:
+        for t, dt in ((self.rowptr, torch.int32), (self.col, torch.int32), (self.val, torch.float64)):
+            if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+                raise TypeError("CSR arrays must be contiguous CUDA tensors (int32, int32, float64)")
+        return sdr_csr(self.n, int(self.val.numel()), self.rowptr.data_ptr(), self.col.data_ptr(),
+                       self.val.data_ptr())
+
+
+def make_params(m, k, t, s, zeta, seed, rel_tol, safety0=1.4, max_cycles=200, persist_safety=0,
+                force_svd=False) -> sdr_params:
+    p = sdr_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety)
+    p.reserved[0] = 1 if force_svd else 0
+    return p
+
+
+def sdr_create(params: sdr_params, n_max: int, stream=None) -> ctypes.c_void_p:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    st = lib.sdr_create(ctypes.byref(params), n_max, stream if stream is not None else _stream(), ctypes.byref(h))
+    _check(st, "sdr_create")
+    return h
+
+
+def sdr_solve(h, A: CSRDevice, b: torch.Tensor, x: torch.Tensor, allow_not_converged=True):
+    """Solve in place into x; returns (status, stats dict)."""
+    lib = load_library()
+    if b.dtype != torch.float64 or x.dtype != torch.float64 or not (b.is_cuda and x.is_cuda):
+        raise TypeError("b and x must be float64 CUDA tensors")
+    csr = A.c_struct()
+    stats = sdr_stats()
+    st = lib.sdr_solve(h, ctypes.byref(csr), _ptr(b), _ptr(x), ctypes.byref(stats))
+    _check(st, "sdr_solve", ok=(0, 4) if allow_not_converged else (0,))
+    return st, stats.as_dict()
+
+
+def sdr_recycle(h, A_next: CSRDevice = None, mode: int = 0):
+    lib = load_library()
+    csr = A_next.c_struct() if A_next is not None else None
+    return _check(lib.sdr_recycle(h, ctypes.byref(csr) if csr is not None else None, mode), "sdr_recycle")
+
+
+def sdr_destroy(h):
+    return load_library().sdr_destroy(h)
+
+
+def sdr_sketch(h, x: torch.Tensor, s: int) -> torch.Tensor:
+    y = torch.empty(s, dtype=torch.float64, device=x.device)
+    _check(load_library().sdr_sketch(h, _ptr(x), x.numel(), _ptr(y)), "sdr_sketch")
+    return y
+
+
+def sdr_get_history(h, cap_steps=1 << 15, cap_cycles=512):
+    lib = load_library()
+    sres = (ctypes.c_double * cap_steps)()
+    logs = (sdr_cycle_log * cap_cycles)()
+    ns, nc = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.sdr_get_history(h, sres, cap_steps, ctypes.byref(ns), logs, cap_cycles, ctypes.byref(nc)),
+           "sdr_get_history")
+    log = [{f: getattr(logs[i], f) for f, _ in sdr_cycle_log._fields_} for i in range(min(nc.value, cap_cycles))]
+    return list(sres[:min(ns.value, cap_steps)]), log
+
+
+def sdr_recycle_dim(h) -> int:
+    k = ctypes.c_int32()
+    _check(load_library().sdr_recycle_dim(h, ctypes.byref(k)), "sdr_recycle_dim")
+    return k.value
+
+
+def sdr_recycle_export(h, n: int, s: int, device="cuda"):
+    kd = sdr_recycle_dim(h)
+    U = torch.empty((kd, n), dtype=torch.float64, device=device)  # row c = column c (column-major n x kd)
+    SU = torch.empty((kd, s), dtype=torch.float64, device=device)
+    SAU = torch.empty((kd, s), dtype=torch.float64, device=device)
+    if kd:
+        _check(load_library().sdr_recycle_export(h, n, _ptr(U), _ptr(SU), _ptr(SAU)), "sdr_recycle_export")
+    return U.T, SU.T, SAU.T
+
+
+def sdr_recycle_import(h, A: CSRDevice, U: torch.Tensor, SU: torch.Tensor = None, SAU: torch.Tensor = None):
+    """U, SU, SAU given as (n x k), (s x k), (s x k) arrays; stored column-major."""
+    n, kd = U.shape
+    Uc = U.T.contiguous()
+    SUc = SU.T.contiguous() if SU is not None else None
+    SAUc = SAU.T.contiguous() if SAU is not None else None
+    csr = A.c_struct() if A is not None else None
+    st = load_library().sdr_recycle_import(h, ctypes.byref(csr) if csr is not None else None, n, kd, _ptr(Uc),
+                                           _ptr(SUc), _ptr(SAUc))
+    return _check(st, "sdr_recycle_import")
+
+
+class Solver:
+    """Convenience wrapper owning one handle (GMRES-SDR for one system size)."""
+
+    def __init__(self, n_max, m, k, t, s, zeta=8, seed=231114206, rel_tol=1e-8, safety0=1.4, max_cycles=200,
+                 persist_safety=0, force_svd=False):
+        self.params = make_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety, force_svd)
+        self.n_max, self.s = n_max, s
+        self.h = sdr_create(self.params, n_max)
+
+    def solve(self, A: CSRDevice, b: torch.Tensor, x: torch.Tensor = None):
+        if x is None:
+            x = torch.zeros_like(b)
+        st, stats = sdr_solve(self.h, A, b, x)
+        return x, st, stats
+
+    def recycle(self, A_next=None, mode=0):
+        return sdr_recycle(self.h, A_next, mode)
+
+    def history(self):
+        return sdr_get_history(self.h)
+
+    def close(self):
+        if self.h is not None:
+            sdr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

@@ -1,0 +1,241 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: sketch indices bit-exact; per-step sketched residuals within 1e-8
+relative (floor 1e-13 ||b|| for rounding cancellation, the sres being formed
+from O(||S b||) terms); final solutions within 1e-6 relative with the true
+residual below tol; recycle spaces compared by principal angles.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sdr as osdr
+from oracle.sketch import SparseSign, sketch_indices
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SEED = 231114206
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2311_14206_gb300 as P
+    return P
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def saw_conditioning(cyc):
+    """kappa(SAW) after each step of an oracle cycle recorded with record=True."""
+    SAU, SAV = cyc.info["SAU_in"], cyc.info["SAV"]
+    return np.array([np.linalg.cond(np.hstack([SAU, SAV[:, :j + 1]])) for j in range(SAV.shape[1])])
+
+
+def sres_close(gpu, ref, bnorm, rel=1e-8, floor=1e-13, kappa=None):
+    """|gpu - ref| <= rel |ref| + (floor + 64 eps kappa_j) ||b||.  The kappa term
+    is the first-order sensitivity of a least-squares residual to rounding in
+    SAW; it is negligible while eps kappa(SAW) << 1e-10 (all t = 2 workloads)."""
+    gpu, ref = np.asarray(gpu), np.asarray(ref)
+    assert gpu.shape == ref.shape, (gpu.shape, ref.shape)
+    err = np.abs(gpu - ref)
+    kap = np.zeros_like(ref) if kappa is None else np.asarray(kappa)[:ref.size]
+    bound = rel * np.abs(ref) + (floor + 64 * np.finfo(float).eps * kap) * bnorm
+    bad = np.nonzero(err > bound)[0]
+    assert bad.size == 0, f"steps {bad[:8]}: gpu {gpu[bad[:4]]} ref {ref[bad[:4]]}"
+    return float(np.max(err / (np.abs(ref) + floor * bnorm)))
+
+
+def principal_angle(X, Y):
+    Qx, _ = np.linalg.qr(X)
+    Qy, _ = np.linalg.qr(Y)
+    sv = np.linalg.svd(Qx.T @ Qy, compute_uv=False)
+    return float(np.arccos(np.clip(sv.min(), -1, 1)))
+
+
+# ---------------------------------------------------------------- sketch
+@pytest.mark.parametrize("n,s,zeta", [(5000, 120, 8), (4096, 480, 8), (3000, 37, 3), (2500, 100, 1)])
+def test_sketch_columns_bit_exact(P, n, s, zeta):
+    solver = P.Solver(n, m=10, k=2, t=2, s=s, zeta=zeta, seed=SEED)
+    rng = np.random.default_rng(0)
+    cols = sorted(set([0, 1, 2047, 2048, 2049, n - 1] + list(rng.integers(0, n, 40))))
+    rows, signs = sketch_indices(SEED, s, zeta, np.array(cols))
+    for i, c in enumerate(cols):
+        e = torch.zeros(n, dtype=torch.float64, device="cuda")
+        e[c] = 1.0
+        y = P.sdr_sketch(solver.h, e, s).cpu().numpy()
+        ref = np.zeros(s)
+        ref[rows[i]] = signs[i] / np.sqrt(float(zeta))
+        assert np.array_equal(y, ref), f"column {c}"
+    solver.close()
+
+
+@pytest.mark.parametrize("n", [5000, 2**21 + 123])
+def test_sketch_random_vector(P, n):
+    s, zeta = 480, 8
+    solver = P.Solver(n, m=10, k=2, t=2, s=s, zeta=zeta, seed=SEED)
+    x = np.random.default_rng(1).standard_normal(n)
+    y = P.sdr_sketch(solver.h, dev(x), s).cpu().numpy()
+    ref = SparseSign(SEED, n, s, zeta).apply(x)
+    assert np.max(np.abs(y - ref)) <= 1e-13 * np.linalg.norm(ref)
+    # bit-for-bit reproducible
+    y2 = P.sdr_sketch(solver.h, dev(x), s).cpu().numpy()
+    assert np.array_equal(y, y2)
+    solver.close()
+
+
+# ---------------------------------------------------------------- solves
+def run_pair(P, A, b, m, k, t, s, zeta, tol, max_cycles=200, **kw):
+    solver = P.Solver(A.n, m, k, t, s, zeta, SEED, tol, max_cycles=max_cycles, **kw)
+    Ad = P.CSRDevice.from_numpy(A)
+    x, st, stats = solver.solve(Ad, dev(b))
+    sres, log = solver.history()
+    ref = osdr.solve(A, b, SparseSign(SEED, A.n, s, zeta), m=m, k=k, t=t, rel_tol=tol, max_cycles=max_cycles,
+                     record=True)
+    return solver, Ad, x.cpu().numpy(), st, stats, sres, log, ref
+
+
+def test_cd2d_64_first_cycle_and_solution(P):
+    A = W.make_cd2d(64, (10.0, 10.0))
+    b = W.rhs(A.n)
+    m, k, t, s, zeta, tol = 50, 10, 2, 120, 8, 1e-8
+    solver, Ad, x, st, stats, sres, log, ref = run_pair(P, A, b, m, k, t, s, zeta, tol)
+    bn = np.linalg.norm(b)
+    sres_close(sres[:len(ref.sres_per_cycle[0])], ref.sres_per_cycle[0], bn)
+    assert st == 0 and stats["converged"] == 1
+    assert abs(stats["cycles"] - ref.cycles) <= 1
+    relres = np.linalg.norm(b - osdr.csr_matvec(A, x)) / bn
+    assert relres <= tol * (1 + 1e-9)
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+    # second cycle (strict in free-running mode)
+    n0 = len(ref.sres_per_cycle[0])
+    sres_close(sres[n0:n0 + len(ref.sres_per_cycle[1])], ref.sres_per_cycle[1], bn)
+    solver.close()
+
+
+def test_cd2d_64_cycle_replay(P):
+    """Each GPU cycle starts from the oracle's state at that cycle's start."""
+    A = W.make_cd2d(64, (10.0, 10.0))
+    b = W.rhs(A.n)
+    m, k, t, s, zeta, tol = 50, 10, 2, 120, 8, 1e-8
+    S = SparseSign(SEED, A.n, s, zeta)
+    states = []
+    ref = osdr.solve(A, b, S, m=m, k=k, t=t, rel_tol=tol, record=True,
+                     cycle_hook=lambda c, x, r, U, SU, SAU, sf: states.append((x.copy(), U, SU, SAU)))
+    Ad = P.CSRDevice.from_numpy(A)
+    bn = np.linalg.norm(b)
+    for ci, (x0, U, SU, SAU) in enumerate(states):
+        solver = P.Solver(A.n, m, k, t, s, zeta, SEED, tol, max_cycles=1)
+        if U is not None and U.shape[1]:
+            P.sdr_recycle_import(solver.h, Ad, dev(U), dev(SU), dev(SAU))
+        xd = dev(x0)
+        st, stats = P.sdr_solve(solver.h, Ad, dev(b), xd)
+        sres, log = solver.history()
+        sres_close(sres, ref.sres_per_cycle[ci], bn)
+        c = ref.cycle_log[ci]
+        assert log[0]["checks"] == len(c.checks)
+        assert abs(log[0]["res"] - c.res) <= 1e-8 * c.res + 1e-13 * bn
+        # recycle space after the cycle: same span as the oracle's
+        Ug, _, _ = P.sdr_recycle_export(solver.h, A.n, s)
+        assert Ug.shape[1] == c.U.shape[1]
+        assert principal_angle(Ug.cpu().numpy(), c.U) < 1e-6
+        solver.close()
+
+
+@pytest.mark.parametrize("t,k,zeta,s", [(1, 10, 8, 120), (3, 10, 8, 120), (4, 5, 4, 90), (2, 0, 8, 100),
+                                        (2, 10, 1, 120), (2, 10, 8, 62)])
+def test_parameter_edges_first_cycles(P, t, k, zeta, s):
+    A = W.make_cd2d(40, (20.0, 5.0))  # N = 1600
+    b = W.rhs(A.n, 7)
+    m, tol = 50, 1e-8
+    solver, Ad, x, st, stats, sres, log, ref = run_pair(P, A, b, m, k, t, s, zeta, tol, max_cycles=2)
+    bn = np.linalg.norm(b)
+    n0 = len(ref.sres_per_cycle[0])
+    sres_close(sres[:n0], ref.sres_per_cycle[0], bn, kappa=saw_conditioning(ref.cycle_log[0]))
+    if t == 2:  # the well-conditioned workloads keep the strict bar with no kappa term
+        sres_close(sres[:n0], ref.sres_per_cycle[0], bn)
+    if len(ref.sres_per_cycle) > 1 and len(log) > 1:
+        sres_close(sres[n0:n0 + len(ref.sres_per_cycle[1])], ref.sres_per_cycle[1], bn,
+                   kappa=saw_conditioning(ref.cycle_log[1]))
+    solver.close()
+
+
+def test_ragged_sizes_and_3d(P):
+    A = W.make_cd3d(17, (20.0, 10.0, 5.0))  # N = 4913: two full sketch tiles and a ragged one
+    b = W.rhs(A.n, 3)
+    m, k, t, s, zeta, tol = 40, 8, 2, 120, 8, 1e-8
+    solver, Ad, x, st, stats, sres, log, ref = run_pair(P, A, b, m, k, t, s, zeta, tol)
+    bn = np.linalg.norm(b)
+    sres_close(sres[:len(ref.sres_per_cycle[0])], ref.sres_per_cycle[0], bn)
+    assert st == 0
+    assert np.linalg.norm(b - osdr.csr_matvec(A, x)) / bn <= tol * (1 + 1e-9)
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+    solver.close()
+
+
+def test_force_svd_path_same_span(P):
+    """The truncated-SVD path and the full-rank path give the same recycle span."""
+    A = W.make_cd2d(40, (10.0, 10.0))
+    b = W.rhs(A.n, 2)
+    m, k, t, s, zeta, tol = 40, 8, 2, 100, 8, 1e-8
+    Ad = P.CSRDevice.from_numpy(A)
+    out = []
+    for force in (False, True):
+        solver = P.Solver(A.n, m, k, t, s, zeta, SEED, tol, max_cycles=1, force_svd=force)
+        x, st, stats = solver.solve(Ad, dev(b))
+        sres, log = solver.history()
+        assert (log[0]["flags"] & 1) == (1 if force else 0)
+        U, _, _ = P.sdr_recycle_export(solver.h, A.n, s)
+        out.append(U.cpu().numpy())
+        solver.close()
+    ref = osdr.solve(A, b, SparseSign(SEED, A.n, s, zeta), m=m, k=k, t=t, rel_tol=tol, max_cycles=1)
+    assert principal_angle(out[0], out[1]) < 1e-7
+    assert principal_angle(out[1], ref.U) < 1e-6
+
+
+def test_sequence_exact_recycling(P):
+    A0 = W.make_cd3d(16, (20.0, 10.0, 5.0))
+    dvec = W.diag_perturbation(A0.n)
+    As = list(W.sequence_matrices(A0, 3, 1e-3 * 1000, dvec))
+    bs = [W.rhs(A0.n, i) for i in range(3)]
+    m, k, t, s, zeta, tol = 40, 8, 2, 120, 8, 1e-8
+    refs = osdr.solve_sequence(As, bs, SparseSign(SEED, A0.n, s, zeta), m=m, k=k, t=t, rel_tol=tol)
+    solver = P.Solver(A0.n, m, k, t, s, zeta, SEED, tol)
+    for i, (A, b, ref) in enumerate(zip(As, bs, refs)):
+        Ad = P.CSRDevice.from_numpy(A)
+        if i > 0:
+            solver.recycle(Ad, 0)
+        x, st, stats = solver.solve(Ad, dev(b))
+        sres, log = solver.history()
+        bn = np.linalg.norm(b)
+        xh = x.cpu().numpy()
+        assert st == 0
+        assert np.linalg.norm(b - osdr.csr_matvec(A, xh)) / bn <= tol * (1 + 1e-9)
+        assert np.linalg.norm(xh - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+        assert abs(stats["cycles"] - ref.cycles) <= 1
+        sres_close(sres[:len(ref.sres_per_cycle[0])], ref.sres_per_cycle[0], bn)
+    solver.close()
+
+
+def test_already_converged_and_errors(P):
+    A = W.make_cd2d(24)
+    b = W.rhs(A.n)
+    xs = np.linalg.solve(W.csr_to_dense(A), b)
+    solver = P.Solver(A.n, 20, 4, 2, 40, 8, SEED, 1e-8)
+    Ad = P.CSRDevice.from_numpy(A)
+    xd = dev(xs)
+    st, stats = P.sdr_solve(solver.h, Ad, dev(b), xd)
+    assert st == 0 and stats["cycles"] == 0
+    # size beyond n_max is rejected on the host
+    big = P.CSRDevice.from_numpy(W.make_cd2d(30))
+    with pytest.raises(P.SdrError):
+        P.sdr_solve(solver.h, big, dev(W.rhs(900)), dev(np.zeros(900)))
+    solver.close()
+    with pytest.raises(P.SdrError):
+        P.Solver(100, 20, 4, 2, 20, 8, SEED, 1e-8)  # s < m + k + 2
