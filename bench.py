@@ -1,0 +1,380 @@
+"""Benchmark: time-to-1e-8 per system of a GMRES-SDR sequence on one GB300.
+
+Workload: 3D convection-diffusion 128^3 (N = 2,097,152, 7-point upwind,
+convection (20, 10, 5)); 20 systems A^(i) = A0 + i 1e-3 D with D = diag(U[0,1]),
+b^(i) ~ N(0,1); m = 100, k = 20, t = 2, s = 480, zeta = 8, rel_tol 1e-8,
+exact recycling (SAU recomputed for each new matrix).  One step = one system:
+sdr_recycle(exact) + sdr_solve to ||b - A x|| < 1e-8 ||b||.
+
+Output: one JSON line.  value = wall time per system on the device (CUDA
+events, inputs resident in HBM); e2e = the same through the C ABI with the
+system's inputs copied from pinned host memory and x copied back inside the
+timed region.  roofline = the dominant kernel class, algorithmic bytes / CUDA
+event time of its launches in the timed region.  cpu_baseline = the FP64 CPU
+oracle on a bounded sample of the same workload (single thread).
+
+--impl reference runs the oracle instead (host cores only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="cd3d_128_seq20", n=128, conv=(20.0, 10.0, 5.0), systems=20, eps=1e-3,
+                m=100, k=20, t=2, s=480, zeta=8, rel_tol=1e-8, seed=231114206)
+METRIC = "time-to-1e-8 residual per system in sequence; cycle HBM GB/s vs ~8 TB/s peak"
+UNIT = "ms/system"
+# Arnoldi-step equivalents per system of this workload (Arnoldi steps + true-residual
+# checks + k SpMVs of the exact recycling) used to scale the oracle's per-step time to
+# a per-system time.  Measured on the GPU arm (the oracle's cycle counts agree within
+# one cycle per system in the parity tests); overwritten by the GPU arm's own count
+# whenever it runs in the same process.
+STEP_EQUIV_PER_SYSTEM = 700
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", os.environ.get("LOCAL_RANK", "0")],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- inputs
+def make_inputs(cfg):
+    import numpy as np
+    import workloads as W
+    A0 = W.make_cd3d(cfg["n"], cfg["conv"])
+    dvec = W.diag_perturbation(A0.n)
+    rows = np.repeat(np.arange(A0.n), np.diff(A0.rowptr.astype(np.int64)))
+    diag_pos = np.nonzero(A0.col.astype(np.int64) == rows)[0]
+    return A0, dvec, diag_pos
+
+
+def system_values(A0, dvec, diag_pos, i, eps):
+    """Values of A^(i) = A0 + i eps D (same sparsity pattern as A0)."""
+    v = A0.val.copy()
+    v[diag_pos] += i * eps * dvec
+    return v
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_2311_14206_gb300 as P
+
+    cfg = WORKLOAD
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda")
+    A0, dvec, diag_pos = make_inputs(cfg)
+    N, nnz = A0.n, A0.nnz
+    nsys = cfg["systems"]
+    rowptr = torch.as_tensor(A0.rowptr, device=dev)
+    col = torch.as_tensor(A0.col, device=dev)
+    vals = [torch.as_tensor(system_values(A0, dvec, diag_pos, i + 1, cfg["eps"]), device=dev) for i in range(nsys)]
+    # each replica solves its own right-hand sides (weak scaling)
+    bs = [torch.as_tensor(W.rhs(N, 1000 * rank + i), device=dev) for i in range(nsys)]
+    mats = [P.CSRDevice(N, rowptr, col, v) for v in vals]
+    solver = P.Solver(N, cfg["m"], cfg["k"], cfg["t"], cfg["s"], cfg["zeta"], cfg["seed"], cfg["rel_tol"])
+    xs = torch.zeros(N, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    seq = {"i": 0}
+
+    def step(stats_out=None):
+        i = seq["i"] % nsys
+        A = mats[i]
+        if seq["i"] > 0:
+            solver.recycle(A, 0)
+        xs.zero_()
+        st, stats = P.sdr_solve(solver.h, A, bs[i], xs)
+        if st != 0:
+            raise RuntimeError(f"system {i}: status {st} {stats}")
+        seq["i"] += 1
+        if stats_out is not None:
+            stats_out.append(stats)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    # ---- timed region: inputs resident in HBM ----
+    P.sdr_profile(solver.h, True)
+    clocks = ClockSampler()
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t_wall = time.perf_counter()
+    stats_list = []
+    launches = 0
+    for _ in range(args.steps):
+        step(stats_list)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = P.sdr_profile_get(solver.h)
+    P.sdr_profile(solver.h, False)
+    # kernels of this library in the timed region: the solves' own count plus four
+    # kernels per recycled column of the exact SAU recomputation
+    launches = sum(s_["kernel_launches"] for s_ in stats_list) + 4 * prof["recycle_sau"][0]
+    # ---- e2e: the same steps through the C ABI from pinned host buffers ----
+    host_vals = [v.cpu().pin_memory() for v in vals]
+    host_bs = [b.cpu().pin_memory() for b in bs]
+    host_x = torch.empty(N, dtype=torch.float64).pin_memory()
+    dval = torch.empty_like(vals[0])
+    db = torch.empty_like(bs[0])
+    dA = P.CSRDevice(N, rowptr, col, dval)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        i = seq["i"] % nsys
+        dval.copy_(host_vals[i], non_blocking=True)
+        db.copy_(host_bs[i], non_blocking=True)
+        solver.recycle(dA, 0)
+        xs.zero_()
+        st, _ = P.sdr_solve(solver.h, dA, db, xs)
+        host_x.copy_(xs, non_blocking=True)
+        seq["i"] += 1
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    h2d = (vals[0].numel() + bs[0].numel()) * 8
+    d2h = N * 8
+    solver.close()
+
+    # ---- roofline of the dominant kernel class ----
+    agg = {k: 0 for k in ("steps", "checks", "cycles", "sau", "svd")}
+    for s_ in stats_list:
+        agg["svd"] += s_["full_svd_cycles"]
+        agg["steps"] += s_["arnoldi_steps"]
+        agg["checks"] += s_["true_res_evals"]
+        agg["cycles"] += s_["cycles"]
+    m, t = cfg["m"], cfg["t"]
+    mat_bytes = 12 * nnz + 4 * (N + 1)
+    vec = 8 * N
+    # spmv_dots: matrix + x gather + w write + (t-1) window reads (none at j = 0)
+    steps_j0 = agg["cycles"]
+    bytes_spmv = agg["steps"] * (mat_bytes + 2 * vec) + (agg["steps"] - steps_j0) * (t - 1) * vec
+    # update_sketch: w and window reads + v_{j+1} write
+    bytes_upd = agg["steps"] * (2 * vec) + (agg["steps"] - steps_j0) * (t - 1) * vec + steps_j0 * 0
+    kprime = cfg["k"] + 1
+    avg_d = (agg["steps"] / max(agg["cycles"], 1)) + kprime
+    bytes_gemm = agg["cycles"] * vec * (avg_d + kprime)
+    hbm, peak_kind = peaks()
+    classes = {
+        "spmv_dots": (bytes_spmv, "hbm"),
+        "update_sketch": (bytes_upd, "hbm"),
+        "recycle_gemm": (bytes_gemm, "hbm"),
+    }
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    rf_name = dom if dom in classes else max(classes, key=lambda c: prof[c][1])
+    rb, bound = classes[rf_name]
+    rl, rms = prof[rf_name]
+    achieved = rb / (rms * 1e-3) / 1e9 if rms > 0 else 0.0
+    systems = args.steps
+    result = dict(ms=ms, wall=wall, clocks=ck, prof=prof, e2e_ms=e2e_ms, h2d=h2d, d2h=d2h, launches=launches,
+                  roofline=dict(kernel=rf_name, bound=bound, achieved=achieved, peak=hbm,
+                                peak_kind=peak_kind, unit="GB/s", frac=achieved / hbm,
+                                bytes_per_launch=rb / max(rl, 1), launches=rl, ms_per_launch=rms / max(rl, 1),
+                                traffic=None),
+                  systems=systems, agg=agg, N=N, nnz=nnz)
+    return result
+
+
+# --------------------------------------------------------------------------- oracle arm
+ORACLE_SAMPLE_STEPS = 12
+
+
+def oracle_sample(steps=ORACLE_SAMPLE_STEPS, system=1):
+    """Time the oracle on the first `steps` Arnoldi steps of one system of the
+    workload (single thread) and return seconds per Arnoldi-step equivalent."""
+    import numpy as np
+    import workloads as W
+    from oracle import sdr as osdr
+    from oracle.sketch import SparseSign
+    cfg = WORKLOAD
+    A0, dvec, diag_pos = make_inputs(cfg)
+    A = W.CSR(A0.n, A0.rowptr, A0.col, system_values(A0, dvec, diag_pos, system, cfg["eps"]))
+    b = W.rhs(A.n, system)
+    S = SparseSign(cfg["seed"], A.n, cfg["s"], cfg["zeta"])
+    t0 = time.perf_counter()
+    # a bounded cycle: `steps` Arnoldi steps with the true-residual check at the end
+    c = osdr.cycle(A, b, None, None, None, S, cfg["rel_tol"] * np.linalg.norm(b), steps, cfg["t"], cfg["k"])
+    dt = time.perf_counter() - t0
+    return dt / (steps + 1), dict(steps=steps, seconds=dt)
+
+
+def run_oracle_subprocess(steps=ORACLE_SAMPLE_STEPS):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; r = bench.oracle_sample(%d); "
+            "print(json.dumps({'per_step': r[0], 'info': r[1]}))" % (ROOT, steps))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(step_equiv):
+    r = run_oracle_subprocess()
+    per_system_ms = r["per_step"] * step_equiv * 1e3
+    return dict(value=per_system_ms, unit=UNIT, cores=1, kind="oracle",
+                sample=(f"FP64 numpy oracle, 1 thread: first {r['info']['steps']} Arnoldi steps of system 1 "
+                        f"(N=2,097,152) plus one true-residual check took {r['info']['seconds']:.1f} s; "
+                        f"scaled by {step_equiv:.0f} step-equivalents per system"))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    per = []
+    for _ in range(args.warmup):
+        run_oracle_subprocess(4)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = run_oracle_subprocess(4)
+        per.append(r["per_step"])
+    wall = time.perf_counter() - t0
+    value = statistics.mean(per) * STEP_EQUIV_PER_SYSTEM * 1e3
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=value, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD["workload"], N=2097152, m=100, k=20, t=2, s=480, zeta=8,
+                            systems=20, rel_tol=1e-8),
+                cpu_baseline=dict(kind="oracle", cores=1, value=value, unit=UNIT,
+                                  sample=("each step: FP64 numpy oracle (1 thread) on 4 Arnoldi steps + one check "
+                                          f"of system 1, scaled by {STEP_EQUIV_PER_SYSTEM} step-equivalents per "
+                                          f"system; {wall:.0f} s for the timed steps")),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--breakdown", action="store_true", help="print the per-kernel-class times to stderr")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+    import torch
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.distributed.init_process_group("nccl")
+    import __graft_entry__ as g
+    g.build()
+    res = run_gpu(args, rank, world)
+    ms_per_system = res["ms"] / res["systems"]
+    if world > 1:
+        t = torch.tensor([res["ms"]], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+        ms_per_system = ms_total / (res["systems"] * world)
+    if rank == 0:
+        agg = res["agg"]
+        step_equiv = (agg["steps"] + agg["checks"] + WORKLOAD["k"] * res["systems"]) / max(res["systems"], 1)
+        cpu = None if args.no_cpu_baseline else cpu_baseline(step_equiv)
+        rf = res["roofline"]
+        line = dict(
+            metric=METRIC, value=ms_per_system, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=res["ms"] / res["systems"], higher_is_better=False, scaling="weak", vs_baseline=None,
+            dtype="f64", data="synthetic",
+            config=dict(workload=WORKLOAD["workload"], N=res["N"], nnz=res["nnz"], m=100, k=20, t=2, s=480,
+                        zeta=8, systems=20, rel_tol=1e-8, recycling="exact", l2="inputs larger than L2",
+                        parallelism=f"replicas{world}"),
+            roofline=dict(bound=rf["bound"], achieved=rf["achieved"], peak=rf["peak"], unit=rf["unit"],
+                          frac=rf["frac"], traffic=rf["traffic"], kernel=rf["kernel"],
+                          peak_source=f"{rf['peak_kind']} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
+                          bytes_per_launch=rf["bytes_per_launch"], ms_per_launch=rf["ms_per_launch"]),
+            clocks=res["clocks"],
+            e2e=dict(value=res["e2e_ms"], unit=UNIT, h2d_bytes_per_step=res["h2d"], d2h_bytes_per_step=res["d2h"]),
+            gpu_launches=res["launches"],
+            cpu_baseline=cpu,
+            per_system=dict(arnoldi_steps=agg["steps"] / res["systems"], checks=agg["checks"] / res["systems"],
+                            cycles=agg["cycles"] / res["systems"], svd_path_cycles=agg["svd"]),
+        )
+        if args.breakdown:
+            tot = sum(v[1] for v in res["prof"].values())
+            for k, (n, t) in sorted(res["prof"].items(), key=lambda kv: -kv[1][1]):
+                print(f"  {k:16s} launches {n:7d}  {t:10.2f} ms  {100 * t / max(tot, 1e-9):5.1f}%  "
+                      f"{1e3 * t / max(n, 1):9.2f} us/launch", file=sys.stderr)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

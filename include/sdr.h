@@ -95,6 +95,8 @@ typedef struct {
   int32_t arnoldi_steps;   /* truncated Arnoldi steps over all cycles */
   int32_t recycle_dim;     /* columns of U after the solve */
   int32_t full_svd_cycles; /* cycles that needed the truncated-SVD path */
+  int32_t kernel_launches; /* kernels of this library launched by the call */
+  int32_t reserved_i;
   double final_res;        /* last true residual norm */
   double tol;              /* rel_tol * ||b|| */
   double final_rel_res;    /* final_res / ||b|| */
@@ -172,6 +174,47 @@ sdr_status sdr_recycle_export(sdr_handle* h, int64_t n, double* U, double* SU, d
  * kdim <= k + 1. */
 sdr_status sdr_recycle_import(sdr_handle* h, const sdr_csr* A, int64_t n, int32_t kdim,
                               const double* U, const double* SU, const double* SAU);
+
+/* ---- timing of the library's own kernels ---------------------------- */
+
+/* Kernel classes of sdr_kernel_time entries (index = class). */
+enum {
+  SDR_K_SOLVE_INIT = 0,   /* ||b||, max|b|, ||A||_inf at the start of a solve */
+  SDR_K_RESIDUAL0,        /* initial residual b - A x0 with its sketch */
+  SDR_K_CYCLE_INIT,       /* S r0, beta, QR of SAU (Algorithm 1 set-up) */
+  SDR_K_SPMV_DOTS,        /* w = A v_j with truncation-window dots */
+  SDR_K_UPDATE_SKETCH,    /* truncated-Arnoldi update with the fused sketch */
+  SDR_K_STEP_DENSE,       /* QR update of SAW, sketched residual, control */
+  SDR_K_CHECK_GEMV,       /* x_trial = x + [U V] y (launched every step, works on checks) */
+  SDR_K_CHECK_RESIDUAL,   /* true residual of x_trial (launched every step, works on checks) */
+  SDR_K_CYCLE_END,        /* harmonic-Ritz recycling: C = Q^T S[U V] (first of eight parts) */
+  SDR_K_RECYCLE_GEMM,     /* U_new = [U V] P */
+  SDR_K_RECYCLE_SAU,      /* SAU = S A U for the exact variant (per column) */
+  SDR_K_SKETCH,           /* stand-alone sketches (sdr_sketch, SU) */
+  SDR_K_CE_RINV,          /* cycle end: R^{-1} */
+  SDR_K_CE_M,             /* cycle end: full-rank certificate and M = R^{-1} C */
+  SDR_K_CE_SVD,           /* cycle end: truncated SVD (only when not certified) */
+  SDR_K_CE_EIG,           /* cycle end: FP32 eigenvalue candidates (Hessenberg + Francis QR) */
+  SDR_K_CE_INVIT,         /* cycle end: FP64 inverse iteration per candidate */
+  SDR_K_CE_SELECT,        /* cycle end: selection of the k largest |mu| */
+  SDR_K_CE_FINISH,        /* cycle end: orthonormal basis Z and P */
+  SDR_K_CE_SKETCHES,      /* cycle end: SU, SAU of the new recycle space */
+  SDR_K_COUNT
+};
+
+typedef struct {
+  int32_t launches;  /* launches of the class since profiling was enabled */
+  int32_t pad;
+  double total_ms;   /* summed CUDA-event time between each launch's start and end */
+} sdr_kernel_time;
+
+/* enable != 0: bracket every kernel launch with CUDA events on the handle's
+ * stream and accumulate per-class times (resets the totals); 0: stop. */
+sdr_status sdr_profile(sdr_handle* h, int32_t enable);
+
+/* Copy min(cap, SDR_K_COUNT) per-class totals into out (host pointer); *n
+ * receives SDR_K_COUNT. */
+sdr_status sdr_profile_get(sdr_handle* h, sdr_kernel_time* out, int32_t cap, int32_t* n);
 
 /* Human-readable text of a status (static storage). */
 const char* sdr_status_string(sdr_status st);

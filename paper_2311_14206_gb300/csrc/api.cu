@@ -20,6 +20,16 @@ size_t ce_scratch_doubles();
 
 using namespace sdr;
 
+// Per-launch CUDA-event timing (enabled by sdr_profile).
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<int> cls;  // class of event pair i (events 2i, 2i+1)
+  double total_ms[SDR_K_COUNT] = {};
+  int launches[SDR_K_COUNT] = {};
+};
+
 struct sdr_handle {
   sdr_params p;
   int64_t n_max;
@@ -34,6 +44,8 @@ struct sdr_handle {
   std::vector<double> hist;
   std::vector<CycleLog> log;
   double* d_tmp = nullptr;  // n_max scratch vector (A u)
+  Prof prof;
+  int launches = 0;  // kernels launched by the current call
 };
 
 namespace {
@@ -75,6 +87,50 @@ CsrDev to_dev(const sdr_csr* A) { return CsrDev{A->n, A->nnz, A->rowptr, A->col,
 
 int* ctl_int_field(Ctl* c, size_t off) { return (int*)((char*)c + off); }
 
+// Kernels issued by each launcher (for the launch count).
+constexpr int kKernelsPerClass[SDR_K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 3, 1, 1, 1, 1, 1, 1, 1, 1};
+
+cudaError_t prof_begin(sdr_handle* h, int cls) {
+  h->launches += kKernelsPerClass[cls];
+  if (!h->prof.on) return cudaSuccess;
+  Prof& P = h->prof;
+  while (P.pool.size() < 2 * (P.cls.size() + 1)) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    P.pool.push_back(e);
+  }
+  P.cls.push_back(cls);
+  return cudaEventRecord(P.pool[2 * (P.cls.size() - 1)], h->st);
+}
+
+cudaError_t prof_end(sdr_handle* h) {
+  if (!h->prof.on) return cudaSuccess;
+  return cudaEventRecord(h->prof.pool[2 * (h->prof.cls.size() - 1) + 1], h->st);
+}
+
+// Fold the recorded event pairs into the totals (stream must be idle).
+cudaError_t prof_collect(sdr_handle* h) {
+  Prof& P = h->prof;
+  if (!P.on) return cudaSuccess;
+  for (size_t i = 0; i < P.cls.size(); ++i) {
+    float ms = 0.f;
+    cudaError_t r = cudaEventElapsedTime(&ms, P.pool[2 * i], P.pool[2 * i + 1]);
+    if (r != cudaSuccess) return r;
+    P.total_ms[P.cls[i]] += ms;
+    P.launches[P.cls[i]] += 1;
+  }
+  P.cls.clear();
+  return cudaSuccess;
+}
+
+#define SDR_LAUNCH(h, cls, call)               \
+  do {                                         \
+    SDR_CK(prof_begin((h), (cls)));            \
+    SDR_CK(call);                              \
+    SDR_CK(prof_end(h));                       \
+  } while (0)
+
 }  // namespace
 
 extern "C" {
@@ -97,6 +153,7 @@ const char* sdr_status_string(sdr_status st) {
 
 sdr_status sdr_destroy(sdr_handle* h) {
   if (!h) return SDR_OK;
+  for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   for (void* q : h->allocs) cudaFree(q);
   delete h;
   return SDR_OK;
@@ -208,11 +265,12 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
   cudaStream_t st = h->st;
   const int m = ws.m;
   unsigned long long* accR = ws.acc + 2 * S_MAX;
-  SDR_CK(launch_solve_init_x(ws, Ad, b, x, h->p.rel_tol, st));
+  h->launches = 0;
+  SDR_LAUNCH(h, SDR_K_SOLVE_INIT, launch_solve_init_x(ws, Ad, b, x, h->p.rel_tol, st));
   double* xcur = x;
   double* xoth = ws.Xw;
   int rb = 0;
-  SDR_CK(launch_residual(ws, Ad, b, xcur, ws.R[rb], accR, -1, 0, st));
+  SDR_LAUNCH(h, SDR_K_RESIDUAL0, launch_residual(ws, Ad, b, xcur, ws.R[rb], accR, -1, 0, st));
   Ctl hc;
   SDR_CK(cudaMemcpyAsync(&hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   SDR_CK(cudaStreamSynchronize(st));
@@ -225,16 +283,18 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
     vcol[0] = ws.R[rb];
     for (int c = 1; c <= m; ++c) vcol[c] = ws.Vs + (int64_t)(c - 1) * ws.ldv;
     const int cu = h->cu, kh = h->kh;
-    SDR_CK(launch_cycle_init(ws, ws.SAU[cu], kh, accR, h->p.persist_safety, st));
+    SDR_LAUNCH(h, SDR_K_CYCLE_INIT, launch_cycle_init(ws, ws.SAU[cu], kh, accR, h->p.persist_safety, st));
     for (int j = 0; j < m; ++j) {
-      SDR_CK(launch_spmv_dots(ws, Ad, vcol.data(), j, st));
-      SDR_CK(launch_update_sketch(ws, vcol.data(), (double*)vcol[j + 1], j, st));
-      SDR_CK(launch_step_dense(ws, j, kh, accR, st));
-      SDR_CK(launch_check_gemv(ws, ws.U[cu], vcol.data(), xcur, xoth, kh, j, st));
-      SDR_CK(launch_residual(ws, Ad, b, xoth, ws.R[1 - rb], accR, j, 1, st));
+      SDR_LAUNCH(h, SDR_K_SPMV_DOTS, launch_spmv_dots(ws, Ad, vcol.data(), j, st));
+      SDR_LAUNCH(h, SDR_K_UPDATE_SKETCH, launch_update_sketch(ws, vcol.data(), (double*)vcol[j + 1], j, st));
+      SDR_LAUNCH(h, SDR_K_STEP_DENSE, launch_step_dense(ws, j, kh, accR, st));
+      SDR_LAUNCH(h, SDR_K_CHECK_GEMV, launch_check_gemv(ws, ws.U[cu], vcol.data(), xcur, xoth, kh, j, st));
+      SDR_LAUNCH(h, SDR_K_CHECK_RESIDUAL, launch_residual(ws, Ad, b, xoth, ws.R[1 - rb], accR, j, 1, st));
     }
-    SDR_CK(launch_cycle_end(ws, kh, ws.SU[cu], ws.SAU[cu], ws.SU[1 - cu], ws.SAU[1 - cu], st));
-    SDR_CK(launch_recycle_gemm(ws, ws.U[cu], vcol.data(), ws.U[1 - cu], kh, st));
+    for (int part = 0; part < CYCLE_END_PARTS; ++part)
+      SDR_LAUNCH(h, part == 0 ? SDR_K_CYCLE_END : SDR_K_CE_RINV + part - 1,
+                 launch_cycle_end_part(part, ws, kh, ws.SU[cu], ws.SAU[cu], ws.SU[1 - cu], ws.SAU[1 - cu], st));
+    SDR_LAUNCH(h, SDR_K_RECYCLE_GEMM, launch_recycle_gemm(ws, ws.U[cu], vcol.data(), ws.U[1 - cu], kh, st));
     SDR_CK(cudaMemcpyAsync(&hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     SDR_CK(cudaStreamSynchronize(st));
     ++cycles;
@@ -265,6 +325,7 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
   if (nh) SDR_CK(cudaMemcpyAsync(h->hist.data(), ws.hist, nh * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (nl) SDR_CK(cudaMemcpyAsync(h->log.data(), ws.log, nl * sizeof(CycleLog), cudaMemcpyDeviceToHost, st));
   SDR_CK(cudaStreamSynchronize(st));
+  SDR_CK(prof_collect(h));
   if (status == SDR_OK && !converged) status = SDR_ERR_NOT_CONVERGED;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
@@ -278,6 +339,7 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
     stats->arnoldi_steps = hc.hist_n;
     stats->recycle_dim = h->kh;
     stats->full_svd_cycles = full_svd;
+    stats->kernel_launches = h->launches;
     stats->final_res = hc.res;
     stats->tol = hc.tol;
     stats->bnorm = hc.bnorm;
@@ -293,14 +355,18 @@ static sdr_status recompute_sau(sdr_handle* h, const sdr_csr* A, int64_t n) {
   const CsrDev Ad = to_dev(A);
   unsigned long long* accG = ws.acc + 4 * S_MAX;
   int* topG = ctl_int_field(ws.ctl, offsetof(Ctl, accG_top));
+  h->launches = 0;
   for (int c = 0; c < h->kh; ++c) {
     const double* u = ws.U[h->cu] + (int64_t)c * ws.ldv;
+    SDR_CK(prof_begin(h, SDR_K_RECYCLE_SAU));
     SDR_CK(launch_spmv(Ad, u, h->d_tmp, h->st));
     SDR_CK(launch_maxabs_top(ws, h->d_tmp, n, topG, h->st));
     SDR_CK(launch_sketch_vec(ws, h->d_tmp, n, accG, topG, h->st));
     SDR_CK(launch_sketch_finish(ws, accG, topG, ws.SAU[h->cu] + (int64_t)c * ws.s, h->st));
+    SDR_CK(prof_end(h));
   }
   SDR_CK(cudaStreamSynchronize(h->st));
+  SDR_CK(prof_collect(h));
   return SDR_OK;
 }
 
@@ -311,11 +377,14 @@ static sdr_status recompute_su(sdr_handle* h, int64_t n) {
   int* topG = ctl_int_field(ws.ctl, offsetof(Ctl, accG_top));
   for (int c = 0; c < h->kh; ++c) {
     const double* u = ws.U[h->cu] + (int64_t)c * ws.ldv;
+    SDR_CK(prof_begin(h, SDR_K_SKETCH));
     SDR_CK(launch_maxabs_top(ws, u, n, topG, h->st));
     SDR_CK(launch_sketch_vec(ws, u, n, accG, topG, h->st));
     SDR_CK(launch_sketch_finish(ws, accG, topG, ws.SU[h->cu] + (int64_t)c * ws.s, h->st));
+    SDR_CK(prof_end(h));
   }
   SDR_CK(cudaStreamSynchronize(h->st));
+  SDR_CK(prof_collect(h));
   return SDR_OK;
 }
 
@@ -338,10 +407,14 @@ sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y) {
   ws.n = n;
   unsigned long long* accG = ws.acc + 4 * S_MAX;
   int* topG = ctl_int_field(ws.ctl, offsetof(Ctl, accG_top));
+  h->launches = 0;
+  SDR_CK(prof_begin(h, SDR_K_SKETCH));
   SDR_CK(launch_maxabs_top(ws, x, n, topG, h->st));
   SDR_CK(launch_sketch_vec(ws, x, n, accG, topG, h->st));
   SDR_CK(launch_sketch_finish(ws, accG, topG, y, h->st));
+  SDR_CK(prof_end(h));
   SDR_CK(cudaStreamSynchronize(h->st));
+  SDR_CK(prof_collect(h));
   return SDR_OK;
 }
 
@@ -354,6 +427,29 @@ sdr_status sdr_get_history(sdr_handle* h, double* sres, int32_t cap_steps, int32
   if (n_cycles) *n_cycles = nl;
   if (sres && cap_steps > 0) std::memcpy(sres, h->hist.data(), sizeof(double) * (nh < cap_steps ? nh : cap_steps));
   if (log && cap_cycles > 0) std::memcpy(log, h->log.data(), sizeof(CycleLog) * (nl < cap_cycles ? nl : cap_cycles));
+  return SDR_OK;
+}
+
+sdr_status sdr_profile(sdr_handle* h, int32_t enable) {
+  if (!h) return SDR_ERR_INVALID_ARG;
+  Prof& P = h->prof;
+  P.on = enable != 0;
+  P.cls.clear();
+  for (int i = 0; i < SDR_K_COUNT; ++i) {
+    P.total_ms[i] = 0.0;
+    P.launches[i] = 0;
+  }
+  return SDR_OK;
+}
+
+sdr_status sdr_profile_get(sdr_handle* h, sdr_kernel_time* out, int32_t cap, int32_t* n) {
+  if (!h) return SDR_ERR_INVALID_ARG;
+  if (n) *n = SDR_K_COUNT;
+  for (int i = 0; i < SDR_K_COUNT && i < cap && out; ++i) {
+    out[i].launches = h->prof.launches[i];
+    out[i].pad = 0;
+    out[i].total_ms = h->prof.total_ms[i];
+  }
   return SDR_OK;
 }
 

@@ -21,9 +21,12 @@
 namespace sdr {
 
 constexpr int LDD = D_MAX;  // leading dimension of the d x d scratch matrices
+constexpr int KC_MARGIN = 8;      // extra eigenvalue candidates beyond k
+constexpr int KC = K_MAX + KC_MARGIN + 1;  // candidates refined in FP64
 
 struct CeLayout {
   double *C, *Rinv, *M, *Hc, *Vh, *As, *tauH, *wr, *wi, *Zr, *Pu, *colsq, *misc, *lu;
+  double *cmu, *cref, *cvec;  // candidate estimates, FP64 eigenvalues, FP64 vectors (re, im)
   int* sel;   // [K_MAX] eigenvalue index per inverse iteration
   int* zcol;  // [K_MAX] first Z column of that eigenvalue
   int* cnt;   // [0] number of inverse iterations
@@ -48,12 +51,17 @@ __host__ __device__ inline CeLayout ce_layout(double* base) {
   L.sel = (int*)(L.misc + 64);
   L.zcol = L.sel + K_MAX;
   L.cnt = L.zcol + K_MAX;
-  L.lu = L.misc + 64 + 3 * K_MAX;  // K_MAX blocks of 2*LDD*LDD (complex LU)
+  L.cmu = L.misc + 64 + 3 * K_MAX;
+  L.cref = L.cmu + 2 * KC;
+  L.cvec = L.cref + 2 * KC;
+  L.lu = L.cvec + (int64_t)2 * KC * LDD;  // KC blocks of 2*LDD*LDD (complex LU)
   return L;
 }
 
-size_t ce_scratch_doubles() { return (size_t)6 * LDD * LDD + 3 * LDD + 2 * (size_t)LDD * K_MAX + 2 * LDD + 64 +
-                                     3 * K_MAX + (size_t)K_MAX * 2 * LDD * LDD + 64; }
+size_t ce_scratch_doubles() {
+  return (size_t)6 * LDD * LDD + 3 * LDD + 2 * (size_t)LDD * K_MAX + 2 * LDD + 64 + 3 * K_MAX + 4 * KC +
+         (size_t)2 * KC * LDD + (size_t)KC * 2 * LDD * LDD + 64;
+}
 
 // Column l of S[U V] / SAW (sketched basis / sketched image).
 __device__ inline const double* sv_col(const WS& ws, const double* SU, int kh, int l) {
@@ -294,10 +302,177 @@ __global__ void __launch_bounds__(512) k_ce_svd(WS ws, int kh) {
 }
 
 // ---------------------------------------------------------------------------
-// Hessenberg reduction + Francis double-shift QR (eigenvalues) + selection.
-// H lives in shared memory with leading dimension n+1.
+// Eigenvalue estimates in FP32: Householder reduction to Hessenberg form and
+// Francis double-shift QR, then the candidate list (k + KC_MARGIN largest
+// |mu|, conjugate pairs kept whole).  FP32 only locates the eigenvalues; every
+// selected eigenpair is recomputed in FP64 by inverse iteration with M itself.
+// (On this GPU a full-warp FP64 instruction and a one-lane FP64 instruction
+// occupy the FP64 pipe equally, so a sequential FP64 QR sweep on one SM costs
+// milliseconds; the FP32 sweep does not.)
 // ---------------------------------------------------------------------------
-__device__ inline double& HS(double* H, int ldh, int i, int j) { return H[i + j * ldh]; }
+__device__ inline float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ inline float block_sum_f(float v, float* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum_f(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    float r = lane < nw ? red[lane] : 0.f;
+    r = warp_sum_f(r);
+    if (lane == 0) red[0] = r;
+  }
+  __syncthreads();
+  const float r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ inline float& HF(float* H, int ldh, int i, int j) { return H[i + j * ldh]; }
+
+// Francis double-shift QR on the upper-Hessenberg H (n x n, ld ldh), one warp;
+// eigenvalues into wr, wi.  Returns false when the iteration limit is reached.
+__device__ bool hqr_f32_warp(float* H, int ldh, int n, float* wr, float* wi) {
+  const int lane = threadIdx.x & 31;
+  const float eps = 1.1920929e-7f;
+  float an = 0.f;
+  for (int idx = lane; idx < n * n; idx += 32) {
+    const int i = idx % n, j = idx / n;
+    if (i <= j + 1) an += fabsf(HF(H, ldh, i, j));
+  }
+  an = warp_sum_f(an);
+  int nn = n - 1, total = 0;
+  float tsh = 0.f;
+  while (nn >= 0) {
+    int its = 0;
+    while (true) {
+      int l = nn;
+      while (l > 0) {
+        float s = fabsf(HF(H, ldh, l - 1, l - 1)) + fabsf(HF(H, ldh, l, l));
+        if (s == 0.f) s = an;
+        if (fabsf(HF(H, ldh, l, l - 1)) <= eps * s) break;
+        --l;
+      }
+      __syncwarp();
+      if (l > 0 && lane == 0) HF(H, ldh, l, l - 1) = 0.f;
+      __syncwarp();
+      float x = HF(H, ldh, nn, nn);
+      if (l == nn) {
+        if (lane == 0) { wr[nn] = x + tsh; wi[nn] = 0.f; }
+        nn -= 1;
+        break;
+      }
+      float y = HF(H, ldh, nn - 1, nn - 1);
+      float w = HF(H, ldh, nn, nn - 1) * HF(H, ldh, nn - 1, nn);
+      if (l == nn - 1) {
+        const float p = 0.5f * (y - x), q = p * p + w;
+        float z = sqrtf(fabsf(q));
+        x += tsh;
+        if (lane == 0) {
+          if (q >= 0.f) {
+            z = p + copysignf(z, p);
+            wr[nn - 1] = wr[nn] = x + z;
+            if (z != 0.f) wr[nn] = x - w / z;
+            wi[nn - 1] = wi[nn] = 0.f;
+          } else {
+            wr[nn - 1] = wr[nn] = x + p;
+            wi[nn - 1] = z;
+            wi[nn] = -z;
+          }
+        }
+        nn -= 2;
+        break;
+      }
+      if (its >= 60 || total >= 60 * n) {
+        for (int i = lane; i <= nn; i += 32) { wr[i] = NAN; wi[i] = 0.f; }
+        __syncwarp();
+        return false;
+      }
+      if (its == 10 || its == 20) {  // exceptional shift
+        tsh += x;
+        __syncwarp();
+        for (int i = lane; i <= nn; i += 32) HF(H, ldh, i, i) -= x;
+        __syncwarp();
+        const float s = fabsf(HF(H, ldh, nn, nn - 1)) + fabsf(HF(H, ldh, nn - 1, nn - 2));
+        x = y = 0.75f * s;
+        w = -0.4375f * s * s;
+      }
+      ++its;
+      ++total;
+      int m = nn - 2;
+      float p = 0.f, q = 0.f, r = 0.f, z = 0.f;
+      while (true) {
+        z = HF(H, ldh, m, m);
+        const float rr = x - z, ss = y - z;
+        p = (rr * ss - w) / HF(H, ldh, m + 1, m) + HF(H, ldh, m, m + 1);
+        q = HF(H, ldh, m + 1, m + 1) - z - rr - ss;
+        r = HF(H, ldh, m + 2, m + 1);
+        const float inv = 1.f / (fabsf(p) + fabsf(q) + fabsf(r));
+        p *= inv; q *= inv; r *= inv;
+        if (m == l) break;
+        const float u = fabsf(HF(H, ldh, m, m - 1)) * (fabsf(q) + fabsf(r));
+        const float v = fabsf(p) * (fabsf(HF(H, ldh, m - 1, m - 1)) + fabsf(z) + fabsf(HF(H, ldh, m + 1, m + 1)));
+        if (u <= eps * v) break;
+        --m;
+      }
+      __syncwarp();
+      for (int i = m + 2 + lane; i <= nn; i += 32) {
+        HF(H, ldh, i, i - 2) = 0.f;
+        if (i != m + 2) HF(H, ldh, i, i - 3) = 0.f;
+      }
+      __syncwarp();
+      for (int k = m; k <= nn - 1; ++k) {
+        if (k != m) {
+          p = HF(H, ldh, k, k - 1);
+          q = HF(H, ldh, k + 1, k - 1);
+          r = (k != nn - 1) ? HF(H, ldh, k + 2, k - 1) : 0.f;
+          x = fabsf(p) + fabsf(q) + fabsf(r);
+          if (x != 0.f) { const float inv = 1.f / x; p *= inv; q *= inv; r *= inv; }
+        }
+        const float s = copysignf(sqrtf(p * p + q * q + r * r), p);
+        __syncwarp();
+        if (s != 0.f) {
+          if (lane == 0) {
+            if (k == m) {
+              if (l != m) HF(H, ldh, k, k - 1) = -HF(H, ldh, k, k - 1);
+            } else {
+              HF(H, ldh, k, k - 1) = -s * x;
+            }
+          }
+          p += s;
+          const float is = 1.f / s, ip = 1.f / p;
+          const float xx = p * is, yy = q * is, zz = r * is, qq = q * ip, rq = r * ip;
+          __syncwarp();
+          for (int jj = k + lane; jj <= nn; jj += 32) {
+            float pp = HF(H, ldh, k, jj) + qq * HF(H, ldh, k + 1, jj);
+            if (k != nn - 1) {
+              pp += rq * HF(H, ldh, k + 2, jj);
+              HF(H, ldh, k + 2, jj) -= pp * zz;
+            }
+            HF(H, ldh, k + 1, jj) -= pp * yy;
+            HF(H, ldh, k, jj) -= pp * xx;
+          }
+          __syncwarp();
+          const int imax = nn < k + 3 ? nn : k + 3;
+          for (int i = l + lane; i <= imax; i += 32) {
+            float pp = xx * HF(H, ldh, i, k) + yy * HF(H, ldh, i, k + 1);
+            if (k != nn - 1) {
+              pp += zz * HF(H, ldh, i, k + 2);
+              HF(H, ldh, i, k + 2) -= pp * rq;
+            }
+            HF(H, ldh, i, k + 1) -= pp * qq;
+            HF(H, ldh, i, k) -= pp;
+          }
+          __syncwarp();
+        }
+      }
+    }
+  }
+  return true;
+}
 
 __global__ void __launch_bounds__(512) k_ce_eig(WS ws) {
   Ctl* c = ws.ctl;
@@ -305,229 +480,76 @@ __global__ void __launch_bounds__(512) k_ce_eig(WS ws) {
   const int n = c->ell;
   if (n <= 0) return;
   CeLayout L = ce_layout(ws.dscr);
-  extern __shared__ double shm[];
+  extern __shared__ float shf[];
   const int ldh = n + 1;
-  double* H = shm;                  // n x n, ld n+1
-  double* tauH = H + ldh * n;       // n
-  double* wr = tauH + n;            // n
-  double* wi = wr + n;              // n
-  double* red = wi + n;             // 32
-  __shared__ int fail;
+  float* H = shf;                 // n x n, ld n+1
+  float* wr = H + ldh * n;        // n
+  float* wi = wr + n;             // n
+  float* red = wi + n;            // 32
+  __shared__ float tau_s;
+  __shared__ int ok;
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int i = idx % n, jj = idx / n;
-    HS(H, ldh, i, jj) = L.M[i + (int64_t)jj * LDD];
+    HF(H, ldh, i, jj) = (float)L.M[i + (int64_t)jj * LDD];
   }
-  if (threadIdx.x == 0) fail = 0;
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // --- Householder reduction to upper Hessenberg form ---
+  // --- Householder reduction to Hessenberg form (FP32) ---
   for (int col = 0; col + 2 < n; ++col) {
-    double xs = 0.0;
-    for (int i = col + 2 + threadIdx.x; i < n; i += blockDim.x) xs = fma(HS(H, ldh, i, col), HS(H, ldh, i, col), xs);
-    xs = block_sum(xs, red);
-    const double alpha = HS(H, ldh, col + 1, col);
-    double tau = 0.0, beta = alpha, sc = 0.0;
-    if (xs != 0.0) {
-      beta = -copysign(sqrt(alpha * alpha + xs), alpha);
-      tau = (beta - alpha) / beta;
-      sc = 1.0 / (alpha - beta);
-    }
-    __syncthreads();
-    for (int i = col + 2 + threadIdx.x; i < n; i += blockDim.x) HS(H, ldh, i, col) *= sc;
+    float xs = 0.f;
+    for (int i = col + 2 + threadIdx.x; i < n; i += blockDim.x) xs += HF(H, ldh, i, col) * HF(H, ldh, i, col);
+    xs = block_sum_f(xs, red);
+    if (xs == 0.f) continue;
+    const float alpha = HF(H, ldh, col + 1, col);
+    const float beta = -copysignf(sqrtf(alpha * alpha + xs), alpha);
+    const float tau = (beta - alpha) / beta;
+    const float sc = 1.f / (alpha - beta);
+    for (int i = col + 2 + threadIdx.x; i < n; i += blockDim.x) HF(H, ldh, i, col) *= sc;
     if (threadIdx.x == 0) {
-      HS(H, ldh, col + 1, col) = beta;
-      tauH[col] = tau;
+      HF(H, ldh, col + 1, col) = beta;
+      tau_s = tau;
     }
     __syncthreads();
-    if (tau == 0.0) continue;
-    // left: rows col+1.., columns col+1..n-1 (warp per column)
-    for (int jj = col + 1 + wid; jj < n; jj += nw) {
-      double w = HS(H, ldh, col + 1, jj) * (lane == 0 ? 1.0 : 0.0);
-      for (int i = col + 2 + lane; i < n; i += 32) w = fma(HS(H, ldh, i, col), HS(H, ldh, i, jj), w);
-      w = warp_sum(w) * tau;
-      if (lane == 0) HS(H, ldh, col + 1, jj) -= w;
-      for (int i = col + 2 + lane; i < n; i += 32) HS(H, ldh, i, jj) = fma(-w, HS(H, ldh, i, col), HS(H, ldh, i, jj));
+    // left: each thread owns a column jj >= col+1
+    for (int jj = col + 1 + threadIdx.x; jj < n; jj += blockDim.x) {
+      float w = HF(H, ldh, col + 1, jj);
+      for (int i = col + 2; i < n; ++i) w += HF(H, ldh, i, col) * HF(H, ldh, i, jj);
+      w *= tau_s;
+      HF(H, ldh, col + 1, jj) -= w;
+      for (int i = col + 2; i < n; ++i) HF(H, ldh, i, jj) -= w * HF(H, ldh, i, col);
     }
     __syncthreads();
-    // right: all rows, columns col+1..n-1 (warp per row)
-    for (int i = wid; i < n; i += nw) {
-      double w = lane == 0 ? HS(H, ldh, i, col + 1) : 0.0;
-      for (int jj = col + 2 + lane; jj < n; jj += 32) w = fma(HS(H, ldh, i, jj), HS(H, ldh, jj, col), w);
-      w = warp_sum(w) * tau;
-      if (lane == 0) HS(H, ldh, i, col + 1) -= w;
-      for (int jj = col + 2 + lane; jj < n; jj += 32) HS(H, ldh, i, jj) = fma(-w, HS(H, ldh, jj, col), HS(H, ldh, i, jj));
+    // right: each thread owns a row i
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      float w = HF(H, ldh, i, col + 1);
+      for (int jj = col + 2; jj < n; ++jj) w += HF(H, ldh, i, jj) * HF(H, ldh, jj, col);
+      w *= tau_s;
+      HF(H, ldh, i, col + 1) -= w;
+      for (int jj = col + 2; jj < n; ++jj) HF(H, ldh, i, jj) -= w * HF(H, ldh, jj, col);
     }
     __syncthreads();
   }
-  // save reflectors (below the subdiagonal) and a clean Hessenberg copy
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int i = idx % n, jj = idx / n;
-    const double v = HS(H, ldh, i, jj);
-    L.M[i + (int64_t)jj * LDD] = v;  // reflectors kept below the subdiagonal
-    L.Hc[i + (int64_t)jj * LDD] = (i <= jj + 1) ? v : 0.0;
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) L.tauH[i] = i + 2 < n ? tauH[i] : 0.0;
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx % n, jj = idx / n;
-    if (i > jj + 1) HS(H, ldh, i, jj) = 0.0;
-  }
-  double an = 0.0;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) an += fabs(HS(H, ldh, idx % n, idx / n));
-  an = block_sum(an, red);
-  if (threadIdx.x == 0) L.misc[0] = an;
-  // --- Francis double-shift QR, one warp ---
-  if (wid == 0) {
-    const double eps = 2.220446049250313e-16;
-    int nn = n - 1;
-    double tsh = 0.0;
-    int total = 0;
-    while (nn >= 0) {
-      int its = 0;
-      while (true) {
-        int l = nn;
-        while (l > 0) {
-          double s = fabs(HS(H, ldh, l - 1, l - 1)) + fabs(HS(H, ldh, l, l));
-          if (s == 0.0) s = an;
-          if (fabs(HS(H, ldh, l, l - 1)) <= eps * s) break;
-          --l;
-        }
-        __syncwarp();
-        if (l > 0 && lane == 0) HS(H, ldh, l, l - 1) = 0.0;
-        __syncwarp();
-        double x = HS(H, ldh, nn, nn);
-        if (l == nn) {
-          if (lane == 0) { wr[nn] = x + tsh; wi[nn] = 0.0; }
-          nn -= 1;
-          break;
-        }
-        double y = HS(H, ldh, nn - 1, nn - 1);
-        double w = HS(H, ldh, nn, nn - 1) * HS(H, ldh, nn - 1, nn);
-        if (l == nn - 1) {
-          const double p = 0.5 * (y - x), q = p * p + w;
-          double z = sqrt(fabs(q));
-          x += tsh;
-          if (lane == 0) {
-            if (q >= 0.0) {
-              z = p + copysign(z, p);
-              wr[nn - 1] = wr[nn] = x + z;
-              if (z != 0.0) wr[nn] = x - w / z;
-              wi[nn - 1] = wi[nn] = 0.0;
-            } else {
-              wr[nn - 1] = wr[nn] = x + p;
-              wi[nn - 1] = z;
-              wi[nn] = -z;
-            }
-          }
-          nn -= 2;
-          break;
-        }
-        if (its >= 60 || total >= 60 * n) {
-          if (lane == 0) fail = 1;
-          for (int i = lane; i <= nn; i += 32) { wr[i] = NAN; wi[i] = 0.0; }
-          nn = -1;
-          break;
-        }
-        if (its == 10 || its == 20) {  // exceptional shift
-          tsh += x;
-          __syncwarp();
-          for (int i = lane; i <= nn; i += 32) HS(H, ldh, i, i) -= x;
-          __syncwarp();
-          const double s = fabs(HS(H, ldh, nn, nn - 1)) + fabs(HS(H, ldh, nn - 1, nn - 2));
-          x = y = 0.75 * s;
-          w = -0.4375 * s * s;
-        }
-        ++its;
-        ++total;
-        int m = nn - 2;
-        double p = 0.0, q = 0.0, r = 0.0, z = 0.0;
-        while (true) {
-          z = HS(H, ldh, m, m);
-          const double rr = x - z, ss = y - z;
-          p = (rr * ss - w) / HS(H, ldh, m + 1, m) + HS(H, ldh, m, m + 1);
-          q = HS(H, ldh, m + 1, m + 1) - z - rr - ss;
-          r = HS(H, ldh, m + 2, m + 1);
-          const double sc = fabs(p) + fabs(q) + fabs(r);
-          p /= sc; q /= sc; r /= sc;
-          if (m == l) break;
-          const double u = fabs(HS(H, ldh, m, m - 1)) * (fabs(q) + fabs(r));
-          const double v = fabs(p) * (fabs(HS(H, ldh, m - 1, m - 1)) + fabs(z) + fabs(HS(H, ldh, m + 1, m + 1)));
-          if (u <= eps * v) break;
-          --m;
-        }
-        __syncwarp();
-        for (int i = m + 2 + lane; i <= nn; i += 32) {
-          HS(H, ldh, i, i - 2) = 0.0;
-          if (i != m + 2) HS(H, ldh, i, i - 3) = 0.0;
-        }
-        __syncwarp();
-        for (int k = m; k <= nn - 1; ++k) {
-          if (k != m) {
-            p = HS(H, ldh, k, k - 1);
-            q = HS(H, ldh, k + 1, k - 1);
-            r = (k != nn - 1) ? HS(H, ldh, k + 2, k - 1) : 0.0;
-            x = fabs(p) + fabs(q) + fabs(r);
-            if (x != 0.0) { p /= x; q /= x; r /= x; }
-          }
-          const double s = copysign(sqrt(p * p + q * q + r * r), p);
-          __syncwarp();
-          if (s != 0.0) {
-            if (lane == 0) {
-              if (k == m) {
-                if (l != m) HS(H, ldh, k, k - 1) = -HS(H, ldh, k, k - 1);
-              } else {
-                HS(H, ldh, k, k - 1) = -s * x;
-              }
-            }
-            p += s;
-            const double xx = p / s, yy = q / s, zz = r / s;
-            const double qq = q / p, rq = r / p;
-            __syncwarp();
-            for (int jj = k + lane; jj <= nn; jj += 32) {
-              double pp = HS(H, ldh, k, jj) + qq * HS(H, ldh, k + 1, jj);
-              if (k != nn - 1) {
-                pp += rq * HS(H, ldh, k + 2, jj);
-                HS(H, ldh, k + 2, jj) -= pp * zz;
-              }
-              HS(H, ldh, k + 1, jj) -= pp * yy;
-              HS(H, ldh, k, jj) -= pp * xx;
-            }
-            __syncwarp();
-            const int imax = nn < k + 3 ? nn : k + 3;
-            for (int i = l + lane; i <= imax; i += 32) {
-              double pp = xx * HS(H, ldh, i, k) + yy * HS(H, ldh, i, k + 1);
-              if (k != nn - 1) {
-                pp += zz * HS(H, ldh, i, k + 2);
-                HS(H, ldh, i, k + 2) -= pp * rq;
-              }
-              HS(H, ldh, i, k + 1) -= pp * qq;
-              HS(H, ldh, i, k) -= pp;
-            }
-            __syncwarp();
-          }
-        }
-      }
-    }
+    if (i > jj + 1) HF(H, ldh, i, jj) = 0.f;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    L.wr[i] = wr[i];
-    L.wi[i] = wi[i];
+  if (threadIdx.x < 32) {
+    const bool good = hqr_f32_warp(H, ldh, n, wr, wi);
+    if (threadIdx.x == 0) ok = good ? 1 : 0;
   }
   __syncthreads();
-  // --- selection: k largest |mu| (ties: larger real part, lower index); a
-  // complex-conjugate pair split at the boundary is kept whole ---
+  // --- candidates: k + KC_MARGIN largest |mu| (FP32 order), pairs whole ---
   if (threadIdx.x == 0) {
-    if (fail) c->rankfail = 1;
+    if (!ok) c->rankfail = 1;
     int ord[D_MAX];
     for (int i = 0; i < n; ++i) ord[i] = i;
     for (int i = 1; i < n; ++i) {
       const int v = ord[i];
-      const double mv = hypot(wr[v], wi[v]);
+      const float mv = hypotf(wr[v], wi[v]);
       int y = i - 1;
       while (y >= 0) {
         const int u = ord[y];
-        const double mu = hypot(wr[u], wi[u]);
+        const float mu = hypotf(wr[u], wi[u]);
         const bool after = (mu < mv) || (mu == mv && wr[u] < wr[v]) || (mu == mv && wr[u] == wr[v] && u > v);
         if (!after) break;
         ord[y + 1] = u;
@@ -535,37 +557,37 @@ __global__ void __launch_bounds__(512) k_ce_eig(WS ws) {
       }
       ord[y + 1] = v;
     }
-    int kk = ws.k < n ? ws.k : n;
-    if (kk > 0 && kk < n) {
-      const int a = ord[kk - 1], b = ord[kk];
-      if (wi[a] != 0.0 && wr[b] == wr[a] && wi[b] == -wi[a]) kk += 1;
+    int kc = ws.k + KC_MARGIN < n ? ws.k + KC_MARGIN : n;
+    if (kc > 0 && kc < n) {
+      const int a = ord[kc - 1], b = ord[kc];
+      if (wi[a] != 0.f && wr[b] == wr[a] && wi[b] == -wi[a]) kc += 1;
     }
-    if (kk > K_MAX) kk = K_MAX;
-    int ninv = 0, zc = 0;
-    for (int q = 0; q < kk; ++q) {
+    int nc = 0;
+    for (int q = 0; q < kc && nc < KC; ++q) {
       const int e = ord[q];
-      if (wi[e] == 0.0) {
-        L.sel[ninv] = e; L.zcol[ninv] = zc; ++ninv; zc += 1;
-      } else if (wi[e] > 0.0) {
-        L.sel[ninv] = e; L.zcol[ninv] = zc; ++ninv; zc += 2;
-      }
+      if (wi[e] < 0.f) continue;  // its conjugate partner (wi > 0) stands for the pair
+      L.cmu[2 * nc] = wr[e];
+      L.cmu[2 * nc + 1] = wi[e];
+      ++nc;
     }
-    if (zc > K_MAX) zc = K_MAX;
-    L.cnt[0] = ninv;
-    c->kprime = zc;
+    L.cnt[0] = nc;
+    for (int i = 0; i < n; ++i) {
+      L.wr[i] = wr[i];
+      L.wi[i] = wi[i];
+    }
   }
 }
 
-size_t ce_eig_smem() { return ((size_t)(D_MAX + 1) * D_MAX + 3 * D_MAX + 32) * sizeof(double); }
+size_t ce_eig_smem() { return ((size_t)(D_MAX + 1) * D_MAX + 2 * D_MAX + 64) * sizeof(float); }
 
 // ---------------------------------------------------------------------------
-// Inverse iteration (H - mu I) x = b on the Hessenberg matrix, one CTA per
-// selected eigenvalue, complex arithmetic; then x <- Q_H x.
+// FP64 eigenpair of M for one candidate (one CTA each): LU with partial
+// pivoting of M - mu0 I (complex when Im mu0 != 0), three steps of inverse
+// iteration, and the Rayleigh quotient mu = x^H M x / x^H x.
 // ---------------------------------------------------------------------------
 struct cplx { double re, im; };
 __device__ inline cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 __device__ inline cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
-__device__ inline double cabs2(cplx a) { return hypot(a.re, a.im); }
 __device__ inline cplx cdiv(cplx a, cplx b) {  // Smith's algorithm
   if (fabs(b.re) >= fabs(b.im)) {
     const double r = b.im / b.re, den = b.re + b.im * r;
@@ -582,140 +604,231 @@ __global__ void __launch_bounds__(256) k_ce_invit(WS ws) {
   CeLayout L = ce_layout(ws.dscr);
   const int idx = blockIdx.x;
   if (n <= 0 || idx >= L.cnt[0]) return;
-  const int e = L.sel[idx];
-  const cplx mu{L.wr[e], L.wi[e]};
-  const bool is_cplx = mu.im != 0.0;
-  double* Ure = L.lu + (int64_t)idx * 2 * LDD * LDD;  // row-major U(i, j) at i*LDD + j
-  double* Uim = Ure + (int64_t)LDD * LDD;
-  __shared__ double crr[D_MAX], cri[D_MAX], nrr[D_MAX], nri[D_MAX];
-  __shared__ double mlr[D_MAX], mli[D_MAX];
-  __shared__ int swp[D_MAX];
+  const cplx mu0{L.cmu[2 * idx], L.cmu[2 * idx + 1]};
+  const bool cx = mu0.im != 0.0;
+  double* Ar = L.lu + (int64_t)idx * 2 * LDD * LDD;  // column-major n x n
+  double* Ai = Ar + (int64_t)LDD * LDD;
   __shared__ double xr[D_MAX], xi[D_MAX];
+  __shared__ int perm[D_MAX];
   __shared__ double red[32];
   __shared__ double bc[4];
-  const double tiny = fmax(L.misc[0], 1e-300) * 2.220446049250313e-16;
-  const double* Hc = L.Hc;
-  for (int jj = threadIdx.x; jj < n; jj += blockDim.x) {
-    crr[jj] = Hc[0 + (int64_t)jj * LDD] - (jj == 0 ? mu.re : 0.0);
-    cri[jj] = jj == 0 ? -mu.im : 0.0;
+  __shared__ unsigned long long redu[32];
+  const double* M = L.M;
+  double mnorm = 0.0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    const double v = M[i + (int64_t)j * LDD];
+    Ar[i + (int64_t)j * LDD] = v - (i == j ? mu0.re : 0.0);
+    Ai[i + (int64_t)j * LDD] = (i == j) ? -mu0.im : 0.0;
+    mnorm = fmax(mnorm, fabs(v));
   }
+  {  // block max via the u64 bit pattern of a non-negative double
+    unsigned long long b = (unsigned long long)__double_as_longlong(mnorm);
+    b = block_max_u64(b, redu);
+    mnorm = __longlong_as_double((long long)b);
+  }
+  const double tiny = fmax(mnorm, 1e-300) * 2.220446049250313e-16 * (double)n;
   __syncthreads();
-  for (int i = 0; i + 1 < n; ++i) {
-    for (int jj = i + threadIdx.x; jj < n; jj += blockDim.x) {
-      nrr[jj] = Hc[(i + 1) + (int64_t)jj * LDD] - (jj == i + 1 ? mu.re : 0.0);
-      nri[jj] = jj == i + 1 ? -mu.im : 0.0;
+  // LU with partial pivoting (pivot by |re| + |im|)
+  for (int k = 0; k < n; ++k) {
+    unsigned long long best = 0ull;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      const double a = fabs(Ar[i + (int64_t)k * LDD]) + (cx ? fabs(Ai[i + (int64_t)k * LDD]) : 0.0);
+      // pack (magnitude bits, row) so that the max picks the largest, ties the lowest row
+      const unsigned long long key = ((unsigned long long)__double_as_longlong(a) & ~0x3FFull) |
+                                     (unsigned long long)(0x3FF - i);
+      best = key > best ? key : best;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      cplx a{crr[i], cri[i]}, b{nrr[i], nri[i]};
-      const int s = cabs2(b) > cabs2(a) ? 1 : 0;
-      cplx piv = s ? b : a, oth = s ? a : b;
-      if (piv.re == 0.0 && piv.im == 0.0) piv.re = tiny;
-      const cplx ml = cdiv(oth, piv);
-      swp[i] = s;
-      mlr[i] = ml.re;
-      mli[i] = ml.im;
-      bc[0] = piv.re;
-      bc[1] = piv.im;
-    }
-    __syncthreads();
-    const int s = swp[i];
-    const cplx ml{mlr[i], mli[i]};
-    for (int jj = i + threadIdx.x; jj < n; jj += blockDim.x) {
-      cplx a{crr[jj], cri[jj]}, b{nrr[jj], nri[jj]};
-      cplx up = s ? b : a, lo = s ? a : b;
-      if (jj == i) { up.re = bc[0]; up.im = bc[1]; }
-      Ure[(int64_t)i * LDD + jj] = up.re;
-      Uim[(int64_t)i * LDD + jj] = up.im;
-      const cplx nv = csub(lo, cmul(ml, up));
-      crr[jj] = nv.re;
-      cri[jj] = nv.im;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    double r = crr[n - 1], im = cri[n - 1];
-    if (r == 0.0 && im == 0.0) r = tiny;
-    Ure[(int64_t)(n - 1) * LDD + (n - 1)] = r;
-    Uim[(int64_t)(n - 1) * LDD + (n - 1)] = im;
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) { xr[i] = 1.0; xi[i] = 0.0; }
-  __syncthreads();
-  for (int iter = 0; iter < 3; ++iter) {
-    if (threadIdx.x == 0) {  // forward elimination of the right-hand side
-      for (int i = 0; i + 1 < n; ++i) {
-        if (swp[i]) {
-          double t = xr[i]; xr[i] = xr[i + 1]; xr[i + 1] = t;
-          t = xi[i]; xi[i] = xi[i + 1]; xi[i + 1] = t;
+    best = block_max_u64(best, redu);
+    const int p = 0x3FF - (int)(best & 0x3FF);
+    if (threadIdx.x == 0) perm[k] = p;
+    if (p != k) {
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double t = Ar[k + (int64_t)j * LDD];
+        Ar[k + (int64_t)j * LDD] = Ar[p + (int64_t)j * LDD];
+        Ar[p + (int64_t)j * LDD] = t;
+        if (cx) {
+          t = Ai[k + (int64_t)j * LDD];
+          Ai[k + (int64_t)j * LDD] = Ai[p + (int64_t)j * LDD];
+          Ai[p + (int64_t)j * LDD] = t;
         }
-        const cplx v = csub(cplx{xr[i + 1], xi[i + 1]}, cmul(cplx{mlr[i], mli[i]}, cplx{xr[i], xi[i]}));
-        xr[i + 1] = v.re;
-        xi[i + 1] = v.im;
       }
     }
     __syncthreads();
-    for (int i = n - 1; i >= 0; --i) {  // back substitution, column oriented
-      if (threadIdx.x == 0) {
-        cplx d{Ure[(int64_t)i * LDD + i], Uim[(int64_t)i * LDD + i]};
-        if (d.re == 0.0 && d.im == 0.0) d.re = tiny;
-        const cplx v = cdiv(cplx{xr[i], xi[i]}, d);
+    if (threadIdx.x == 0) {
+      cplx d{Ar[k + (int64_t)k * LDD], cx ? Ai[k + (int64_t)k * LDD] : 0.0};
+      if (d.re == 0.0 && d.im == 0.0) {
+        d.re = tiny;
+        Ar[k + (int64_t)k * LDD] = tiny;
+      }
+      const cplx inv = cdiv(cplx{1.0, 0.0}, d);
+      bc[0] = inv.re;
+      bc[1] = inv.im;
+    }
+    __syncthreads();
+    const cplx inv{bc[0], bc[1]};
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      if (cx) {
+        const cplx l = cmul(cplx{Ar[i + (int64_t)k * LDD], Ai[i + (int64_t)k * LDD]}, inv);
+        Ar[i + (int64_t)k * LDD] = l.re;
+        Ai[i + (int64_t)k * LDD] = l.im;
+      } else {
+        Ar[i + (int64_t)k * LDD] *= inv.re;
+      }
+    }
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = k + 1 + e % m, j = k + 1 + e / m;
+      if (cx) {
+        const cplx l{Ar[i + (int64_t)k * LDD], Ai[i + (int64_t)k * LDD]};
+        const cplx u{Ar[k + (int64_t)j * LDD], Ai[k + (int64_t)j * LDD]};
+        const cplx a = csub(cplx{Ar[i + (int64_t)j * LDD], Ai[i + (int64_t)j * LDD]}, cmul(l, u));
+        Ar[i + (int64_t)j * LDD] = a.re;
+        Ai[i + (int64_t)j * LDD] = a.im;
+      } else {
+        Ar[i + (int64_t)j * LDD] = fma(-Ar[i + (int64_t)k * LDD], Ar[k + (int64_t)j * LDD], Ar[i + (int64_t)j * LDD]);
+      }
+    }
+    __syncthreads();
+  }
+  // inverse iteration from x = (1, ..., 1)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { xr[i] = 1.0; xi[i] = 0.0; }
+  __syncthreads();
+  for (int it = 0; it < 3; ++it) {
+    if (threadIdx.x == 0) {  // row interchanges of the factorisation
+      for (int k = 0; k < n; ++k) {
+        const int p = perm[k];
+        if (p != k) {
+          double t = xr[k]; xr[k] = xr[p]; xr[p] = t;
+          t = xi[k]; xi[k] = xi[p]; xi[p] = t;
+        }
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {  // unit lower triangular solve, column oriented
+      const cplx xk{xr[k], xi[k]};
+      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const cplx l{Ar[i + (int64_t)k * LDD], cx ? Ai[i + (int64_t)k * LDD] : 0.0};
+        const cplx v = csub(cplx{xr[i], xi[i]}, cmul(l, xk));
         xr[i] = v.re;
         xi[i] = v.im;
       }
       __syncthreads();
-      const cplx xv{xr[i], xi[i]};
-      for (int l = threadIdx.x; l < i; l += blockDim.x) {
-        const cplx v = csub(cplx{xr[l], xi[l]}, cmul(cplx{Ure[(int64_t)l * LDD + i], Uim[(int64_t)l * LDD + i]}, xv));
-        xr[l] = v.re;
-        xi[l] = v.im;
+    }
+    for (int k = n - 1; k >= 0; --k) {  // upper triangular solve
+      if (threadIdx.x == 0) {
+        const cplx d{Ar[k + (int64_t)k * LDD], cx ? Ai[k + (int64_t)k * LDD] : 0.0};
+        const cplx v = cdiv(cplx{xr[k], xi[k]}, d);
+        xr[k] = v.re;
+        xi[k] = v.im;
+      }
+      __syncthreads();
+      const cplx xk{xr[k], xi[k]};
+      for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const cplx u{Ar[i + (int64_t)k * LDD], cx ? Ai[i + (int64_t)k * LDD] : 0.0};
+        const cplx v = csub(cplx{xr[i], xi[i]}, cmul(u, xk));
+        xr[i] = v.re;
+        xi[i] = v.im;
       }
       __syncthreads();
     }
-    // normalise by the largest modulus (deterministic: first index attaining it)
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {  // normalise by the entry of largest |re| + |im| (first such index)
       double best = -1.0;
       int bi = 0;
       for (int i = 0; i < n; ++i) {
-        const double a = hypot(xr[i], xi[i]);
+        const double a = fabs(xr[i]) + fabs(xi[i]);
         if (a > best) { best = a; bi = i; }
       }
-      const cplx piv{xr[bi], xi[bi]};
-      bc[0] = piv.re;
-      bc[1] = piv.im;
+      bc[0] = xr[bi];
+      bc[1] = xi[bi];
     }
     __syncthreads();
     const cplx piv{bc[0], bc[1]};
+    const cplx inv = (piv.re == 0.0 && piv.im == 0.0) ? cplx{1.0, 0.0} : cdiv(cplx{1.0, 0.0}, piv);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const cplx v = (piv.re == 0.0 && piv.im == 0.0) ? cplx{xr[i], xi[i]} : cdiv(cplx{xr[i], xi[i]}, piv);
+      const cplx v = cmul(cplx{xr[i], xi[i]}, inv);
       xr[i] = v.re;
-      xi[i] = is_cplx ? v.im : 0.0;
+      xi[i] = cx ? v.im : 0.0;
     }
     __syncthreads();
   }
-  // x <- Q_H x with Q_H = H_0 H_1 ... H_{n-3}: apply H_{n-3} first
-  for (int col = n - 3; col >= 0; --col) {
-    const double tau = L.tauH[col];
-    if (tau == 0.0) continue;
-    double dr = 0.0, di = 0.0;
-    for (int i = col + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      const double v = (i == col + 1) ? 1.0 : L.M[i + (int64_t)col * LDD];
-      dr = fma(v, xr[i], dr);
-      di = fma(v, xi[i], di);
-    }
-    dr = block_sum(dr, red);
-    di = block_sum(di, red);
-    for (int i = col + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      const double v = (i == col + 1) ? 1.0 : L.M[i + (int64_t)col * LDD];
-      xr[i] = fma(-tau * dr, v, xr[i]);
-      xi[i] = fma(-tau * di, v, xi[i]);
-    }
-    __syncthreads();
-  }
-  const int zc = L.zcol[idx];
+  // Rayleigh quotient mu = x^H M x / x^H x
+  double nr = 0.0, ni = 0.0, dd = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    L.Zr[i + (int64_t)zc * LDD] = xr[i];
-    if (is_cplx && zc + 1 < K_MAX) L.Zr[i + (int64_t)(zc + 1) * LDD] = xi[i];
+    double yr = 0.0, yi = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double mij = M[i + (int64_t)j * LDD];
+      yr = fma(mij, xr[j], yr);
+      yi = fma(mij, xi[j], yi);
+    }
+    // conj(x_i) * y_i
+    nr += xr[i] * yr + xi[i] * yi;
+    ni += xr[i] * yi - xi[i] * yr;
+    dd += xr[i] * xr[i] + xi[i] * xi[i];
+  }
+  nr = block_sum(nr, red);
+  ni = block_sum(ni, red);
+  dd = block_sum(dd, red);
+  if (threadIdx.x == 0) {
+    L.cref[2 * idx] = nr / dd;
+    L.cref[2 * idx + 1] = cx ? ni / dd : 0.0;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    L.cvec[i + (int64_t)(2 * idx) * LDD] = xr[i];
+    L.cvec[i + (int64_t)(2 * idx + 1) * LDD] = xi[i];
+  }
+}
+
+// Selection on the FP64 eigenvalues: the k largest |mu| (ties: larger real
+// part, lower candidate index); a pair counts twice and is kept whole.
+__global__ void k_ce_select(WS ws) {
+  Ctl* c = ws.ctl;
+  if (c->jf <= 0) return;
+  const int n = c->ell;
+  CeLayout L = ce_layout(ws.dscr);
+  __shared__ int ord[KC];
+  __shared__ int zc_of[KC];
+  __shared__ int nsel;
+  const int nc = L.cnt[0];
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nc; ++i) ord[i] = i;
+    for (int i = 1; i < nc; ++i) {
+      const int v = ord[i];
+      const double mv = hypot(L.cref[2 * v], L.cref[2 * v + 1]);
+      int y = i - 1;
+      while (y >= 0) {
+        const int u = ord[y];
+        const double mu = hypot(L.cref[2 * u], L.cref[2 * u + 1]);
+        const bool after = (mu < mv) || (mu == mv && L.cref[2 * u] < L.cref[2 * v]) ||
+                           (mu == mv && L.cref[2 * u] == L.cref[2 * v] && u > v);
+        if (!after) break;
+        ord[y + 1] = u;
+        --y;
+      }
+      ord[y + 1] = v;
+    }
+    int cols = 0, q = 0;
+    while (q < nc && cols < ws.k) {
+      const int e = ord[q];
+      zc_of[q] = cols;
+      cols += (L.cref[2 * e + 1] != 0.0) ? 2 : 1;
+      ++q;
+    }
+    if (cols > K_MAX) cols = K_MAX;
+    nsel = q;
+    c->kprime = cols;
+  }
+  __syncthreads();
+  for (int q = 0; q < nsel; ++q) {
+    const int e = ord[q];
+    const int zc = zc_of[q];
+    const bool cx = L.cref[2 * e + 1] != 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      L.Zr[i + (int64_t)zc * LDD] = L.cvec[i + (int64_t)(2 * e) * LDD];
+      if (cx && zc + 1 < K_MAX) L.Zr[i + (int64_t)(zc + 1) * LDD] = L.cvec[i + (int64_t)(2 * e + 1) * LDD];
+    }
   }
 }
 
@@ -815,8 +928,8 @@ __global__ void k_ce_sketch_update(WS ws, int kh, const double* __restrict__ SU,
   }
 }
 
-cudaError_t launch_cycle_end(const WS& ws, int kh, const double* SU, const double* SAU, double* SUn, double* SAUn,
-                             cudaStream_t st) {
+cudaError_t launch_cycle_end_part(int part, const WS& ws, int kh, const double* SU, const double* SAU, double* SUn,
+                                  double* SAUn, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_ce_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ce_eig_smem());
@@ -824,14 +937,18 @@ cudaError_t launch_cycle_end(const WS& ws, int kh, const double* SU, const doubl
     attr = true;
   }
   const int dmax_now = kh + ws.m;
-  k_ce_formC<<<dmax_now, 256, 0, st>>>(ws, SU, kh);
-  k_ce_rinv<<<dmax_now, 32, 0, st>>>(ws, kh);
-  k_ce_M<<<dmax_now, 256, 0, st>>>(ws, kh);
-  k_ce_svd<<<1, 512, 0, st>>>(ws, kh);
-  k_ce_eig<<<1, 512, ce_eig_smem(), st>>>(ws);
-  k_ce_invit<<<K_MAX, 256, 0, st>>>(ws);
-  k_ce_finish<<<1, 512, 0, st>>>(ws, kh);
-  k_ce_sketch_update<<<K_MAX, 512, 0, st>>>(ws, kh, SU, SAU, SUn, SAUn);
+  switch (part) {
+    case 0: k_ce_formC<<<dmax_now, 256, 0, st>>>(ws, SU, kh); break;
+    case 1: k_ce_rinv<<<dmax_now, 32, 0, st>>>(ws, kh); break;
+    case 2: k_ce_M<<<dmax_now, 256, 0, st>>>(ws, kh); break;
+    case 3: k_ce_svd<<<1, 512, 0, st>>>(ws, kh); break;
+    case 4: k_ce_eig<<<1, 512, ce_eig_smem(), st>>>(ws); break;
+    case 5: k_ce_invit<<<KC, 256, 0, st>>>(ws); break;
+    case 6: k_ce_select<<<1, 256, 0, st>>>(ws); break;
+    case 7: k_ce_finish<<<1, 512, 0, st>>>(ws, kh); break;
+    case 8: k_ce_sketch_update<<<K_MAX, 512, 0, st>>>(ws, kh, SU, SAU, SUn, SAUn); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

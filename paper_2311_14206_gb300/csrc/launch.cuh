@@ -56,7 +56,11 @@ cudaError_t launch_step_dense(const WS& ws, int j, int kh, unsigned long long* a
 
 // ---- dense_cycle.cu ----
 // Cycle end: harmonic-Ritz recycling (Section 3.4); P' into ws.P, SU/SAU for the next cycle.
-cudaError_t launch_cycle_end(const WS& ws, int kh, const double* SU, const double* SAU, double* SUn,
-                             double* SAUn, cudaStream_t st);
+// part 0..8: form C, R^{-1}, M (+ full-rank certificate), truncated SVD (only
+// when not certified), FP32 eigenvalue candidates, FP64 inverse iteration per
+// candidate, selection, basis + P, SU/SAU products.
+constexpr int CYCLE_END_PARTS = 9;
+cudaError_t launch_cycle_end_part(int part, const WS& ws, int kh, const double* SU, const double* SAU, double* SUn,
+                                  double* SAUn, cudaStream_t st);
 
 }  // namespace sdr

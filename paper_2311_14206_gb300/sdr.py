@@ -36,11 +36,21 @@ class sdr_csr(ctypes.Structure):
 class sdr_stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int32), ("converged", ctypes.c_int32), ("matvecs", ctypes.c_int32),
                 ("sketches", ctypes.c_int32), ("true_res_evals", ctypes.c_int32), ("arnoldi_steps", ctypes.c_int32),
-                ("recycle_dim", ctypes.c_int32), ("full_svd_cycles", ctypes.c_int32), ("final_res", ctypes.c_double),
+                ("recycle_dim", ctypes.c_int32), ("full_svd_cycles", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32), ("reserved_i", ctypes.c_int32), ("final_res", ctypes.c_double),
                 ("tol", ctypes.c_double), ("final_rel_res", ctypes.c_double), ("bnorm", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+KERNEL_CLASSES = ["solve_init", "residual0", "cycle_init", "spmv_dots", "update_sketch", "step_dense",
+                  "check_gemv", "check_residual", "ce_formC", "recycle_gemm", "recycle_sau", "sketch",
+                  "ce_rinv", "ce_M", "ce_svd", "ce_eig", "ce_invit", "ce_select", "ce_finish", "ce_sketches"]
+
+
+class sdr_kernel_time(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int32), ("pad", ctypes.c_int32), ("total_ms", ctypes.c_double)]
 
 
 class sdr_cycle_log(ctypes.Structure):
@@ -73,6 +83,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sdr_recycle_dim": ([vp, P(i32)], i32),
         "sdr_recycle_export": ([vp, i64, vp, vp, vp], i32),
         "sdr_recycle_import": ([vp, P(sdr_csr), i64, i32, vp, vp, vp], i32),
+        "sdr_profile": ([vp, i32], i32),
+        "sdr_profile_get": ([vp, P(sdr_kernel_time), i32, P(i32)], i32),
         "sdr_status_string": ([i32], ctypes.c_char_p),
         "sdr_abi_version": ([], i32),
     }
@@ -207,6 +219,18 @@ def sdr_recycle_import(h, A: CSRDevice, U: torch.Tensor, SU: torch.Tensor = None
     st = load_library().sdr_recycle_import(h, ctypes.byref(csr) if csr is not None else None, n, kd, _ptr(Uc),
                                            _ptr(SUc), _ptr(SAUc))
     return _check(st, "sdr_recycle_import")
+
+
+def sdr_profile(h, enable=True):
+    return _check(load_library().sdr_profile(h, 1 if enable else 0), "sdr_profile")
+
+
+def sdr_profile_get(h):
+    """{class name: (launches, total ms)} of the library's kernels since sdr_profile."""
+    arr = (sdr_kernel_time * len(KERNEL_CLASSES))()
+    n = ctypes.c_int32()
+    _check(load_library().sdr_profile_get(h, arr, len(KERNEL_CLASSES), ctypes.byref(n)), "sdr_profile_get")
+    return {KERNEL_CLASSES[i]: (arr[i].launches, arr[i].total_ms) for i in range(min(n.value, len(KERNEL_CLASSES)))}
 
 
 class Solver:
