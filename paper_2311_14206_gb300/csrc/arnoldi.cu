@@ -13,6 +13,7 @@
 // in the control block and is folded into every coefficient that touches a
 // column, which saves a normalisation pass per step.
 #include "launch.cuh"
+#include "eidot.cuh"
 
 namespace sdr {
 
@@ -148,13 +149,16 @@ __global__ void k_residual(WS ws, CsrDev A, const double* __restrict__ b, const 
   __shared__ double red[32];
   const double xm = __longlong_as_double((long long)c->xmax);
   const int top = window_top((c->bmax + c->anorm_inf * xm) * (1.0 + 1e-12), ws.win_bits);
-  unsigned long long lo = 0ull, hi = 0ull, rm = 0ull;
+  unsigned long long lo[SK_RPT], hi[SK_RPT], rm = 0ull;
+#pragma unroll
+  for (int k = 0; k < SK_RPT; ++k) lo[k] = hi[k] = 0ull;
   double nrm = 0.0;
   const int64_t n = A.n;
   const int ntiles = (int)((n + tileR - 1) / tileR);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = (int64_t)tile * tileR;
     const int ncols = (int)(n - r0 < (int64_t)tileR ? n - r0 : (int64_t)tileR);
+    tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
     for (int i = threadIdx.x; i < tileR; i += blockDim.x) {
       double v = 0.0;
       if (i < ncols) {
@@ -167,10 +171,13 @@ __global__ void k_residual(WS ws, CsrDev A, const double* __restrict__ b, const 
       }
       vals[i] = v;
     }
-    __syncthreads();
-    tile_sketch_accumulate(ws, tileR, tile, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
+    tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
   }
-  if (threadIdx.x < ws.s) atomic_add128(accR + 2 * threadIdx.x, lo, hi);
+#pragma unroll
+  for (int k = 0; k < SK_RPT; ++k) {
+    const int row = threadIdx.x + k * blockDim.x;
+    if (row < ws.s) atomic_add128(accR + 2 * row, lo[k], hi[k]);
+  }
   nrm = block_sum(nrm, red);
   rm = block_max_u64(rm, redu);
   if (threadIdx.x == 0) {
@@ -219,7 +226,8 @@ static cudaError_t set_smem(const void* f, size_t sm, bool& done) {
 static int grid_tiles(const WS& ws, int64_t n) {
   int tileR = sketch_tile_rows(ws.zeta);
   int ntiles = (int)((n + tileR - 1) / tileR);
-  int g = ntiles < ws.grid_max ? ntiles : ws.grid_max;
+  const int gmax = ws.grid_max / 2;  // four CTAs per SM
+  int g = ntiles < gmax ? ntiles : gmax;
   return g < 1 ? 1 : g;
 }
 
@@ -229,92 +237,59 @@ cudaError_t launch_residual(const WS& ws, CsrDev A, const double* b, const doubl
   static bool attr = false;
   cudaError_t e = set_smem((const void*)k_residual, sketch_smem_bytes(ZETA_MAX), attr);
   if (e != cudaSuccess) return e;
-  k_residual<<<grid_tiles(ws, A.n), 512, sm, st>>>(ws, A, b, x, rout, accR, j, mode);
+  k_residual<<<grid_tiles(ws, A.n), SK_THREADS, sm, st>>>(ws, A, b, x, rout, accR, j, mode);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Arnoldi step j, part 1: w = A v_hat_j, dots with the window, MGS coefficients.
+// Column j of the basis is finished by the first kernel that runs after the
+// update which produced it: h(j, j-1) = ||v_hat_j||, alpha_j = 1/h, the window
+// dots v_hat_j . v_hat_{j-1-d} and max |v_hat_j| are reduced from the update's
+// per-CTA partials (fixed order).  Runs in one CTA.
 // ---------------------------------------------------------------------------
-__global__ void k_spmv_dots(WS ws, CsrDev A, Win win, int j) {
+__device__ void finish_column(const WS& ws, int j, int grid2, double* buf, unsigned long long* redu) {
   Ctl* c = ws.ctl;
-  if (c->done) return;
-  __shared__ double red[32];
-  __shared__ unsigned long long redu[32];
-  const double* __restrict__ x = win.v[win.nw - 1];
-  double* __restrict__ w = ws.Wv;
-  double d[T_MAX] = {0.0, 0.0, 0.0, 0.0};
-  unsigned long long wm = 0ull;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.n; r += (int64_t)gridDim.x * blockDim.x) {
-    double y = csr_row_dot(A.rowptr, A.col, A.val, x, r);
-    w[r] = y;
+  const int t = ws.t;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < grid2; b += blockDim.x) v += ws.part2[b * NPART + 0];
+  const double nrm = block_sum_lean(v, buf);
+  double cross[T_MAX - 1];
 #pragma unroll
-    for (int a = 0; a < T_MAX; ++a)
-      if (a < win.nw) d[a] = fma(win.v[a][r], y, d[a]);
-    unsigned long long u = abs_bits(y);
-    wm = u > wm ? u : wm;
-  }
-#pragma unroll
-  for (int a = 0; a < T_MAX; ++a)
-    if (a < win.nw) d[a] = block_sum(d[a], red);
-  wm = block_max_u64(wm, redu);
-  if (threadIdx.x == 0) {
-    double* pp = ws.part + blockIdx.x * NPART;
-    for (int a = 0; a < win.nw; ++a) pp[a] = d[a];
-    pp[T_MAX] = __longlong_as_double((long long)wm);
-  }
-  if (last_block(&c->counter)) {
-    double p[T_MAX];
-#pragma unroll
-    for (int a = 0; a < T_MAX; ++a) p[a] = a < win.nw ? reduce_parts(ws.part, gridDim.x, a, red) : 0.0;
-    unsigned long long wmx = reduce_parts_max(ws.part, gridDim.x, T_MAX, redu);
-    if (threadIdx.x == 0) {
-      // Truncated MGS (Algorithm 1, inner loop) from the dots: with
-      // v_i = alpha_i v_hat_i and w_true = alpha_j w,
-      // H(i,j) = v_i . (w_true - sum_{l<i} H(l,j) v_l).
-      const int t = ws.t;
-      const double aj = c->alpha[j];
-      double h[T_MAX];
-      for (int a = 0; a < win.nw; ++a) {
-        const int i = win.lo + a;
-        const double ai = c->alpha[i];
-        double v = ai * aj * p[a];
-        for (int b2 = 0; b2 < a; ++b2) {
-          const int l = win.lo + b2;
-          v -= h[b2] * ai * c->alpha[l] * c->gram[i][i - l - 1];
-        }
-        h[a] = v;
-        c->hband[j][i - j + t - 1] = v;
-      }
-      double bound = fabs(aj) * __longlong_as_double((long long)wmx);
-      c->coef[0] = aj;
-      for (int a = 0; a < win.nw; ++a) {
-        const int i = win.lo + a;
-        c->coef[1 + a] = h[a] * c->alpha[i];
-        bound += fabs(c->coef[1 + a]) * __longlong_as_double((long long)c->vmax[i]);
-      }
-      c->wmax = wmx;
-      c->acc_top = window_top(bound * (1.0 + 1e-12), ws.win_bits);
-      c->matvecs += 1;
+  for (int d = 0; d < T_MAX - 1; ++d) {
+    double cv = 0.0;
+    if (d < t - 1) {
+      for (int b = threadIdx.x; b < grid2; b += blockDim.x) cv += ws.part2[b * NPART + 1 + d];
+      cv = block_sum_lean(cv, buf);
     }
+    cross[d] = cv;
   }
-}
-
-cudaError_t launch_spmv_dots(const WS& ws, CsrDev A, const double* const* vcol, int j, cudaStream_t st) {
-  Win win;
-  win.lo = j - ws.t + 1 > 0 ? j - ws.t + 1 : 0;
-  win.nw = j - win.lo + 1;
-  for (int a = 0; a < T_MAX; ++a) win.v[a] = a < win.nw ? vcol[win.lo + a] : nullptr;
-  k_spmv_dots<<<grid_rows(A.n, 256, ws.grid_max), 256, 0, st>>>(ws, A, win, j);
-  return cudaGetLastError();
+  unsigned long long vm = 0ull;
+  for (int b = threadIdx.x; b < grid2; b += blockDim.x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(ws.part2[b * NPART + T_MAX]);
+    vm = u > vm ? u : vm;
+  }
+  vm = block_max_u64(vm, redu);
+  if (threadIdx.x == 0) {
+    const double h = sqrt(nrm);
+    const bool bd = !(h > 0.0) || !isfinite(h);
+    c->alpha[j] = bd ? 0.0 : 1.0 / h;
+    c->vmax[j] = vm;
+    for (int d = 0; d < t - 1; ++d) c->gram[j][d] = cross[d];
+    c->hband[j - 1][t] = bd ? 0.0 : h;  // H(j, j-1)
+    if (bd) c->breakdown = 1;
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
-// Arnoldi step j, part 2: v_hat_{j+1}, ||v_hat_{j+1}||^2, window dots for the
-// next step, and S v_hat_{j+1} into the 128-bit accumulators ws.acc.
-// Partials per CTA: [0] norm^2, [1..t-1] v_hat_{j+1}.v_hat_{j-d}, [T_MAX] max.
+// Arnoldi step j, part 1: w = A v_hat_j (one thread per row) with the dots of
+// w against the truncation window, and, for j >= 1, the sketch S v_hat_j of
+// the vector being multiplied (tile by tile, on the integer and load/store
+// pipes while the FP64 pipe runs the SpMV).  The last CTA finishes column j
+// and turns the dots into the MGS coefficients H(i, j).
 // ---------------------------------------------------------------------------
-__global__ void k_update_sketch(WS ws, Win win, double* __restrict__ vnext, int j) {
+template <int NW, bool SK>  // NW window vectors v_hat_lo .. v_hat_j; SK: sketch v_hat_j
+__global__ void __launch_bounds__(SK_THREADS) k_spmv_dots(WS ws, CsrDev A, Win win, int j, int grid2) {
   Ctl* c = ws.ctl;
   if (c->done) return;
   extern __shared__ unsigned char smem[];
@@ -322,103 +297,308 @@ __global__ void k_update_sketch(WS ws, Win win, double* __restrict__ vnext, int 
   double* vals = (double*)smem;
   uint16_t* ent_s = (uint16_t*)(vals + tileR);
   uint16_t* ptr_s = ent_s + tileR * ws.zeta;
+  __shared__ double buf[SK_THREADS];
   __shared__ unsigned long long redu[32];
-  __shared__ double red[32];
-  const int top = c->acc_top;
-  double cf[T_MAX + 1];
+  const double* __restrict__ x = win.v[NW - 1];
+  double* __restrict__ w = ws.Wv;
+  const int top = SK ? c->vtop[j] : 0;
+  double d[NW];
 #pragma unroll
-  for (int a = 0; a <= T_MAX; ++a) cf[a] = a <= win.nw ? c->coef[a] : 0.0;
-  const double* __restrict__ w = ws.Wv;
-  const int64_t n = ws.n;
-  double nrm = 0.0;
-  double cr[T_MAX] = {0.0, 0.0, 0.0, 0.0};  // cr[d] = v_hat_{j+1} . v_hat_{j-d}
-  unsigned long long vm = 0ull, lo = 0ull, hi = 0ull;
-  const int ncross = ws.t - 1;
+  for (int a = 0; a < NW; ++a) d[a] = 0.0;
+  unsigned long long wm = 0ull;
+  unsigned long long lo[SK_RPT], hi[SK_RPT];
+#pragma unroll
+  for (int k = 0; k < SK_RPT; ++k) lo[k] = hi[k] = 0ull;
+  const int32_t* __restrict__ rp = A.rowptr;
+  const int32_t* __restrict__ ci = A.col;
+  const double* __restrict__ va = A.val;
+  const int64_t n = A.n;
   const int ntiles = (int)((n + tileR - 1) / tileR);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = (int64_t)tile * tileR;
     const int ncols = (int)(n - r0 < (int64_t)tileR ? n - r0 : (int64_t)tileR);
+    if (SK) tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
     for (int i = threadIdx.x; i < tileR; i += blockDim.x) {
-      double v = 0.0;
+      double xv = 0.0;
       if (i < ncols) {
         const int64_t r = r0 + i;
-        double wv[T_MAX];
+        const double y = csr_row_dot(rp, ci, va, x, r);
+        w[r] = y;
 #pragma unroll
-        for (int a = 0; a < T_MAX; ++a) wv[a] = a < win.nw ? win.v[a][r] : 0.0;
-        v = cf[0] * w[r];
-#pragma unroll
-        for (int a = 0; a < T_MAX; ++a)
-          if (a < win.nw) v = fma(-cf[1 + a], wv[a], v);
-        vnext[r] = v;
-        nrm = fma(v, v, nrm);
-#pragma unroll
-        for (int d = 0; d < T_MAX; ++d)
-          if (d < ncross && d < win.nw) cr[d] = fma(v, wv[win.nw - 1 - d], cr[d]);
-        unsigned long long u = abs_bits(v);
-        vm = u > vm ? u : vm;
+        for (int a = 0; a < NW; ++a) d[a] = fma(win.v[a][r], y, d[a]);
+        const unsigned long long u = abs_bits(y);
+        wm = u > wm ? u : wm;
+        if (SK) xv = x[r];
       }
-      vals[i] = v;
+      if (SK) vals[i] = xv;
     }
-    __syncthreads();
-    tile_sketch_accumulate(ws, tileR, tile, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
+    if (SK) tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
   }
-  if (threadIdx.x < ws.s) atomic_add128(ws.acc + 2 * threadIdx.x, lo, hi);
-  nrm = block_sum(nrm, red);
+  if (SK) {
 #pragma unroll
-  for (int d = 0; d < T_MAX; ++d)
-    if (d < ncross) cr[d] = block_sum(cr[d], red);
-  vm = block_max_u64(vm, redu);
+    for (int k = 0; k < SK_RPT; ++k) {
+      const int row = threadIdx.x + k * blockDim.x;
+      if (row < ws.s) atomic_add128(ws.acc + 2 * row, lo[k], hi[k]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < NW; ++a) d[a] = block_sum_lean(d[a], buf);
+  wm = block_max_u64(wm, redu);
   if (threadIdx.x == 0) {
     double* pp = ws.part + blockIdx.x * NPART;
-    pp[0] = nrm;
-    for (int d = 0; d < ncross; ++d) pp[1 + d] = cr[d];
-    pp[T_MAX] = __longlong_as_double((long long)vm);
+#pragma unroll
+    for (int a = 0; a < NW; ++a) pp[a] = d[a];
+    pp[T_MAX] = __longlong_as_double((long long)wm);
+  }
+  if (last_block(&c->counter)) {
+    if (j >= 1) finish_column(ws, j, grid2, buf, redu);
+    double p[NW];
+#pragma unroll
+    for (int a = 0; a < NW; ++a) {
+      double v = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += ws.part[b * NPART + a];
+      p[a] = block_sum_lean(v, buf);
+    }
+    const unsigned long long wmx = reduce_parts_max(ws.part, gridDim.x, T_MAX, redu);
+    if (threadIdx.x == 0) {
+      // Truncated MGS (Algorithm 1, inner loop) from the dots: with
+      // v_i = alpha_i v_hat_i and w_true = alpha_j w,
+      // H(i,j) = v_i . (w_true - sum_{l<i} H(l,j) v_l).
+      const int t = ws.t;
+      const double aj = c->alpha[j];
+      double h[NW];
+      double bound = fabs(aj) * __longlong_as_double((long long)wmx);
+      c->coef[0] = aj;
+#pragma unroll
+      for (int a = 0; a < NW; ++a) {
+        const int i = win.lo + a;
+        const double ai = c->alpha[i];
+        double v = ai * aj * p[a];
+#pragma unroll
+        for (int b2 = 0; b2 < a; ++b2) {
+          const int l = win.lo + b2;
+          v -= h[b2] * ai * c->alpha[l] * c->gram[i][i - l - 1];
+        }
+        h[a] = v;
+        c->hband[j][i - j + t - 1] = v;
+        c->coef[1 + a] = v * ai;
+        bound += fabs(c->coef[1 + a]) * __longlong_as_double((long long)c->vmax[i]);
+      }
+      c->wmax = wmx;
+      c->vtop[j + 1] = window_top(bound * (1.0 + 1e-12), ws.win_bits);
+      c->matvecs += 1;
+      if (SK) c->sketches += 1;
+    }
   }
 }
 
-int update_grid(const WS& ws) { return grid_tiles(ws, ws.n); }
+int update_grid(const WS& ws) {
+  const int g = (ws.grid_max / 8) * 2;  // two CTAs per SM, many rows per thread
+  return g < 1 ? 1 : g;
+}
 
-cudaError_t launch_update_sketch(const WS& ws, const double* const* vcol, double* vnext, int j,
-                                 cudaStream_t st) {
+template <int NW, bool SK>
+static cudaError_t launch_spmv_t(const WS& ws, CsrDev A, const Win& win, int j, cudaStream_t st) {
+  static bool attr = false;
+  cudaError_t e = set_smem((const void*)k_spmv_dots<NW, SK>, sketch_smem_bytes(ZETA_MAX), attr);
+  if (e != cudaSuccess) return e;
+  const size_t sm = SK ? sketch_smem_bytes(ws.zeta) : 0;
+  k_spmv_dots<NW, SK><<<grid_tiles(ws, A.n), SK_THREADS, sm, st>>>(ws, A, win, j, update_grid(ws));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_dots(const WS& ws, CsrDev A, const double* const* vcol, int j, cudaStream_t st) {
   Win win;
   win.lo = j - ws.t + 1 > 0 ? j - ws.t + 1 : 0;
   win.nw = j - win.lo + 1;
   for (int a = 0; a < T_MAX; ++a) win.v[a] = a < win.nw ? vcol[win.lo + a] : nullptr;
-  size_t sm = sketch_smem_bytes(ws.zeta);
+  if (j == 0) return launch_spmv_t<1, false>(ws, A, win, j, st);  // S r0 came with r0
+  switch (win.nw) {
+    case 1: return launch_spmv_t<1, true>(ws, A, win, j, st);
+    case 2: return launch_spmv_t<2, true>(ws, A, win, j, st);
+    case 3: return launch_spmv_t<3, true>(ws, A, win, j, st);
+    default: return launch_spmv_t<4, true>(ws, A, win, j, st);
+  }
+}
+
+// S v_hat_j for the last column of a cycle (no SpMV follows it), with the
+// column's finish.
+__global__ void __launch_bounds__(SK_THREADS) k_sketch_col(WS ws, const double* __restrict__ x, int j, int grid2) {
+  Ctl* c = ws.ctl;
+  if (c->done) return;
+  extern __shared__ unsigned char smem[];
+  const int tileR = sketch_tile_rows(ws.zeta);
+  double* vals = (double*)smem;
+  uint16_t* ent_s = (uint16_t*)(vals + tileR);
+  uint16_t* ptr_s = ent_s + tileR * ws.zeta;
+  __shared__ double buf[SK_THREADS];
+  __shared__ unsigned long long redu[32];
+  const int top = c->vtop[j];
+  unsigned long long lo[SK_RPT], hi[SK_RPT];
+#pragma unroll
+  for (int k = 0; k < SK_RPT; ++k) lo[k] = hi[k] = 0ull;
+  const int64_t n = ws.n;
+  const int ntiles = (int)((n + tileR - 1) / tileR);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = (int64_t)tile * tileR;
+    const int ncols = (int)(n - r0 < (int64_t)tileR ? n - r0 : (int64_t)tileR);
+    tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
+    for (int i = threadIdx.x; i < tileR; i += blockDim.x) vals[i] = i < ncols ? x[r0 + i] : 0.0;
+    tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
+  }
+#pragma unroll
+  for (int k = 0; k < SK_RPT; ++k) {
+    const int row = threadIdx.x + k * blockDim.x;
+    if (row < ws.s) atomic_add128(ws.acc + 2 * row, lo[k], hi[k]);
+  }
+  if (last_block(&c->counter)) {
+    finish_column(ws, j, grid2, buf, redu);
+    if (threadIdx.x == 0) c->sketches += 1;
+  }
+}
+
+cudaError_t launch_sketch_col(const WS& ws, const double* x, int j, cudaStream_t st) {
   static bool attr = false;
-  cudaError_t e = set_smem((const void*)k_update_sketch, sketch_smem_bytes(ZETA_MAX), attr);
+  cudaError_t e = set_smem((const void*)k_sketch_col, sketch_smem_bytes(ZETA_MAX), attr);
   if (e != cudaSuccess) return e;
-  k_update_sketch<<<update_grid(ws), 512, sm, st>>>(ws, win, vnext, j);
+  k_sketch_col<<<grid_tiles(ws, ws.n), SK_THREADS, sketch_smem_bytes(ws.zeta), st>>>(ws, x, j, update_grid(ws));
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// x_trial = x + [U, V(:, 0:j+1)] y' with y'_U = y_tilde(0:kh), y'_V,c = y_tilde(kh+c) alpha_c.
+// Arnoldi step j, part 2: v_hat_{j+1} = a_0 w - sum_i a_i v_hat_i, with
+// ||v_hat_{j+1}||^2, its dots with the t-1 newest window vectors and its max
+// magnitude as per-CTA partials (part2).  Pure streaming: many rows per thread.
+// ---------------------------------------------------------------------------
+template <int NW, int NC>  // NW window vectors, NC = t - 1 dots kept for the next window
+__global__ void __launch_bounds__(256) k_update(WS ws, Win win, double* __restrict__ vnext, int j) {
+  Ctl* c = ws.ctl;
+  if (c->done) return;
+  __shared__ double buf[256];
+  __shared__ unsigned long long redu[32];
+  double cf[NW + 1];
+#pragma unroll
+  for (int a = 0; a <= NW; ++a) cf[a] = c->coef[a];
+  const double* __restrict__ w = ws.Wv;
+  double nrm = 0.0;
+  double cr[NC > 0 ? NC : 1];
+#pragma unroll
+  for (int q = 0; q < (NC > 0 ? NC : 1); ++q) cr[q] = 0.0;
+  unsigned long long vm = 0ull;
+  const int64_t n = ws.n, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+    double wv[NW];
+#pragma unroll
+    for (int a = 0; a < NW; ++a) wv[a] = win.v[a][r];
+    double v = cf[0] * w[r];
+#pragma unroll
+    for (int a = 0; a < NW; ++a) v = fma(-cf[1 + a], wv[a], v);
+    vnext[r] = v;
+    nrm = fma(v, v, nrm);
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+      if (q < NW) cr[q] = fma(v, wv[NW - 1 - q], cr[q]);
+    const unsigned long long u = abs_bits(v);
+    vm = u > vm ? u : vm;
+  }
+  nrm = block_sum_lean(nrm, buf);
+#pragma unroll
+  for (int q = 0; q < NC; ++q) cr[q] = block_sum_lean(cr[q], buf);
+  vm = block_max_u64(vm, redu);
+  if (threadIdx.x == 0) {
+    double* pp = ws.part2 + blockIdx.x * NPART;
+    pp[0] = nrm;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) pp[1 + q] = cr[q];
+    pp[T_MAX] = __longlong_as_double((long long)vm);
+  }
+}
+
+template <int NW, int NC>
+static cudaError_t launch_upd(const WS& ws, const Win& win, double* vnext, int j, cudaStream_t st) {
+  k_update<NW, NC><<<update_grid(ws), 256, 0, st>>>(ws, win, vnext, j);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_sketch(const WS& ws, const double* const* vcol, double* vnext, int j, cudaStream_t st) {
+  Win win;
+  win.lo = j - ws.t + 1 > 0 ? j - ws.t + 1 : 0;
+  win.nw = j - win.lo + 1;
+  for (int a = 0; a < T_MAX; ++a) win.v[a] = a < win.nw ? vcol[win.lo + a] : nullptr;
+  const int nc = ws.t - 1;
+  switch (win.nw * 10 + nc) {
+    case 10: return launch_upd<1, 0>(ws, win, vnext, j, st);
+    case 11: return launch_upd<1, 1>(ws, win, vnext, j, st);
+    case 12: return launch_upd<1, 2>(ws, win, vnext, j, st);
+    case 13: return launch_upd<1, 3>(ws, win, vnext, j, st);
+    case 21: return launch_upd<2, 1>(ws, win, vnext, j, st);
+    case 22: return launch_upd<2, 2>(ws, win, vnext, j, st);
+    case 23: return launch_upd<2, 3>(ws, win, vnext, j, st);
+    case 32: return launch_upd<3, 2>(ws, win, vnext, j, st);
+    case 33: return launch_upd<3, 3>(ws, win, vnext, j, st);
+    case 43: return launch_upd<4, 3>(ws, win, vnext, j, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tall products with [U, V] on the integer pipe (see eidot.cuh).  Column l of
+// W = [U, V(:, 0:j)] is scaled by 2^delta_l so that its largest magnitude lies
+// in [0.5, 1); all elements then share one fixed-point unit 2^-51, and the
+// coefficients carry the inverse scales (prepared by the dense kernels).
 // ---------------------------------------------------------------------------
 struct Cols {
   const double* v0;  // column 0 of V (the cycle's residual)
   const double* vs;  // columns 1.. (column c at vs + (c-1)*ldv)
 };
 
-__global__ void k_check_gemv(WS ws, const double* __restrict__ U, Cols V, const double* __restrict__ xcur,
-                             double* __restrict__ xtrial, int kh, int j) {
+__device__ __forceinline__ const double* wcol(const double* U, const Cols& V, int64_t ld, int kh, int l) {
+  return l < kh ? U + (int64_t)l * ld : (l == kh ? V.v0 : V.vs + (int64_t)(l - kh - 1) * ld);
+}
+
+// delta_l = -(frexp exponent of the column's max |.|), from recorded maxima.
+__device__ __forceinline__ int col_delta(const Ctl* c, int ubuf, int kh, int l) {
+  const unsigned long long mb = l < kh ? c->umax[ubuf][l] : c->vmax[l - kh];
+  const int e = bexp_of_bits(mb);
+  return e == 0 ? 0 : -(e - 1022);
+}
+
+// x_trial = x + W y'  (one thread per row).
+__global__ void __launch_bounds__(256) k_check_q(WS ws, const double* __restrict__ U, Cols V,
+                                                 const double* __restrict__ xcur, double* __restrict__ xtrial,
+                                                 int kh, int j, int ubuf) {
   Ctl* c = ws.ctl;
   if (!c->check) return;
-  __shared__ double cf[D_MAX];
+  __shared__ Q52 yq[D_MAX];
+  __shared__ int dl[D_MAX];
   __shared__ unsigned long long redu[32];
   const int d = kh + j + 1;
-  for (int l = threadIdx.x; l < d; l += blockDim.x)
-    cf[l] = l < kh ? ws.ytil[l] : ws.ytil[l] * c->alpha[l - kh];
+  for (int l = threadIdx.x; l < d; l += blockDim.x) {
+    const unsigned long long b = ws.ytq[l];
+    yq[l].hi = (int)(b >> 32);
+    yq[l].lo = (unsigned)(b & 0xFFFFFFFFull);
+    dl[l] = col_delta(c, ubuf, kh, l);
+  }
   __syncthreads();
+  const int sexp = (1022 - 1022) - 51 + ws.yexp[0] - 51;
   const int64_t ld = ws.ldv;
   unsigned long long xm = 0ull;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ws.n; r += (int64_t)gridDim.x * blockDim.x) {
-    double acc = xcur[r];
-    for (int l = 0; l < kh; ++l) acc = fma(U[r + l * ld], cf[l], acc);
-    acc = fma(V.v0[r], cf[kh], acc);
-    for (int cc = 1; cc <= j; ++cc) acc = fma(V.vs[r + (int64_t)(cc - 1) * ld], cf[kh + cc], acc);
-    xtrial[r] = acc;
-    unsigned long long u = abs_bits(acc);
+    Acc3 acc;
+    acc.zero();
+    int l = 0;
+    for (; l + 4 <= d; l += 4) {
+      const double w0 = wcol(U, V, ld, kh, l)[r], w1 = wcol(U, V, ld, kh, l + 1)[r];
+      const double w2 = wcol(U, V, ld, kh, l + 2)[r], w3 = wcol(U, V, ld, kh, l + 3)[r];
+      acc.mac(q52(w0, 1022, dl[l]), yq[l]);
+      acc.mac(q52(w1, 1022, dl[l + 1]), yq[l + 1]);
+      acc.mac(q52(w2, 1022, dl[l + 2]), yq[l + 2]);
+      acc.mac(q52(w3, 1022, dl[l + 3]), yq[l + 3]);
+    }
+    for (; l < d; ++l) acc.mac(q52(wcol(U, V, ld, kh, l)[r], 1022, dl[l]), yq[l]);
+    const double v = xcur[r] + acc_to_double(acc, sexp);
+    xtrial[r] = v;
+    const unsigned long long u = abs_bits(v);
     xm = u > xm ? u : xm;
   }
   xm = block_max_u64(xm, redu);
@@ -426,55 +606,104 @@ __global__ void k_check_gemv(WS ws, const double* __restrict__ U, Cols V, const 
 }
 
 cudaError_t launch_check_gemv(const WS& ws, const double* U, const double* const* vcol, const double* xcur,
-                              double* xtrial, int kh, int j, cudaStream_t st) {
+                              double* xtrial, int kh, int j, int ubuf, cudaStream_t st) {
   Cols V{vcol[0], ws.Vs};
-  k_check_gemv<<<grid_rows(ws.n, 256, ws.grid_max), 256, 0, st>>>(ws, U, V, xcur, xtrial, kh, j);
+  k_check_q<<<grid_rows(ws.n, 256, ws.grid_max), 256, 0, st>>>(ws, U, V, xcur, xtrial, kh, j, ubuf);
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// U_new = [U, V(:, 0:jf)] P' (P' rows for V already scaled by alpha).
-// ---------------------------------------------------------------------------
-__global__ void k_recycle_gemm(WS ws, const double* __restrict__ U, Cols V, double* __restrict__ Unew, int kh) {
+// U_new = W P' for the kprime recycle columns.  A CTA stages RT rows of W as
+// fixed-point values in shared memory; thread (r, g) accumulates row r against
+// columns 8g .. 8g+7 of P'' (read through L1: every lane of a warp reads the
+// same coefficient).
+constexpr int RT = 32;
+__global__ void __launch_bounds__(128, 4) k_recycle_q(WS ws, const double* __restrict__ U, Cols V,
+                                                      double* __restrict__ Unew, int kh, int ucur, int unext) {
   Ctl* c = ws.ctl;
-  const int kp = c->kprime;
-  const int d = kh + c->jf;
-  if (kp <= 0 || c->jf <= 0) return;
-  extern __shared__ double Ps[];  // d x kp, row-major (Ps[l*K_MAX + col])
-  for (int i = threadIdx.x; i < d * K_MAX; i += blockDim.x) {
-    int l = i / K_MAX, cc = i % K_MAX;
-    Ps[i] = cc < kp ? ws.P[l + cc * D_MAX] : 0.0;
-  }
+  const int kp = c->kprime, jf = c->jf;
+  if (kp <= 0 || jf <= 0) return;
+  const int d = kh + jf;
+  extern __shared__ unsigned long long smq[];
+  Q52* tile = (Q52*)smq;  // [d][RT]
+  __shared__ int dl[D_MAX];
+  __shared__ int fx[K_MAX];
+  for (int l = threadIdx.x; l < d; l += blockDim.x) dl[l] = col_delta(c, ucur, kh, l);
+  for (int cc = threadIdx.x; cc < K_MAX; cc += blockDim.x) fx[cc] = ws.Pexp[cc];
   __syncthreads();
-  const int64_t ld = ws.ldv;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ws.n; r += (int64_t)gridDim.x * blockDim.x) {
-    double acc[K_MAX];
+  const int64_t ld = ws.ldv, n = ws.n;
+  const int r = threadIdx.x % RT, g = threadIdx.x / RT;
+  const int ngroups = (kp + 7) / 8;
+  unsigned long long um[8] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+  const int64_t ntiles = (n + RT - 1) / RT;
+  const int step = blockDim.x / RT;
+  for (int64_t tile_i = blockIdx.x; tile_i < ntiles; tile_i += gridDim.x) {
+    const int64_t r0 = tile_i * RT;
+    const int nr = (int)(n - r0 < RT ? n - r0 : RT);
+    for (int l0 = g; l0 < d; l0 += 8 * step) {  // issue eight loads before converting any
+      double w[8];
 #pragma unroll
-    for (int cc = 0; cc < K_MAX; ++cc) acc[cc] = 0.0;
-    for (int l = 0; l < d; ++l) {
-      double wv;
-      if (l < kh) wv = U[r + l * ld];
-      else if (l == kh) wv = V.v0[r];
-      else wv = V.vs[r + (int64_t)(l - kh - 1) * ld];
-      const double* pr = Ps + l * K_MAX;
+      for (int u = 0; u < 8; ++u) {
+        const int l = l0 + u * step;
+        w[u] = (l < d && r < nr) ? wcol(U, V, ld, kh, l)[r0 + r] : 0.0;
+      }
 #pragma unroll
-      for (int cc = 0; cc < K_MAX; ++cc)
-        if (cc < kp) acc[cc] = fma(wv, pr[cc], acc[cc]);
+      for (int u = 0; u < 8; ++u) {
+        const int l = l0 + u * step;
+        if (l < d) tile[l * RT + r] = q52(w[u], 1022, dl[l]);
+      }
     }
+    __syncthreads();
+    for (int gg = g; gg < ngroups; gg += step) {
+      Acc3 acc[8];
 #pragma unroll
-    for (int cc = 0; cc < K_MAX; ++cc)
-      if (cc < kp) Unew[r + cc * ld] = acc[cc];
+      for (int q = 0; q < 8; ++q) acc[q].zero();
+      const unsigned long long* __restrict__ yc = ws.Pq + (int64_t)(gg * 8) * D_MAX;
+      for (int l = 0; l < d; ++l) {
+        const Q52 x = tile[l * RT + r];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const unsigned long long yb = __ldg(yc + q * D_MAX + l);  // packed (hi << 32) | lo
+          Q52 y;
+          y.hi = (int)(yb >> 32);
+          y.lo = (unsigned)(yb & 0xFFFFFFFFull);
+          acc[q].mac(x, y);
+        }
+      }
+      if (r < nr) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int col = gg * 8 + q;
+          if (col < kp) {
+            const double v = acc_to_double(acc[q], -51 + fx[col] - 51);
+            Unew[r0 + r + (int64_t)col * ld] = v;
+            const unsigned long long u = abs_bits(v);
+            if (gg == g) um[q] = u > um[q] ? u : um[q];
+            else atomicMax(&c->umax[unext][col], u);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (g < ngroups) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int col = g * 8 + q;
+      unsigned long long u = warp_max_u64(um[q]);
+      if ((threadIdx.x & 31) == 0 && col < kp && u) atomicMax(&c->umax[unext][col], u);
+    }
   }
 }
 
 cudaError_t launch_recycle_gemm(const WS& ws, const double* U, const double* const* vcol, double* Unew, int kh,
-                                cudaStream_t st) {
+                                int ucur, int unext, cudaStream_t st) {
   Cols V{vcol[0], ws.Vs};
-  size_t sm = (size_t)D_MAX * K_MAX * sizeof(double);
+  const size_t sm = (size_t)D_MAX * RT * sizeof(Q52);
   static bool attr = false;
-  cudaError_t e = set_smem((const void*)k_recycle_gemm, sm, attr);
+  cudaError_t e = set_smem((const void*)k_recycle_q, sm, attr);
   if (e != cudaSuccess) return e;
-  k_recycle_gemm<<<grid_rows(ws.n, 128, ws.grid_max * 2), 128, sm, st>>>(ws, U, V, Unew, kh);
+  const int nsm = ws.grid_max / 8;
+  k_recycle_q<<<nsm * 4, 128, sm, st>>>(ws, U, V, Unew, kh, ucur, unext);
   return cudaGetLastError();
 }
 

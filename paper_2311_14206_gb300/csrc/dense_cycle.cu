@@ -17,6 +17,7 @@
 // selected eigenvectors, back-transformation, and an orthonormal real basis of
 // their span (real and imaginary parts of complex pairs).
 #include "launch.cuh"
+#include "eidot.cuh"
 
 namespace sdr {
 
@@ -836,7 +837,7 @@ __global__ void k_ce_select(WS ws) {
 // Orthonormal basis Z of the selected eigenvectors (MGS, two passes), P, the
 // alpha-scaled P' for the tall update, and the cycle log.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_ce_finish(WS ws, int kh) {
+__global__ void __launch_bounds__(512) k_ce_finish(WS ws, int kh, int ucur) {
   Ctl* c = ws.ctl;
   if (c->jf <= 0) return;
   const int n = c->ell;
@@ -884,6 +885,33 @@ __global__ void __launch_bounds__(512) k_ce_finish(WS ws, int kh) {
     ws.P[l + (int64_t)col * D_MAX] = l < kh ? v : v * c->alpha[l - kh];
   }
   __syncthreads();
+  // fixed-point P'' = diag(2^(E_l)) P' per column for the tall update, where
+  // 2^(-E_l) scales column l of [U V] to a maximum in [0.5, 1)
+  {
+    __shared__ unsigned long long redu[32];
+    for (int col = 0; col < kp; ++col) {
+      unsigned long long mb = 0ull;
+      for (int l = threadIdx.x; l < d; l += blockDim.x) {
+        const unsigned long long cb = l < kh ? c->umax[ucur][l] : c->vmax[l - kh];
+        const int ce = bexp_of_bits(cb);
+        const double pv = ws.P[l + (int64_t)col * D_MAX];
+        const double pp = ce == 0 ? 0.0 : ldexp(pv, ce - 1022);
+        L.Hc[l] = pp;  // scratch row (Hc is unused here)
+        const unsigned long long u = abs_bits(pp);
+        mb = u > mb ? u : mb;
+      }
+      mb = block_max_u64(mb, redu);
+      const int emax = bexp_of_bits(mb);
+      for (int l = threadIdx.x; l < d; l += blockDim.x) {
+        const Q52 q = q52(L.Hc[l], emax, 0);
+        ws.Pq[l + (int64_t)col * D_MAX] = ((unsigned long long)(unsigned)q.hi << 32) | (unsigned long long)q.lo;
+      }
+      if (threadIdx.x == 0) ws.Pexp[col] = emax - 1022;
+      __syncthreads();
+    }
+    for (int col = threadIdx.x; col < K_MAX; col += blockDim.x) c->umax[1 - ucur][col] = 0ull;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     const int li = c->log_n;
     if (li < LOG_MAX) {
@@ -928,8 +956,8 @@ __global__ void k_ce_sketch_update(WS ws, int kh, const double* __restrict__ SU,
   }
 }
 
-cudaError_t launch_cycle_end_part(int part, const WS& ws, int kh, const double* SU, const double* SAU, double* SUn,
-                                  double* SAUn, cudaStream_t st) {
+cudaError_t launch_cycle_end_part(int part, const WS& ws, int kh, int ucur, const double* SU, const double* SAU,
+                                  double* SUn, double* SAUn, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_ce_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ce_eig_smem());
@@ -945,7 +973,7 @@ cudaError_t launch_cycle_end_part(int part, const WS& ws, int kh, const double* 
     case 4: k_ce_eig<<<1, 512, ce_eig_smem(), st>>>(ws); break;
     case 5: k_ce_invit<<<KC, 256, 0, st>>>(ws); break;
     case 6: k_ce_select<<<1, 256, 0, st>>>(ws); break;
-    case 7: k_ce_finish<<<1, 512, 0, st>>>(ws, kh); break;
+    case 7: k_ce_finish<<<1, 512, 0, st>>>(ws, kh, ucur); break;
     case 8: k_ce_sketch_update<<<K_MAX, 512, 0, st>>>(ws, kh, SU, SAU, SUn, SAUn); break;
     default: return cudaErrorInvalidValue;
   }

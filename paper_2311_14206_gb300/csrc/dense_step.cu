@@ -9,6 +9,7 @@
 // reflectors are added; the sketched residual ||S r0 - SAW y|| equals the norm
 // of z below the current column.
 #include "launch.cuh"
+#include "eidot.cuh"
 
 namespace sdr {
 
@@ -129,6 +130,8 @@ __global__ void __launch_bounds__(DT) k_cycle_init(WS ws, const double* __restri
     double v = int128_to_double(accR[2 * i], accR[2 * i + 1], top - 126) * ws.inv_sqrt_zeta;
     accR[2 * i] = 0ull;
     accR[2 * i + 1] = 0ull;
+    ws.acc[2 * i] = 0ull;  // a cycle that stopped early can leave a speculative sketch here
+    ws.acc[2 * i + 1] = 0ull;
     ws.Sr0[i] = v;
     sm.z[i] = v;
     ws.SV[i] = beta > 0.0 ? v / beta : 0.0;
@@ -181,7 +184,7 @@ cudaError_t launch_cycle_init(const WS& ws, const double* SAU, int kh, unsigned 
 // ---------------------------------------------------------------------------
 // Arnoldi step j, dense part.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(DT) k_step_dense(WS ws, int j, int kh, int grid2, unsigned long long* accR) {
+__global__ void __launch_bounds__(DT) k_step_dense(WS ws, int j, int kh, int ubuf, int grid2, unsigned long long* accR) {
   Ctl* c = ws.ctl;
   if (c->done) return;
   __shared__ QrSmem sm;
@@ -192,42 +195,21 @@ __global__ void __launch_bounds__(DT) k_step_dense(WS ws, int j, int kh, int gri
   const int s = ws.s, t = ws.t;
   const int p = kh + j;
   const int lo = j - t + 1 > 0 ? j - t + 1 : 0;
-  // 1. reduce the update kernel's partials
-  double nrm = 0.0;
-  for (int b = threadIdx.x; b < grid2; b += blockDim.x) nrm += ws.part[b * NPART + 0];
-  nrm = block_sum(nrm, sm.red);
-  double cross[T_MAX];
-  for (int d = 0; d < T_MAX; ++d) {
-    double v = 0.0;
-    if (d < t - 1) {
-      for (int b = threadIdx.x; b < grid2; b += blockDim.x) v += ws.part[b * NPART + 1 + d];
-      v = block_sum(v, sm.red);
-    }
-    cross[d] = v;
-  }
-  unsigned long long vm = 0ull;
-  for (int b = threadIdx.x; b < grid2; b += blockDim.x) {
-    unsigned long long u = (unsigned long long)__double_as_longlong(ws.part[b * NPART + T_MAX]);
-    vm = u > vm ? u : vm;
-  }
-  vm = block_max_u64(vm, redu);
-  const double h = sqrt(nrm);
-  const bool breakdown = !(h > 0.0) || !isfinite(h);
+  // 1. column j+1 was finished (h(j+1, j), alpha_{j+1}) by the kernel that
+  //    sketched it
+  const bool breakdown = !(c->alpha[j + 1] > 0.0);
   if (threadIdx.x == 0) {
     rank_flag = 0;
-    const double a = breakdown ? 0.0 : 1.0 / h;
-    sh_alpha = a;
-    c->alpha[j + 1] = a;
-    c->vmax[j + 1] = vm;
-    for (int d = 0; d < t - 1; ++d) c->gram[j + 1][d] = cross[d];
-    c->hband[j][t] = breakdown ? 0.0 : h;
-    if (breakdown) c->breakdown = 1;
-    for (int o = 0; o <= T_MAX; ++o) hcol[o] = o < t ? c->hband[j][o] : 0.0;
-    hcol[t] = breakdown ? 0.0 : h;
+    sh_alpha = c->alpha[j + 1];
+    for (int o = 0; o <= T_MAX; ++o) hcol[o] = o <= t ? c->hband[j][o] : 0.0;
+    if (breakdown) {
+      hcol[t] = 0.0;
+      c->breakdown = 1;
+    }
   }
   __syncthreads();
   // 2. S v_hat_{j+1} from the accumulators; SV(:, j+1); 3. SAV(:, j)
-  const int top = c->acc_top;
+  const int top = c->vtop[j + 1];
   const double a1 = sh_alpha;
   for (int i = threadIdx.x; i < s; i += blockDim.x) {
     double raw = int128_to_double(ws.acc[2 * i], ws.acc[2 * i + 1], top - 126) * ws.inv_sqrt_zeta;
@@ -278,10 +260,52 @@ __global__ void __launch_bounds__(DT) k_step_dense(WS ws, int j, int kh, int gri
     for (int l = threadIdx.x; l < i; l += blockDim.x) sm.z[l] = fma(-ws.Rf[l + (int64_t)i * ws.dmax], y, sm.z[l]);
     __syncthreads();
   }
+  // fixed-point coefficients for the check GEMV: y''_l = y'_l 2^(E_l) with
+  // y'_l = y_l (U part) or y_l alpha_l (V part) and 2^(-E_l) the column scale
+  unsigned long long mb = 0ull;
+  for (int l = threadIdx.x; l <= p; l += blockDim.x) {
+    const unsigned long long cb = l < kh ? c->umax[ubuf][l] : c->vmax[l - kh];
+    const int ce = bexp_of_bits(cb);
+    const double yp = l < kh ? ws.ytil[l] : ws.ytil[l] * c->alpha[l - kh];
+    const double yy = ce == 0 ? 0.0 : ldexp(yp, ce - 1022);
+    sm.c[l] = yy;
+    const unsigned long long u = abs_bits(yy);
+    mb = u > mb ? u : mb;
+  }
+  mb = block_max_u64(mb, redu);
+  const int emax = bexp_of_bits(mb);
+  for (int l = threadIdx.x; l <= p; l += blockDim.x) {
+    const Q52 q = q52(sm.c[l], emax, 0);
+    ws.ytq[l] = ((unsigned long long)(unsigned)q.hi << 32) | (unsigned long long)q.lo;
+  }
+  if (threadIdx.x == 0) ws.yexp[0] = emax - 1022;
 }
 
-cudaError_t launch_step_dense(const WS& ws, int j, int kh, unsigned long long* accR, cudaStream_t st) {
-  k_step_dense<<<1, DT, 0, st>>>(ws, j, kh, update_grid(ws), accR);
+// max |U(:, l)| per column into ctl->umax[ubuf][l].
+__global__ void k_umax(WS ws, const double* __restrict__ U, int kdim, int ubuf) {
+  __shared__ unsigned long long redu[32];
+  const int l = blockIdx.y;
+  unsigned long long m = 0ull;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ws.n; r += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long u = abs_bits(U[r + (int64_t)l * ws.ldv]);
+    m = u > m ? u : m;
+  }
+  m = block_max_u64(m, redu);
+  if (threadIdx.x == 0 && m) atomicMax(&ws.ctl->umax[ubuf][l], m);
+}
+
+cudaError_t launch_umax(const WS& ws, const double* U, int kdim, int ubuf, cudaStream_t st) {
+  if (kdim <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(&ws.ctl->umax[ubuf][0], 0, sizeof(unsigned long long) * K_MAX, st);
+  if (e != cudaSuccess) return e;
+  int gx = (int)((ws.n + 255) / 256);
+  if (gx > 64) gx = 64;
+  k_umax<<<dim3(gx, kdim), 256, 0, st>>>(ws, U, kdim, ubuf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_dense(const WS& ws, int j, int kh, int ubuf, unsigned long long* accR, cudaStream_t st) {
+  k_step_dense<<<1, DT, 0, st>>>(ws, j, kh, ubuf, update_grid(ws), accR);
   return cudaGetLastError();
 }
 

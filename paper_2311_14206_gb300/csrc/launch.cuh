@@ -39,20 +39,24 @@ cudaError_t launch_update_sketch(const WS& ws, const double* const* vcol, double
                                  cudaStream_t st);
 // x_trial = x_cur + [U V(:,0:j+1)] (scaled ytil) when ctl->check.
 cudaError_t launch_check_gemv(const WS& ws, const double* U, const double* const* vcol, const double* xcur,
-                              double* xtrial, int kh, int j, cudaStream_t st);
+                              double* xtrial, int kh, int j, int ubuf, cudaStream_t st);
 // U_new = [U V(:,0:jf)] P' (kprime columns from ctl).
 cudaError_t launch_recycle_gemm(const WS& ws, const double* U, const double* const* vcol, double* Unew,
-                                int kh, cudaStream_t st);
+                                int kh, int ucur, int unext, cudaStream_t st);
 // y = A x (plain SpMV, used for A U in the exact recycling variant).
 cudaError_t launch_spmv(CsrDev A, const double* x, double* y, cudaStream_t st);
 int update_grid(const WS& ws);
+// S v_hat_j of the cycle's last column, with the column's finish.
+cudaError_t launch_sketch_col(const WS& ws, const double* x, int j, cudaStream_t st);
 
 // ---- dense_step.cu ----
 // Cycle start: Sr0, beta, SV(:,0), QR of SAU (kh columns).
 cudaError_t launch_cycle_init(const WS& ws, const double* SAU, int kh, unsigned long long* accR,
                               int persist_safety, cudaStream_t st);
 // Arnoldi step j, small dense part: h(j+1,j), SV(:,j+1), SAV(:,j), QR update, sres, control.
-cudaError_t launch_step_dense(const WS& ws, int j, int kh, unsigned long long* accR, cudaStream_t st);
+cudaError_t launch_step_dense(const WS& ws, int j, int kh, int ubuf, unsigned long long* accR, cudaStream_t st);
+// max |U(:, l)| of kdim columns into ctl->umax[ubuf] (after an import).
+cudaError_t launch_umax(const WS& ws, const double* U, int kdim, int ubuf, cudaStream_t st);
 
 // ---- dense_cycle.cu ----
 // Cycle end: harmonic-Ritz recycling (Section 3.4); P' into ws.P, SU/SAU for the next cycle.
@@ -60,7 +64,7 @@ cudaError_t launch_step_dense(const WS& ws, int j, int kh, unsigned long long* a
 // when not certified), FP32 eigenvalue candidates, FP64 inverse iteration per
 // candidate, selection, basis + P, SU/SAU products.
 constexpr int CYCLE_END_PARTS = 9;
-cudaError_t launch_cycle_end_part(int part, const WS& ws, int kh, const double* SU, const double* SAU, double* SUn,
-                                  double* SAUn, cudaStream_t st);
+cudaError_t launch_cycle_end_part(int part, const WS& ws, int kh, int ucur, const double* SU, const double* SAU,
+                                  double* SUn, double* SAUn, cudaStream_t st);
 
 }  // namespace sdr

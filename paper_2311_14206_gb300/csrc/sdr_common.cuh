@@ -11,7 +11,8 @@ constexpr int D_MAX = M_MAX + K_MAX;  // columns of SAW
 constexpr int S_MAX = 512;   // sketch rows
 constexpr int T_MAX = 4;     // Arnoldi truncation window
 constexpr int ZETA_MAX = 32;
-constexpr int TILE_R = 2048; // rows per sketch tile (zeta*TILE_R < 65536 for uint16 offsets)
+constexpr int PTR_STRIDE = S_MAX + 8;  // per-tile row-pointer stride (16-byte multiple)
+constexpr int TILE_R = 1024; // rows per sketch tile (zeta*TILE_R < 65536 for uint16 offsets)
 constexpr int NPART = 8;     // doubles of per-CTA partial results
 constexpr int HIST_MAX = 1 << 15;  // logged Arnoldi steps per solve
 constexpr int LOG_MAX = 512;       // logged cycles per solve
@@ -42,8 +43,10 @@ struct Ctl {
   unsigned int counter;   // last-CTA counter for grid reductions
   unsigned int counter2;
   double alpha[M_MAX + 2];                // 1 / ||v_hat_c||
+  int vtop[M_MAX + 2];                    // window top for the sketch of v_hat_c
   unsigned long long vmax[M_MAX + 2];     // bits of max |v_hat_c|
   unsigned long long wmax, xmax, rmax;    // bits of max |w|, |x_trial|, |r|
+  unsigned long long umax[2][K_MAX];      // bits of max |U(:, l)| of each recycle buffer
   double hband[M_MAX][T_MAX + 1];         // H(i, j), i = j-t+1 .. j+1 at index i-(j-t+1)
   double gram[M_MAX + 2][T_MAX];          // v_hat_c . v_hat_{c-1-d}, d = 0..t-2
   double coef[T_MAX + 1];                 // a_0 (w) and a_1.. (window) for the update
@@ -76,6 +79,7 @@ struct WS {
   int ntiles;
   // reductions
   double* part;             // [grid_max][NPART]
+  double* part2;            // [grid_max][NPART] partials of the Arnoldi update
   unsigned long long* acc;  // 128-bit accumulators, acc[2*i] = lo, acc[2*i+1] = hi
   int grid_max;
   // small dense (column-major)
@@ -91,6 +95,10 @@ struct WS {
   double* Sr0;   // s
   double* ytil;  // dmax
   double* P;     // dmax x kmax: recycle coefficients (V rows scaled by alpha)
+  unsigned long long* Pq;  // D_MAX x K_MAX fixed-point P'' (Q52 bits) for the tall update
+  int* Pexp;     // K_MAX: exponent of each P'' column's scale
+  unsigned long long* ytq; // D_MAX fixed-point y'' for the check GEMV
+  int* yexp;     // [0]: exponent of y'' scale
   double* dscr;  // dense scratch for the cycle-end kernel
   double* hist;  // HIST_MAX sres values
   CycleLog* log; // LOG_MAX entries
@@ -218,8 +226,10 @@ __host__ __device__ inline int sketch_tile_rows(int zeta) {
 }
 inline size_t sketch_smem_bytes(int zeta) {
   int tileR = sketch_tile_rows(zeta);
-  return (size_t)tileR * 8 + (size_t)tileR * zeta * 2 + (S_MAX + 8) * 2;
+  return (size_t)tileR * 8 + (size_t)tileR * zeta * 2 + (S_MAX + 16) * 2;
 }
+constexpr int SK_THREADS = 256;              // threads of the tile-sketch kernels
+constexpr int SK_RPT = S_MAX / SK_THREADS;   // sketch rows per thread
 
 // ---------------------------------------------------------------------------
 // Block-level helpers.
@@ -256,6 +266,26 @@ __device__ inline double block_sum(double v, double* red) {
   return r;
 }
 
+// Block sum with one FP64 add per value staged: every thread stores its value,
+// the first warp adds blockDim/32 values per lane and then reduces across lanes
+// (about a dozen FP64 warp instructions for 256 threads instead of ~45 for a
+// shuffle tree per warp).  buf needs blockDim.x doubles.  Fixed order.
+__device__ inline double block_sum_lean(double v, double* buf) {
+  __syncthreads();
+  buf[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < blockDim.x; i += 32) a += buf[i];
+    a = warp_sum(a);
+    if (threadIdx.x == 0) buf[0] = a;
+  }
+  __syncthreads();
+  const double r = buf[0];
+  __syncthreads();
+  return r;
+}
+
 __device__ inline unsigned long long block_max_u64(unsigned long long v, unsigned long long* red) {
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   v = warp_max_u64(v);
@@ -273,40 +303,63 @@ __device__ inline unsigned long long block_max_u64(unsigned long long v, unsigne
   return r;
 }
 
-// Add the tile's contribution S_tile x_tile to the 128-bit accumulator of
-// sketch row threadIdx.x (threads >= s do nothing).  vals holds the tile's
-// values (tileR doubles, zero beyond ncols) and is overwritten.  All threads
-// of the block must call it.
-__device__ inline void tile_sketch_accumulate(const WS& ws, int tileR, int tile, int ncols, double* vals,
-                                              uint16_t* ent_s, uint16_t* ptr_s, unsigned long long* red,
-                                              int top, unsigned long long& lo, unsigned long long& hi) {
-  const uint4* src = (const uint4*)(ws.sk_ent + (int64_t)tile * tileR * ws.zeta);
-  uint4* dst = (uint4*)ent_s;
-  const int nvec = (tileR * ws.zeta) / 8;
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = src[i];
-  const uint16_t* psrc = ws.sk_ptr + (int64_t)tile * (S_MAX + 1);
-  for (int i = threadIdx.x; i <= ws.s; i += blockDim.x) ptr_s[i] = psrc[i];
+// Sketch of one tile: the tile's index lists (tileR*zeta offsets and s+1 row
+// pointers) are copied to shared memory with cp.async (16-byte pieces) so the
+// copy overlaps the caller's computation of the tile's values.
+__device__ inline void tile_sketch_prefetch(const WS& ws, int tileR, int tile, uint16_t* ent_s, uint16_t* ptr_s) {
+  const char* src = (const char*)(ws.sk_ent + (int64_t)tile * tileR * ws.zeta);
+  const int nvec = (tileR * ws.zeta) / 8;  // 16-byte pieces
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+    const unsigned saddr = (unsigned)__cvta_generic_to_shared(ent_s + 8 * i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(src + 16 * (int64_t)i));
+  }
+  const char* psrc = (const char*)(ws.sk_ptr + (int64_t)tile * PTR_STRIDE);
+  // S_MAX + 1 uint16 rounded down to whole 16-byte pieces, the tail by plain loads
+  const int pvec = ((ws.s + 1) * 2) / 16;
+  for (int i = threadIdx.x; i < pvec; i += blockDim.x) {
+    const unsigned saddr = (unsigned)__cvta_generic_to_shared(ptr_s + 8 * i);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(psrc + 16 * (int64_t)i));
+  }
+  asm volatile("cp.async.commit_group;\n" ::);
+  const uint16_t* pp = ws.sk_ptr + (int64_t)tile * PTR_STRIDE;
+  for (int i = pvec * 8 + threadIdx.x; i <= ws.s; i += blockDim.x) ptr_s[i] = pp[i];
+}
+
+// Add the tile's contribution S_tile x_tile to the 128-bit accumulators of the
+// sketch rows this thread owns (rows threadIdx.x + q * blockDim.x, q < RPT).
+// vals holds the tile's values (tileR doubles, zero beyond ncols) and is
+// overwritten; the index lists must have been prefetched.  All threads of the
+// block must call it.
+template <int RPT>
+__device__ inline void tile_sketch_accumulate(const WS& ws, int ncols, double* vals, const uint16_t* ent_s,
+                                              const uint16_t* ptr_s, unsigned long long* red, int top,
+                                              unsigned long long* lo, unsigned long long* hi) {
+  asm volatile("cp.async.wait_all;\n" ::);
   unsigned long long mb = 0ull;
   for (int i = threadIdx.x; i < ncols; i += blockDim.x) {
-    unsigned long long b = abs_bits(vals[i]);
+    const unsigned long long b = abs_bits(vals[i]);
     mb = b > mb ? b : mb;
   }
-  mb = block_max_u64(mb, red);  // synchronises the block
+  mb = block_max_u64(mb, red);  // synchronises the block (also publishes the prefetch)
   const int emax = bexp_of_bits(mb);
   if (emax == 0 || emax == 0x7FF) return;  // all zero, or non-finite (caught through the norms)
   long long* q = (long long*)vals;
   for (int i = threadIdx.x; i < ncols; i += blockDim.x) q[i] = quantize_fixed(vals[i], emax);
   __syncthreads();
-  if (threadIdx.x < ws.s) {
-    long long a = 0;
-    const int e0 = ptr_s[threadIdx.x], e1 = ptr_s[threadIdx.x + 1];
-    for (int e = e0; e < e1; ++e) {
-      const uint16_t c = ent_s[e];
-      const long long v = q[c & 0x7FFF];
-      a += (c & 0x8000) ? -v : v;
+  const int sh = (emax - 1022) - 51 - (top - 126);  // tile unit 2^(e_t - 51) in window units
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int row = threadIdx.x + k * blockDim.x;
+    if (row < ws.s) {
+      long long a = 0;
+      const int e0 = ptr_s[row], e1 = ptr_s[row + 1];
+      for (int e = e0; e < e1; ++e) {
+        const uint16_t c = ent_s[e];
+        const long long v = q[c & 0x7FFF];
+        a += (c & 0x8000) ? -v : v;
+      }
+      add_shifted128(lo[k], hi[k], a, sh);
     }
-    // tile value = a * 2^(e_t - 51) with e_t = emax - 1022; window unit 2^(top - 126)
-    add_shifted128(lo, hi, a, (emax - 1022) - 51 - (top - 126));
   }
   __syncthreads();
 }

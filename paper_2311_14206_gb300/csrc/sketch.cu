@@ -74,7 +74,7 @@ __global__ void k_sketch_build(uint64_t seed, int s, int zeta, int64_t n, int ti
       e[y + 1] = v;
     }
   }
-  uint16_t* p = ptr + (int64_t)tile * (S_MAX + 1);
+  uint16_t* p = ptr + (int64_t)tile * PTR_STRIDE;
   for (int r = threadIdx.x; r <= s; r += blockDim.x) p[r] = (uint16_t)cnt[r];
 }
 
@@ -102,16 +102,22 @@ __global__ void k_sketch_vec(WS ws, const double* __restrict__ x, int64_t n, uns
   uint16_t* ptr_s = ent_s + tileR * ws.zeta;
   __shared__ unsigned long long red[32];
   const int top = *top_dev;
-  unsigned long long lo = 0ull, hi = 0ull;
+  unsigned long long lo[SK_RPT], hi[SK_RPT];
+#pragma unroll
+  for (int k = 0; k < SK_RPT; ++k) lo[k] = hi[k] = 0ull;
   const int ntiles = (int)((n + tileR - 1) / tileR);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = (int64_t)tile * tileR;
     const int ncols = (int)(n - r0 < (int64_t)tileR ? n - r0 : (int64_t)tileR);
+    tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
     for (int i = threadIdx.x; i < tileR; i += blockDim.x) vals[i] = i < ncols ? x[r0 + i] : 0.0;
-    __syncthreads();
-    tile_sketch_accumulate(ws, tileR, tile, ncols, vals, ent_s, ptr_s, red, top, lo, hi);
+    tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, red, top, lo, hi);
   }
-  if (threadIdx.x < ws.s) atomic_add128(acc + 2 * threadIdx.x, lo, hi);
+#pragma unroll
+  for (int k = 0; k < SK_RPT; ++k) {
+    const int row = threadIdx.x + k * blockDim.x;
+    if (row < ws.s) atomic_add128(acc + 2 * row, lo[k], hi[k]);
+  }
 }
 
 cudaError_t launch_sketch_vec(const WS& ws, const double* x, int64_t n, unsigned long long* acc,
@@ -128,7 +134,7 @@ cudaError_t launch_sketch_vec(const WS& ws, const double* x, int64_t n, unsigned
   int ntiles = (int)((n + tileR - 1) / tileR);
   int grid = ntiles < ws.grid_max ? ntiles : ws.grid_max;
   if (grid < 1) grid = 1;
-  k_sketch_vec<<<grid, 512, sm, st>>>(ws, x, n, acc, top_dev);
+  k_sketch_vec<<<grid, SK_THREADS, sm, st>>>(ws, x, n, acc, top_dev);
   return cudaGetLastError();
 }
 
