@@ -154,6 +154,31 @@ sdr_status sdr_destroy(sdr_handle* h);
  *   x: device pointer (n entries).  y: device pointer (s entries). */
 sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y);
 
+/* y = S x without allocating any device memory.  S is the same hash-defined
+ * sparse-sign embedding a handle with these s, zeta and seed applies (for a
+ * handle whose n_max equals n the results agree bit for bit).  The paper has
+ * no counterpart: this entry point exists for callers that must not let a
+ * library allocate device memory, such as code running while another
+ * component owns the device's memory (a framework's pool, or a budget fixed at
+ * start-up) and latency-critical paths that cannot afford a cudaMalloc, which
+ * may synchronise the device.
+ *   x: device pointer, n entries (1 <= n <= 2^31 - 1).
+ *   y: device pointer, s entries (1 <= s <= 512), overwritten.
+ *   zeta: nonzeros per column, 1 <= zeta <= min(s, 32).
+ *   stream: a cudaStream_t (NULL = legacy default stream).  The call enqueues
+ *   its kernels on it and returns; y is ready when the stream gets there.
+ * Scratch: one file-scope device array of 8,256 bytes, which every GPU that
+ * loads this library keeps until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  Every call
+ * shares the array and clears it before use, so calls whose work overlaps on
+ * the GPU (other streams, or other host threads, before an earlier call's
+ * kernels have finished) race and corrupt each other's results.
+ * Errors: INVALID_ARG for sizes or pointers outside these limits (nothing is
+ * launched), CUDA if the address lookup or a launch fails. */
+sdr_status sdr_sketch_noalloc(const double* x, int64_t n, int32_t s, int32_t zeta, uint64_t seed, double* y,
+                              void* stream);
+
 /* Sketched residual norms of every Arnoldi step of the last sdr_solve, in
  * order, and the per-cycle log.  sres: host pointer with room for cap_steps
  * doubles (may be NULL).  log: host pointer with room for cap_cycles entries

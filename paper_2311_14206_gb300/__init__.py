@@ -21,5 +21,6 @@ from .sdr import (  # noqa: F401
     sdr_recycle_export,
     sdr_recycle_import,
     sdr_sketch,
+    sdr_sketch_noalloc,
     sdr_solve,
 )

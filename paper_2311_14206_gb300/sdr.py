@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sdr_recycle": ([vp, P(sdr_csr), i32], i32),
         "sdr_destroy": ([vp], i32),
         "sdr_sketch": ([vp, vp, i64, vp], i32),
+        "sdr_sketch_noalloc": ([vp, i64, i32, i32, ctypes.c_uint64, vp, vp], i32),
         "sdr_get_history": ([vp, P(ctypes.c_double), i32, P(i32), P(sdr_cycle_log), i32, P(i32)], i32),
         "sdr_recycle_dim": ([vp, P(i32)], i32),
         "sdr_recycle_export": ([vp, i64, vp, vp, vp], i32),
@@ -179,6 +180,16 @@ def sdr_destroy(h):
 def sdr_sketch(h, x: torch.Tensor, s: int) -> torch.Tensor:
     y = torch.empty(s, dtype=torch.float64, device=x.device)
     _check(load_library().sdr_sketch(h, _ptr(x), x.numel(), _ptr(y)), "sdr_sketch")
+    return y
+
+
+def sdr_sketch_noalloc(x: torch.Tensor, s: int, zeta: int, seed: int, y: torch.Tensor = None) -> torch.Tensor:
+    """y = S x through the allocation-free entry point (y preallocated by the
+    caller, or here by torch when y is None)."""
+    if y is None:
+        y = torch.empty(s, dtype=torch.float64, device=x.device)
+    _check(load_library().sdr_sketch_noalloc(_ptr(x), x.numel(), s, zeta, seed, _ptr(y), _stream()),
+           "sdr_sketch_noalloc")
     return y
 
 
