@@ -218,6 +218,9 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   }
   chk(halloc(h, &ws.Y, (size_t)s * D_MAX));
   chk(halloc(h, &ws.T, (size_t)D_MAX * D_MAX));
+  chk(halloc(h, &ws.Yq, (size_t)s * D_MAX));
+  chk(halloc(h, &ws.Tq, (size_t)D_MAX * D_MAX));
+  chk(halloc(h, &ws.texp, (size_t)D_MAX));
   chk(halloc(h, &ws.Rf, (size_t)D_MAX * D_MAX));
   chk(halloc(h, &ws.tau, (size_t)D_MAX));
   chk(halloc(h, &ws.z, (size_t)S_MAX));

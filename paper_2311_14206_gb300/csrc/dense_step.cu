@@ -15,57 +15,96 @@ namespace sdr {
 
 constexpr int DT = 512;  // threads of the dense-step CTA
 
+// ---- fixed-point helpers (see eidot.cuh) ----------------------------------
+__device__ __forceinline__ Q52 unpack(unsigned long long b) {
+  Q52 q;
+  q.hi = (int)(b >> 32);
+  q.lo = (unsigned)(b & 0xFFFFFFFFull);
+  return q;
+}
+__device__ __forceinline__ unsigned long long pack(Q52 q) {
+  return ((unsigned long long)(unsigned)q.hi << 32) | (unsigned long long)q.lo;
+}
+__device__ __forceinline__ void warp_reduce_acc(Acc3& a) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a.hh += __shfl_xor_sync(0xffffffffu, a.hh, o);
+    a.mx += __shfl_xor_sync(0xffffffffu, a.mx, o);
+    a.my += __shfl_xor_sync(0xffffffffu, a.my, o);
+    a.ll += __shfl_xor_sync(0xffffffffu, a.ll, o);
+  }
+}
+// Quantise n values of src (shared) into dst with one common exponent; returns
+// that exponent e (x ~ X 2^(e-51)).  Block-wide, synchronising.
+__device__ int quant_block(const double* src, Q52* dst, int n, unsigned long long* redu) {
+  unsigned long long mb = 0ull;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned long long u = abs_bits(src[i]);
+    mb = u > mb ? u : mb;
+  }
+  mb = block_max_u64(mb, redu);
+  const int emax = bexp_of_bits(mb);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = q52(src[i], emax, 0);
+  __syncthreads();
+  return emax - 1022;
+}
+
+constexpr int YQ_E = 1;  // every Householder vector has max |v_i| = v_p = 1: exponent 1
+
 struct QrSmem {
   double c[S_MAX];
   double z[S_MAX];
   double u[D_MAX];
   double u2[D_MAX];
-  double red[32];
+  Q52 cq[S_MAX];
+  Q52 uq[D_MAX];
+  double red[DT];
+  unsigned long long redu[32];
 };
 
-// y_l = sum_{i >= rowstart(l)} Y(i, l) x_i for l < ncols, warp per column.
-__device__ inline void gemv_yt(const double* __restrict__ Y, int ldy, int s, int ncols, int minrow,
-                               const double* __restrict__ x, double* __restrict__ y) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int l = wid; l < ncols; l += nw) {
-    const int r0 = l > minrow ? l : minrow;
-    const double* col = Y + (int64_t)l * ldy;
-    double acc = 0.0;
-    for (int i = r0 + lane; i < s; i += 32) acc = fma(col[i], x[i], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) y[l] = acc;
-  }
-}
-
-// Add column c (in sm.c, length s) as column p of SAW's QR.  Updates Y, T, Rf,
-// tau (global) and sm.z.  Returns the sketched residual ||z(p+1:s)||.
+// Add column c (in sm.c, length s) as column p of SAW's QR.  Updates Y, Yq, T,
+// Tq, texp, Rf, tau (global) and sm.z.  Returns the sketched residual
+// ||z(p+1:s)||.  The products with Y and T run on the integer pipe.
 __device__ double qr_add_column(const WS& ws, int p, QrSmem& sm, int* rank_flag) {
   const int s = ws.s, ld = ws.dmax;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* __restrict__ Y = ws.Y;
   double* __restrict__ T = ws.T;
+  const unsigned long long* __restrict__ Yq = ws.Yq;
+  const unsigned long long* __restrict__ Tq = ws.Tq;
   // u = Y(:, 0:p)^T c
-  gemv_yt(Y, s, s, p, 0, sm.c, sm.u);
+  const int ec = quant_block(sm.c, sm.cq, s, sm.redu);
+  for (int l = wid; l < p; l += nw) {
+    Acc3 acc;
+    acc.zero();
+    for (int i = l + lane; i < s; i += 32) acc.mac(unpack(Yq[i + (int64_t)l * s]), sm.cq[i]);
+    warp_reduce_acc(acc);
+    if (lane == 0) sm.u[l] = acc_to_double(acc, (YQ_E - 51) + (ec - 51));
+  }
   __syncthreads();
-  // u2 = T(0:p, 0:p)^T u
-  for (int l = threadIdx.x; l < p; l += blockDim.x) {
-    const double* tc = T + (int64_t)l * ld;
-    double a = 0.0;
-    for (int m = 0; m <= l; ++m) a = fma(tc[m], sm.u[m], a);
-    sm.u2[l] = a;
+  // u2 = T(0:p, 0:p)^T u  (column l of T against u)
+  const int eu = quant_block(sm.u, sm.uq, p, sm.redu);
+  for (int l = wid; l < p; l += nw) {
+    Acc3 acc;
+    acc.zero();
+    for (int m = lane; m <= l; m += 32) acc.mac(unpack(Tq[m + (int64_t)l * ld]), sm.uq[m]);
+    warp_reduce_acc(acc);
+    if (lane == 0) sm.u2[l] = acc_to_double(acc, (ws.texp[l] - 51) + (eu - 51));
   }
   __syncthreads();
   // c = c - Y u2   (Y(i, l) = 0 for i < l)
+  const int eu2 = quant_block(sm.u2, sm.uq, p, sm.redu);
   for (int i = threadIdx.x; i < s; i += blockDim.x) {
-    double a = sm.c[i];
     const int lmax = i < p - 1 ? i : p - 1;
-    for (int l = 0; l <= lmax; ++l) a = fma(-Y[i + (int64_t)l * s], sm.u2[l], a);
-    sm.c[i] = a;
+    Acc3 acc;
+    acc.zero();
+    for (int l = 0; l <= lmax; ++l) acc.mac(unpack(Yq[i + (int64_t)l * s]), sm.uq[l]);
+    sm.c[i] -= acc_to_double(acc, (YQ_E - 51) + (eu2 - 51));
   }
   __syncthreads();
   // Householder reflector for c(p:s): H c(p:s) = beta e_1, H = I - tau v v^T, v_0 = 1
   double xs = 0.0;
   for (int i = p + 1 + threadIdx.x; i < s; i += blockDim.x) xs = fma(sm.c[i], sm.c[i], xs);
-  xs = block_sum(xs, sm.red);
+  xs = block_sum_lean(xs, sm.red);
   const double alpha = sm.c[p];
   double beta, tau, scale;
   if (xs == 0.0) {
@@ -78,38 +117,53 @@ __device__ double qr_add_column(const WS& ws, int p, QrSmem& sm, int* rank_flag)
     scale = 1.0 / (alpha - beta);
   }
   if (beta == 0.0 && threadIdx.x == 0) *rank_flag = 1;
-  // R(0:p, p) = c(0:p), R(p, p) = beta; Y(:, p) = v
+  // R(0:p, p) = c(0:p), R(p, p) = beta; Y(:, p) = v (|v_i| <= 1, v_p = 1)
   for (int i = threadIdx.x; i < s; i += blockDim.x) {
     if (i < p) ws.Rf[i + (int64_t)p * ld] = sm.c[i];
     if (i == p) ws.Rf[i + (int64_t)p * ld] = beta;
     const double v = i < p ? 0.0 : (i == p ? 1.0 : sm.c[i] * scale);
     Y[i + (int64_t)p * s] = v;
+    const Q52 q = q52(v, 1022 + YQ_E, 0);
+    ws.Yq[i + (int64_t)p * s] = pack(q);
+    sm.cq[i] = q;
     sm.c[i] = v;  // c now holds v
   }
   if (threadIdx.x == 0) ws.tau[p] = tau;
   __syncthreads();
-  // T(0:p, p) = -tau T(0:p, 0:p) (Y(:, 0:p)^T v),  T(p, p) = tau
-  gemv_yt(Y, s, s, p, p, sm.c, sm.u);
-  __syncthreads();
-  for (int l = threadIdx.x; l <= p; l += blockDim.x) {
-    double a = 0.0;
-    if (l < p) {
-      for (int m = l; m < p; ++m) a = fma(T[l + (int64_t)m * ld], sm.u[m], a);
-      a = -tau * a;
-    } else {
-      a = tau;
-    }
-    T[l + (int64_t)p * ld] = a;
+  // g = Y(:, 0:p)^T v  (v is zero above p), then T(0:p, p) = -tau T(0:p, 0:p) g
+  for (int m = wid; m < p; m += nw) {
+    Acc3 acc;
+    acc.zero();
+    for (int i = p + lane; i < s; i += 32) acc.mac(unpack(Yq[i + (int64_t)m * s]), sm.cq[i]);
+    warp_reduce_acc(acc);
+    // g_m 2^(texp[m]): column m of T is stored scaled by 2^(-texp[m])
+    if (lane == 0) sm.u[m] = acc_to_double(acc, (YQ_E - 51) + (YQ_E - 51) + ws.texp[m]);
   }
+  __syncthreads();
+  const int eg = quant_block(sm.u, sm.uq, p, sm.redu);
+  for (int l = wid; l < p; l += nw) {
+    Acc3 acc;
+    acc.zero();
+    for (int m = l + lane; m < p; m += 32) acc.mac(unpack(Tq[l + (int64_t)m * ld]), sm.uq[m]);
+    warp_reduce_acc(acc);
+    if (lane == 0) sm.u2[l] = -tau * acc_to_double(acc, -51 + (eg - 51));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sm.u2[p] = tau;
+  __syncthreads();
+  for (int l = threadIdx.x; l <= p; l += blockDim.x) T[l + (int64_t)p * ld] = sm.u2[l];
+  const int et = quant_block(sm.u2, sm.uq, p + 1, sm.redu);
+  for (int l = threadIdx.x; l <= p; l += blockDim.x) ws.Tq[l + (int64_t)p * ld] = pack(sm.uq[l]);
+  if (threadIdx.x == 0) ws.texp[p] = et;
   // z(p:s) -= tau v (v^T z(p:s))
   double dz = 0.0;
   for (int i = p + threadIdx.x; i < s; i += blockDim.x) dz = fma(sm.c[i], sm.z[i], dz);
-  dz = block_sum(dz, sm.red);
+  dz = block_sum_lean(dz, sm.red);
   for (int i = p + threadIdx.x; i < s; i += blockDim.x) sm.z[i] = fma(-tau * dz, sm.c[i], sm.z[i]);
   __syncthreads();
   double rr = 0.0;
   for (int i = p + 1 + threadIdx.x; i < s; i += blockDim.x) rr = fma(sm.z[i], sm.z[i], rr);
-  rr = block_sum(rr, sm.red);
+  rr = block_sum_lean(rr, sm.red);
   return sqrt(rr);
 }
 

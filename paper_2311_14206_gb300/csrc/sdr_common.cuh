@@ -88,6 +88,9 @@ struct WS {
   double* SU[2]; // s x kmax
   double* SAU[2];
   double* Y;     // s x dmax Householder vectors
+  unsigned long long* Yq;  // s x dmax fixed-point copy of Y (|Y| <= 1, unit 2^-50)
+  unsigned long long* Tq;  // dmax x dmax fixed-point copy of T, scaled per column
+  int* texp;     // dmax: frexp exponent of each T column's scale
   double* T;     // dmax x dmax
   double* Rf;    // dmax x dmax
   double* tau;   // dmax
