@@ -7,8 +7,8 @@
  * restart cycle is Algorithm 1: a truncated Arnoldi process, a sparse
  * subspace embedding S applied to the new basis vectors, a sketched least
  * squares problem solved through an updated QR factorisation, residual
- * control with a safety factor (Section 3.3), and a sketched harmonic-Ritz
- * update of the recycle space U (Section 3.4).  Section 3.5 defines how U, SU
+ * control with a safety factor (Section 3.4), and a sketched harmonic-Ritz
+ * update of the recycle space U (Section 3.5).  Section 3.6 defines how U, SU
  * and SAU are carried from one system to the next.
  *
  * Conventions for every entry point:
@@ -52,7 +52,7 @@ typedef enum {
 } sdr_status;
 
 /* Solver parameters (Algorithm 1 inputs m, t, k, S and safety; the stopping
- * rule of Section 3.3).
+ * rule of Section 3.4).
  *   m          Krylov columns per cycle (V has m+1 columns), 1 <= m <= 128.
  *   k          recycle dimension; up to k+1 columns are kept when the k-th and
  *              (k+1)-th harmonic Ritz values form a conjugate pair. 0 <= k <= 31.
@@ -136,7 +136,7 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
  * INVALID_ARG or CUDA. */
 sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x, sdr_stats* stats);
 
-/* Prepare the recycle space for the next system in a sequence (Section 3.5).
+/* Prepare the recycle space for the next system in a sequence (Section 3.6).
  *   mode 0 (exact): keep U and SU, recompute SAU = S A_next U with k products
  *          with A_next and k sketches (A_next: host pointer to a CSR
  *          descriptor of device arrays).

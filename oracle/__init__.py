@@ -9,7 +9,7 @@ with the CUDA path (the two sides only share the seeded input generators in
 Modules:
   sketch   -- the hash-defined sparse-sign embedding S (Section 3, eq. (sketch))
   sdr      -- one cycle of Algorithm 1, the restart driver and the sequence
-              driver of Section 3.5 (exact and inexact recycling)
+              driver of Section 3.6 (exact and inexact recycling)
   adjoint  -- gradients of L = ||x(theta) - x_t||^2 through A(theta) x = b
 """
 from . import sketch, sdr  # noqa: F401

@@ -1,14 +1,14 @@
 """GMRES-SDR in plain FP64, step by step as the paper states it.
 
-Algorithm 1 (one cycle), Section 3.3 (residual control with `safety`),
-Section 3.4 (sketched harmonic Ritz extraction with a truncated SVD and an
-ordered QZ), Section 3.5 (sequences: fixed A with varying b, and the exact and
+Algorithm 1 (one cycle), Section 3.4 (residual control with `safety`),
+Section 3.5 (sketched harmonic Ritz extraction with a truncated SVD and an
+ordered QZ), Section 3.6 (sequences: fixed A with varying b, and the exact and
 inexact variants for varying A).
 
 Readings where the paper is silent or garbled (each one is listed in the
 design notes of the repository):
   * the zero blocks of SV in Algorithm 1 are s x m (printed as N x m);
-  * "SW" in the M_ell line is S[U, V] = [SU, SV(:, 1:j)] (Section 3.4);
+  * "SW" in the M_ell line is S[U, V] = [SU, SV(:, 1:j)] (Section 3.5);
   * after an early break the recycle update uses the j columns actually built;
   * ell = #{sigma_i > sigma_1 * d * eps}, d the number of columns of SAW;
   * QZ of (M_ell, Sigma_ell) is taken through the eigenpairs of
@@ -69,7 +69,7 @@ def sketched_ls(SAW: np.ndarray, Sr0: np.ndarray):
 
 
 def numerical_rank(sig: np.ndarray, d: int) -> int:
-    """ell = #{sigma_i > sigma_1 * d * eps} (truncated economic SVD, Section 3.4)."""
+    """ell = #{sigma_i > sigma_1 * d * eps} (truncated economic SVD, Section 3.5)."""
     if sig.size == 0 or sig[0] == 0.0:
         return 0
     return int(np.count_nonzero(sig > sig[0] * d * EPS))
@@ -78,7 +78,7 @@ def numerical_rank(sig: np.ndarray, d: int) -> int:
 def select_largest(mu: np.ndarray, k: int) -> np.ndarray:
     """Indices of the k eigenvalues of largest modulus (ties: larger real part,
     then lower index), extended by one when the k-th and (k+1)-th are a
-    complex-conjugate pair (Section 3.4 targets the largest-modulus mu)."""
+    complex-conjugate pair (Section 3.5 targets the largest-modulus mu)."""
     idx = np.arange(mu.size)
     order = np.lexsort((idx, -mu.real, -np.abs(mu)))
     kk = min(k, mu.size)
@@ -114,7 +114,7 @@ def invariant_basis(mu: np.ndarray, Y: np.ndarray, sel: np.ndarray) -> np.ndarra
 
 
 def harmonic_ritz_update(SAW, SW, k):
-    """Section 3.4 / Algorithm 1 recycling block.
+    """Section 3.5 / Algorithm 1 recycling block.
 
     Truncated SVD SAW ~ U_l Sigma_l V_l^*, M_l = U_l^* (S[U V]) V_l, ordered QZ
     of (M_l, Sigma_l) with the k largest-modulus eigenvalues first; returns
@@ -211,7 +211,7 @@ def cycle(A, r0, U, SU, SAU, S, tol, m, t, k, safety=1.4, record=False) -> Cycle
             if breakdown:
                 jf = j + 1
                 break
-    # Recycling block (Section 3.4) over the columns actually built.
+    # Recycling block (Section 3.5) over the columns actually built.
     SAW = np.hstack([SAU, SAV[:, :jf]])
     SW = np.hstack([SU, SV[:, :jf]])
     P, hr = harmonic_ritz_update(SAW, SW, k)
@@ -276,7 +276,7 @@ def solve(A, b, S, m, k, t, rel_tol, safety0=1.4, max_cycles=200, U=None, SU=Non
 
 
 def solve_sequence(As, bs, S, m, k, t, rel_tol, exact=True, fixed_matrix=False, **kw):
-    """Section 3.5: carry U, SU, SAU from system i to i+1.
+    """Section 3.6: carry U, SU, SAU from system i to i+1.
 
     fixed_matrix: A is the same for every system, so U, SU, SAU are reused as
     they are.  Otherwise the exact variant recomputes SAU = S A^(i+1) U with k

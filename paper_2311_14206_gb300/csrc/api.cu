@@ -365,7 +365,7 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
   return status;
 }
 
-// Recompute SAU = S A U column by column (exact variant, Section 3.5).
+// Recompute SAU = S A U column by column (exact variant, Section 3.6).
 static sdr_status recompute_sau(sdr_handle* h, const sdr_csr* A, int64_t n) {
   WS ws = h->ws;
   ws.n = n;

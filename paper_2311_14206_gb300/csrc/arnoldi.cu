@@ -5,9 +5,9 @@
 //  k_update_sketch v_hat_{j+1} = w - sum_i H(i,j) v_i (truncated Arnoldi), its
 //                  norm and window dots, and S v_hat_{j+1} (one sketch per step).
 //  k_residual      r = b - A x with ||r|| and S r; applies the residual control
-//                  of Section 3.3 when it serves a true-residual check.
+//                  of Section 3.4 when it serves a true-residual check.
 //  k_check_gemv    x_trial = x + [U V] y_tilde.
-//  k_recycle_gemm  U_new = [U V] P (recycle update, Section 3.4).
+//  k_recycle_gemm  U_new = [U V] P (recycle update, Section 3.5).
 //
 // Basis columns are stored unnormalised (v_hat); alpha_c = 1/||v_hat_c|| lives
 // in the control block and is folded into every coefficient that touches a

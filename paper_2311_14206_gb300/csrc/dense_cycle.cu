@@ -1,5 +1,5 @@
 // Cycle end of GMRES-SDR: sketched harmonic-Ritz update of the recycle space
-// (Section 3.4 and the last block of Algorithm 1), FP64.
+// (Section 3.5 and the last block of Algorithm 1), FP64.
 //
 // With SAW = Q R (the QR kept by the step kernels) and S[U V] the sketched
 // basis, the sketched harmonic Ritz problem is M y = mu y with

@@ -59,7 +59,7 @@ cudaError_t launch_step_dense(const WS& ws, int j, int kh, int ubuf, unsigned lo
 cudaError_t launch_umax(const WS& ws, const double* U, int kdim, int ubuf, cudaStream_t st);
 
 // ---- dense_cycle.cu ----
-// Cycle end: harmonic-Ritz recycling (Section 3.4); P' into ws.P, SU/SAU for the next cycle.
+// Cycle end: harmonic-Ritz recycling (Section 3.5); P' into ws.P, SU/SAU for the next cycle.
 // part 0..8: form C, R^{-1}, M (+ full-rank certificate), truncated SVD (only
 // when not certified), FP32 eigenvalue candidates, FP64 inverse iteration per
 // candidate, selection, basis + P, SU/SAU products.

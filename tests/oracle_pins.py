@@ -3,7 +3,7 @@
 Each pin takes the oracle module (``oracle.sdr`` or a copy with a planted
 mistake) and raises AssertionError when the oracle disagrees with:
   * dense LU (numpy.linalg.solve) on small systems, including a sequence of
-    perturbed systems with exact recycling (Section 3.5);
+    perturbed systems with exact recycling (Section 3.6);
   * GMRES residual norms from an independent Householder-Arnoldi basis and
     numpy.linalg.lstsq when S = I (Section 2.1, eq. (sgmres) with S = I);
   * the augmented minimum-residual problem and the dense harmonic Ritz pencil
@@ -64,7 +64,7 @@ def pin_sequence_lu(sdr):
         xs = np.linalg.solve(W.csr_to_dense(A), b)
         assert o.converged and np.linalg.norm(o.x - xs) / np.linalg.norm(xs) < 1e-8
         # every cycle starts from sketches consistent with the current A^(i):
-        # SU = S U and SAU = S A^(i) U (the exact variant of Section 3.5)
+        # SU = S U and SAU = S A^(i) U (the exact variant of Section 3.6)
         D = W.csr_to_dense(A)
         for c in o.cycle_log:
             U_in = c.info["U_in"]
