@@ -33,7 +33,11 @@ struct Prof {
 struct sdr_handle {
   sdr_params p;
   int64_t n_max;
-  cudaStream_t st;
+  cudaStream_t st;   // the caller's stream: Arnoldi kernels and everything outside a cycle
+  cudaStream_t st2 = nullptr;  // control stream: dense steps and true-residual checks
+  std::vector<cudaEvent_t> evS;  // evS[j]: step j's SpMV (column j sketched and finished)
+  std::vector<cudaEvent_t> evD;  // evD[j]: dense step j and its check
+  cudaEvent_t evFork = nullptr, evJoin = nullptr;
   int device;
   WS ws;
   std::vector<void*> allocs;
@@ -90,7 +94,7 @@ int* ctl_int_field(Ctl* c, size_t off) { return (int*)((char*)c + off); }
 // Kernels issued by each launcher (for the launch count).
 constexpr int kKernelsPerClass[SDR_K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 1, 1, 1, 1, 1, 1, 1, 1, 1};
 
-cudaError_t prof_begin(sdr_handle* h, int cls) {
+cudaError_t prof_begin(sdr_handle* h, int cls, cudaStream_t st) {
   h->launches += kKernelsPerClass[cls];
   if (!h->prof.on) return cudaSuccess;
   Prof& P = h->prof;
@@ -101,12 +105,12 @@ cudaError_t prof_begin(sdr_handle* h, int cls) {
     P.pool.push_back(e);
   }
   P.cls.push_back(cls);
-  return cudaEventRecord(P.pool[2 * (P.cls.size() - 1)], h->st);
+  return cudaEventRecord(P.pool[2 * (P.cls.size() - 1)], st);
 }
 
-cudaError_t prof_end(sdr_handle* h) {
+cudaError_t prof_end(sdr_handle* h, cudaStream_t st) {
   if (!h->prof.on) return cudaSuccess;
-  return cudaEventRecord(h->prof.pool[2 * (h->prof.cls.size() - 1) + 1], h->st);
+  return cudaEventRecord(h->prof.pool[2 * (h->prof.cls.size() - 1) + 1], st);
 }
 
 // Fold the recorded event pairs into the totals (stream must be idle).
@@ -124,12 +128,13 @@ cudaError_t prof_collect(sdr_handle* h) {
   return cudaSuccess;
 }
 
-#define SDR_LAUNCH(h, cls, call)               \
+#define SDR_LAUNCH_ON(h, cls, stream, call)    \
   do {                                         \
-    SDR_CK(prof_begin((h), (cls)));            \
+    SDR_CK(prof_begin((h), (cls), (stream)));  \
     SDR_CK(call);                              \
-    SDR_CK(prof_end(h));                       \
+    SDR_CK(prof_end((h), (stream)));           \
   } while (0)
+#define SDR_LAUNCH(h, cls, call) SDR_LAUNCH_ON(h, cls, (h)->st, call)
 
 }  // namespace
 
@@ -153,7 +158,13 @@ const char* sdr_status_string(sdr_status st) {
 
 sdr_status sdr_destroy(sdr_handle* h) {
   if (!h) return SDR_OK;
+  if (h->st2) cudaStreamSynchronize(h->st2);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->evS) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->evD) cudaEventDestroy(e);
+  if (h->evFork) cudaEventDestroy(h->evFork);
+  if (h->evJoin) cudaEventDestroy(h->evJoin);
+  if (h->st2) cudaStreamDestroy(h->st2);
   for (void* q : h->allocs) cudaFree(q);
   delete h;
   return SDR_OK;
@@ -209,6 +220,19 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   chk(halloc(h, &ws.part, (size_t)ws.grid_max * 2 * NPART));
   chk(halloc(h, &ws.part2, (size_t)ws.grid_max * 2 * NPART));
   chk(halloc(h, &ws.acc, (size_t)6 * S_MAX + 16));
+  chk(halloc(h, &ws.accV, CYCLE_SCRATCH_WORDS));
+  ws.tctr = (int*)(ws.accV + (size_t)(M_MAX + 2) * 2 * S_MAX);
+  chk(halloc(h, &ws.part3, (size_t)ws.grid_max * 2 * NPART));
+  chk(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking));
+  chk(cudaEventCreateWithFlags(&h->evFork, cudaEventDisableTiming));
+  chk(cudaEventCreateWithFlags(&h->evJoin, cudaEventDisableTiming));
+  for (int j = 0; j <= M_MAX + 1 && e == cudaSuccess; ++j) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    chk(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    if (a) h->evS.push_back(a);
+    chk(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    if (b) h->evD.push_back(b);
+  }
   const int s = p->s;
   chk(halloc(h, &ws.SV, (size_t)s * (M_MAX + 1)));
   chk(halloc(h, &ws.SAV, (size_t)s * M_MAX));
@@ -241,6 +265,7 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
     return st;
   }
   chk(cudaMemsetAsync(ws.acc, 0, (6 * S_MAX + 16) * sizeof(unsigned long long), h->st));
+  chk(cudaMemsetAsync(ws.accV, 0, CYCLE_SCRATCH_WORDS * sizeof(unsigned long long), h->st));
   chk(cudaMemsetAsync(ws.ctl, 0, sizeof(Ctl), h->st));
   chk(cudaMemsetAsync(ws.T, 0, (size_t)D_MAX * D_MAX * sizeof(double), h->st));
   chk(cudaMemsetAsync(ws.Rf, 0, (size_t)D_MAX * D_MAX * sizeof(double), h->st));
@@ -270,10 +295,13 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
   WS ws = h->ws;
   ws.n = A->n;
   const CsrDev Ad = to_dev(A);
-  cudaStream_t st = h->st;
+  cudaStream_t st = h->st, st2 = h->st2;
   const int m = ws.m;
   unsigned long long* accR = ws.acc + 2 * S_MAX;
   h->launches = 0;
+  // anything a failed earlier call left on the control stream comes first
+  SDR_CK(cudaEventRecord(h->evJoin, st2));
+  SDR_CK(cudaStreamWaitEvent(st, h->evJoin, 0));
   SDR_LAUNCH(h, SDR_K_SOLVE_INIT, launch_solve_init_x(ws, Ad, b, x, h->p.rel_tol, st));
   double* xcur = x;
   double* xoth = ws.Xw;
@@ -291,23 +319,38 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
     vcol[0] = ws.R[rb];
     for (int c = 1; c <= m; ++c) vcol[c] = ws.Vs + (int64_t)(c - 1) * ws.ldv;
     const int cu = h->cu, kh = h->kh;
-    SDR_LAUNCH(h, SDR_K_CYCLE_INIT, launch_cycle_init(ws, ws.SAU[cu], kh, accR, h->p.persist_safety, st));
-    // Step j's SpMV also sketches v_hat_j, so the dense part of step j-1 (which
-    // needs S v_hat_j) runs after it; the last column is sketched on its own.
+    // Two streams per cycle.  The Arnoldi stream (st) runs the SpMV, sketch
+    // and update of every step; the control stream (st2) runs the one-CTA
+    // dense step of each column and the true-residual check it may call for.
+    // The dense step of column j-1 needs step j's SpMV (which sketches and
+    // finishes column j); step j waits for the control work of column
+    // j - SPEC_LAG, so it knows whether an earlier check ended the cycle.
+    SDR_CK(cudaMemsetAsync(ws.accV, 0, CYCLE_SCRATCH_WORDS * sizeof(unsigned long long), st));
+    SDR_LAUNCH(h, SDR_K_CYCLE_INIT, launch_cycle_head(ws, kh, accR, h->p.persist_safety, st));
+    SDR_CK(cudaEventRecord(h->evFork, st));
+    SDR_CK(cudaStreamWaitEvent(st2, h->evFork, 0));
+    SDR_LAUNCH_ON(h, SDR_K_CYCLE_INIT, st2, launch_cycle_qr(ws, ws.SAU[cu], kh, st2));
     for (int j = 0; j <= m; ++j) {
+      if (j >= SPEC_LAG) SDR_CK(cudaStreamWaitEvent(st, h->evD[j - SPEC_LAG], 0));
       if (j < m) {
         SDR_LAUNCH(h, SDR_K_SPMV_DOTS, launch_spmv_dots(ws, Ad, vcol.data(), j, st));
       } else {
         SDR_LAUNCH(h, SDR_K_SKETCH, launch_sketch_col(ws, vcol[m], m, st));
       }
       if (j >= 1) {
-        SDR_LAUNCH(h, SDR_K_STEP_DENSE, launch_step_dense(ws, j - 1, kh, cu, accR, st));
-        SDR_LAUNCH(h, SDR_K_CHECK_GEMV,
-                   launch_check_gemv(ws, ws.U[cu], vcol.data(), xcur, xoth, kh, j - 1, cu, st));
-        SDR_LAUNCH(h, SDR_K_CHECK_RESIDUAL, launch_residual(ws, Ad, b, xoth, ws.R[1 - rb], accR, j - 1, 1, st));
+        SDR_CK(cudaEventRecord(h->evS[j], st));
+        SDR_CK(cudaStreamWaitEvent(st2, h->evS[j], 0));
+        SDR_LAUNCH_ON(h, SDR_K_STEP_DENSE, st2, launch_step_dense(ws, j - 1, kh, cu, accR, st2));
+        SDR_LAUNCH_ON(h, SDR_K_CHECK_GEMV, st2,
+                      launch_check_gemv(ws, ws.U[cu], vcol.data(), xcur, xoth, kh, j - 1, cu, st2));
+        SDR_LAUNCH_ON(h, SDR_K_CHECK_RESIDUAL, st2,
+                      launch_residual(ws, Ad, b, xoth, ws.R[1 - rb], accR, j - 1, 1, st2));
+        SDR_CK(cudaEventRecord(h->evD[j - 1], st2));
       }
       if (j < m) SDR_LAUNCH(h, SDR_K_UPDATE_SKETCH, launch_update_sketch(ws, vcol.data(), (double*)vcol[j + 1], j, st));
     }
+    SDR_CK(cudaEventRecord(h->evJoin, st2));
+    SDR_CK(cudaStreamWaitEvent(st, h->evJoin, 0));
     for (int part = 0; part < CYCLE_END_PARTS; ++part)
       SDR_LAUNCH(h, part == 0 ? SDR_K_CYCLE_END : SDR_K_CE_RINV + part - 1,
                  launch_cycle_end_part(part, ws, kh, cu, ws.SU[cu], ws.SAU[cu], ws.SU[1 - cu], ws.SAU[1 - cu], st));
@@ -325,7 +368,7 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
       if (hc.svd_path) ++full_svd;
     }
     converged = hc.converged != 0;
-    if (!converged && hc.breakdown) {
+    if (!converged && hc.bd_dense) {
       status = SDR_ERR_BREAKDOWN;
       break;
     }
@@ -375,12 +418,12 @@ static sdr_status recompute_sau(sdr_handle* h, const sdr_csr* A, int64_t n) {
   h->launches = 0;
   for (int c = 0; c < h->kh; ++c) {
     const double* u = ws.U[h->cu] + (int64_t)c * ws.ldv;
-    SDR_CK(prof_begin(h, SDR_K_RECYCLE_SAU));
+    SDR_CK(prof_begin(h, SDR_K_RECYCLE_SAU, h->st));
     SDR_CK(launch_spmv(Ad, u, h->d_tmp, h->st));
     SDR_CK(launch_maxabs_top(ws, h->d_tmp, n, topG, h->st));
     SDR_CK(launch_sketch_vec(ws, h->d_tmp, n, accG, topG, h->st));
     SDR_CK(launch_sketch_finish(ws, accG, topG, ws.SAU[h->cu] + (int64_t)c * ws.s, h->st));
-    SDR_CK(prof_end(h));
+    SDR_CK(prof_end(h, h->st));
   }
   SDR_CK(cudaStreamSynchronize(h->st));
   SDR_CK(prof_collect(h));
@@ -394,12 +437,12 @@ static sdr_status recompute_su(sdr_handle* h, int64_t n) {
   int* topG = ctl_int_field(ws.ctl, offsetof(Ctl, accG_top));
   for (int c = 0; c < h->kh; ++c) {
     const double* u = ws.U[h->cu] + (int64_t)c * ws.ldv;
-    SDR_CK(prof_begin(h, SDR_K_SKETCH));
+    SDR_CK(prof_begin(h, SDR_K_SKETCH, h->st));
     h->launches += 2;  // three kernels under one timing bracket
     SDR_CK(launch_maxabs_top(ws, u, n, topG, h->st));
     SDR_CK(launch_sketch_vec(ws, u, n, accG, topG, h->st));
     SDR_CK(launch_sketch_finish(ws, accG, topG, ws.SU[h->cu] + (int64_t)c * ws.s, h->st));
-    SDR_CK(prof_end(h));
+    SDR_CK(prof_end(h, h->st));
   }
   SDR_CK(cudaStreamSynchronize(h->st));
   SDR_CK(prof_collect(h));
@@ -426,12 +469,12 @@ sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y) {
   unsigned long long* accG = ws.acc + 4 * S_MAX;
   int* topG = ctl_int_field(ws.ctl, offsetof(Ctl, accG_top));
   h->launches = 0;
-  SDR_CK(prof_begin(h, SDR_K_SKETCH));
+  SDR_CK(prof_begin(h, SDR_K_SKETCH, h->st));
   h->launches += 2;  // three kernels under one timing bracket
   SDR_CK(launch_maxabs_top(ws, x, n, topG, h->st));
   SDR_CK(launch_sketch_vec(ws, x, n, accG, topG, h->st));
   SDR_CK(launch_sketch_finish(ws, accG, topG, y, h->st));
-  SDR_CK(prof_end(h));
+  SDR_CK(prof_end(h, h->st));
   SDR_CK(cudaStreamSynchronize(h->st));
   SDR_CK(prof_collect(h));
   return SDR_OK;

@@ -137,7 +137,8 @@ cudaError_t launch_solve_init_x(const WS& ws, CsrDev A, const double* b, const d
 // then applies Algorithm 1's residual control in the last CTA.
 // ---------------------------------------------------------------------------
 __global__ void k_residual(WS ws, CsrDev A, const double* __restrict__ b, const double* __restrict__ x,
-                           double* __restrict__ rout, unsigned long long* accR, int j, int mode) {
+                           double* __restrict__ rout, unsigned long long* accR, int j, int mode,
+                           double* __restrict__ part, unsigned int* counter) {
   Ctl* c = ws.ctl;
   if (mode == 1 && !c->check) return;
   extern __shared__ unsigned char smem[];
@@ -181,19 +182,19 @@ __global__ void k_residual(WS ws, CsrDev A, const double* __restrict__ b, const 
   nrm = block_sum(nrm, red);
   rm = block_max_u64(rm, redu);
   if (threadIdx.x == 0) {
-    ws.part[blockIdx.x * NPART + 0] = nrm;
-    ws.part[blockIdx.x * NPART + 1] = __longlong_as_double((long long)rm);
+    part[blockIdx.x * NPART + 0] = nrm;
+    part[blockIdx.x * NPART + 1] = __longlong_as_double((long long)rm);
   }
-  if (last_block(&c->counter)) {
-    double s = reduce_parts(ws.part, gridDim.x, 0, red);
-    unsigned long long m = reduce_parts_max(ws.part, gridDim.x, 1, redu);
+  if (last_block(counter)) {
+    double s = reduce_parts(part, gridDim.x, 0, red);
+    unsigned long long m = reduce_parts_max(part, gridDim.x, 1, redu);
     if (threadIdx.x == 0) {
       double res = sqrt(s);
       c->res = res;
       c->rmax = m;
       c->accR_top = top;
-      c->matvecs += 1;
-      c->sketches += 1;
+      atomicAdd(&c->matvecs, 1);
+      atomicAdd(&c->sketches, 1);
       if (mode == 1) {
         c->nchecks += 1;
         c->check = 0;
@@ -201,11 +202,13 @@ __global__ void k_residual(WS ws, CsrDev A, const double* __restrict__ b, const 
           c->converged = 1;
           c->done = 1;
           c->jf = j + 1;
+          c->jstop = j + 1;
         } else {
           c->safety = c->sres > 0.0 ? res / c->sres : c->safety;  // increase the safety factor
-          if (j == ws.m - 1 || c->breakdown) {
+          if (j == ws.m - 1 || c->bd_dense) {
             c->done = 1;
             c->jf = j + 1;
+            c->jstop = j + 1;
           }
         }
       } else {
@@ -237,7 +240,11 @@ cudaError_t launch_residual(const WS& ws, CsrDev A, const double* b, const doubl
   static bool attr = false;
   cudaError_t e = set_smem((const void*)k_residual, sketch_smem_bytes(ZETA_MAX), attr);
   if (e != cudaSuccess) return e;
-  k_residual<<<grid_tiles(ws, A.n), SK_THREADS, sm, st>>>(ws, A, b, x, rout, accR, j, mode);
+  // the check (mode 1) runs on the control stream beside the Arnoldi kernels:
+  // it reduces through its own partials and counter
+  double* part = mode == 1 ? ws.part3 : ws.part;
+  unsigned int* counter = mode == 1 ? &ws.ctl->counter2 : &ws.ctl->counter;
+  k_residual<<<grid_tiles(ws, A.n), SK_THREADS, sm, st>>>(ws, A, b, x, rout, accR, j, mode, part, counter);
   return cudaGetLastError();
 }
 
@@ -291,7 +298,7 @@ __device__ void finish_column(const WS& ws, int j, int grid2, double* buf, unsig
 template <int NW, bool SK>  // NW window vectors v_hat_lo .. v_hat_j; SK: sketch v_hat_j
 __global__ void __launch_bounds__(SK_THREADS) k_spmv_dots(WS ws, CsrDev A, Win win, int j, int grid2) {
   Ctl* c = ws.ctl;
-  if (c->done) return;
+  if (arnoldi_stopped(c, j)) return;
   extern __shared__ unsigned char smem[];
   const int tileR = sketch_tile_rows(ws.zeta);
   double* vals = (double*)smem;
@@ -314,7 +321,15 @@ __global__ void __launch_bounds__(SK_THREADS) k_spmv_dots(WS ws, CsrDev A, Win w
   const double* __restrict__ va = A.val;
   const int64_t n = A.n;
   const int ntiles = (int)((n + tileR - 1) / tileR);
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  // Tiles are handed out by a counter, so CTAs that start late (an SM shared
+  // with the dense step on the other stream) take fewer tiles.
+  __shared__ int next_tile;
+  int* __restrict__ tctr = ws.tctr + j;
+  if (threadIdx.x == 0) next_tile = atomicAdd(tctr, 1);
+  __syncthreads();
+  for (int tile = next_tile; tile < ntiles; tile = next_tile) {
+    __syncthreads();  // every thread holds this tile's index before it is replaced
+    if (threadIdx.x == 0) next_tile = atomicAdd(tctr, 1);
     const int64_t r0 = (int64_t)tile * tileR;
     const int ncols = (int)(n - r0 < (int64_t)tileR ? n - r0 : (int64_t)tileR);
     if (SK) tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
@@ -333,12 +348,13 @@ __global__ void __launch_bounds__(SK_THREADS) k_spmv_dots(WS ws, CsrDev A, Win w
       if (SK) vals[i] = xv;
     }
     if (SK) tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
+    __syncthreads();  // next_tile is published
   }
   if (SK) {
 #pragma unroll
     for (int k = 0; k < SK_RPT; ++k) {
       const int row = threadIdx.x + k * blockDim.x;
-      if (row < ws.s) atomic_add128(ws.acc + 2 * row, lo[k], hi[k]);
+      if (row < ws.s) atomic_add128(ws.accV + (int64_t)j * 2 * S_MAX + 2 * row, lo[k], hi[k]);
     }
   }
 #pragma unroll
@@ -386,8 +402,8 @@ __global__ void __launch_bounds__(SK_THREADS) k_spmv_dots(WS ws, CsrDev A, Win w
       }
       c->wmax = wmx;
       c->vtop[j + 1] = window_top(bound * (1.0 + 1e-12), ws.win_bits);
-      c->matvecs += 1;
-      if (SK) c->sketches += 1;
+      atomicAdd(&c->matvecs, 1);
+      if (SK) atomicAdd(&c->sketches, 1);
     }
   }
 }
@@ -425,7 +441,7 @@ cudaError_t launch_spmv_dots(const WS& ws, CsrDev A, const double* const* vcol, 
 // column's finish.
 __global__ void __launch_bounds__(SK_THREADS) k_sketch_col(WS ws, const double* __restrict__ x, int j, int grid2) {
   Ctl* c = ws.ctl;
-  if (c->done) return;
+  if (arnoldi_stopped(c, j)) return;
   extern __shared__ unsigned char smem[];
   const int tileR = sketch_tile_rows(ws.zeta);
   double* vals = (double*)smem;
@@ -449,11 +465,11 @@ __global__ void __launch_bounds__(SK_THREADS) k_sketch_col(WS ws, const double* 
 #pragma unroll
   for (int k = 0; k < SK_RPT; ++k) {
     const int row = threadIdx.x + k * blockDim.x;
-    if (row < ws.s) atomic_add128(ws.acc + 2 * row, lo[k], hi[k]);
+    if (row < ws.s) atomic_add128(ws.accV + (int64_t)j * 2 * S_MAX + 2 * row, lo[k], hi[k]);
   }
   if (last_block(&c->counter)) {
     finish_column(ws, j, grid2, buf, redu);
-    if (threadIdx.x == 0) c->sketches += 1;
+    if (threadIdx.x == 0) atomicAdd(&c->sketches, 1);
   }
 }
 
@@ -473,7 +489,7 @@ cudaError_t launch_sketch_col(const WS& ws, const double* x, int j, cudaStream_t
 template <int NW, int NC>  // NW window vectors, NC = t - 1 dots kept for the next window
 __global__ void __launch_bounds__(256) k_update(WS ws, Win win, double* __restrict__ vnext, int j) {
   Ctl* c = ws.ctl;
-  if (c->done) return;
+  if (arnoldi_stopped(c, j)) return;
   __shared__ double buf[256];
   __shared__ unsigned long long redu[32];
   double cf[NW + 1];

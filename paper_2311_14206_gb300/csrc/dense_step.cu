@@ -168,14 +168,13 @@ __device__ double qr_add_column(const WS& ws, int p, QrSmem& sm, int* rank_flag)
 }
 
 // ---------------------------------------------------------------------------
-// Cycle start (Algorithm 1, before the Arnoldi loop): S r0 from the residual
-// accumulators, beta = ||r0||, V(:,1) and SV(:,1) scales, z = S r0, and the QR
-// of the kh recycled columns SAU.
+// Cycle start (Algorithm 1, before the Arnoldi loop), in two kernels.
+// k_cycle_head (Arnoldi stream): S r0 from the residual accumulators,
+// beta = ||r0||, the scale of V(:,1), SV(:,1), z = S r0 and the control flags.
+// k_cycle_qr (control stream): the QR of the kh recycled columns SAU, which
+// only the dense steps need, so the first Arnoldi steps run beside it.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(DT) k_cycle_init(WS ws, const double* __restrict__ SAU, int kh,
-                                                   unsigned long long* accR, int persist_safety) {
-  __shared__ QrSmem sm;
-  __shared__ int rank_flag;
+__global__ void __launch_bounds__(DT) k_cycle_head(WS ws, int kh, unsigned long long* accR, int persist_safety) {
   Ctl* c = ws.ctl;
   const int s = ws.s;
   const double beta = c->res;
@@ -184,14 +183,11 @@ __global__ void __launch_bounds__(DT) k_cycle_init(WS ws, const double* __restri
     double v = int128_to_double(accR[2 * i], accR[2 * i + 1], top - 126) * ws.inv_sqrt_zeta;
     accR[2 * i] = 0ull;
     accR[2 * i + 1] = 0ull;
-    ws.acc[2 * i] = 0ull;  // a cycle that stopped early can leave a speculative sketch here
-    ws.acc[2 * i + 1] = 0ull;
     ws.Sr0[i] = v;
-    sm.z[i] = v;
+    ws.z[i] = v;
     ws.SV[i] = beta > 0.0 ? v / beta : 0.0;
   }
   if (threadIdx.x == 0) {
-    rank_flag = 0;
     c->alpha[0] = beta > 0.0 ? 1.0 / beta : 0.0;
     c->vmax[0] = c->rmax;
     c->beta = beta;
@@ -201,6 +197,7 @@ __global__ void __launch_bounds__(DT) k_cycle_init(WS ws, const double* __restri
     c->step = 0;
     c->nchecks = 0;
     c->breakdown = 0;
+    c->bd_dense = 0;
     c->rankfail = 0;
     c->kprime = 0;
     c->ell = 0;
@@ -208,7 +205,17 @@ __global__ void __launch_bounds__(DT) k_cycle_init(WS ws, const double* __restri
     if (!persist_safety) c->safety = c->safety0;
     c->converged = beta < c->tol ? 1 : 0;
     c->done = c->converged;
+    c->jstop = c->converged ? -(1 << 20) : (1 << 20);
   }
+}
+
+__global__ void __launch_bounds__(DT) k_cycle_qr(WS ws, const double* __restrict__ SAU, int kh) {
+  __shared__ QrSmem sm;
+  __shared__ int rank_flag;
+  Ctl* c = ws.ctl;
+  const int s = ws.s;
+  if (threadIdx.x == 0) rank_flag = 0;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) sm.z[i] = ws.z[i];
   __syncthreads();
   double sres = 0.0;
   {
@@ -229,9 +236,13 @@ __global__ void __launch_bounds__(DT) k_cycle_init(WS ws, const double* __restri
   }
 }
 
-cudaError_t launch_cycle_init(const WS& ws, const double* SAU, int kh, unsigned long long* accR,
-                              int persist_safety, cudaStream_t st) {
-  k_cycle_init<<<1, DT, 0, st>>>(ws, SAU, kh, accR, persist_safety);
+cudaError_t launch_cycle_head(const WS& ws, int kh, unsigned long long* accR, int persist_safety, cudaStream_t st) {
+  k_cycle_head<<<1, DT, 0, st>>>(ws, kh, accR, persist_safety);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cycle_qr(const WS& ws, const double* SAU, int kh, cudaStream_t st) {
+  k_cycle_qr<<<1, DT, 0, st>>>(ws, SAU, kh);
   return cudaGetLastError();
 }
 
@@ -256,6 +267,7 @@ __global__ void __launch_bounds__(DT) k_step_dense(WS ws, int j, int kh, int ubu
     rank_flag = 0;
     sh_alpha = c->alpha[j + 1];
     for (int o = 0; o <= T_MAX; ++o) hcol[o] = o <= t ? c->hband[j][o] : 0.0;
+    c->bd_dense = breakdown ? 1 : 0;
     if (breakdown) {
       hcol[t] = 0.0;
       c->breakdown = 1;
@@ -265,10 +277,11 @@ __global__ void __launch_bounds__(DT) k_step_dense(WS ws, int j, int kh, int ubu
   // 2. S v_hat_{j+1} from the accumulators; SV(:, j+1); 3. SAV(:, j)
   const int top = c->vtop[j + 1];
   const double a1 = sh_alpha;
+  unsigned long long* __restrict__ acc = ws.accV + (int64_t)(j + 1) * 2 * S_MAX;  // S v_hat_{j+1}
   for (int i = threadIdx.x; i < s; i += blockDim.x) {
-    double raw = int128_to_double(ws.acc[2 * i], ws.acc[2 * i + 1], top - 126) * ws.inv_sqrt_zeta;
-    ws.acc[2 * i] = 0ull;
-    ws.acc[2 * i + 1] = 0ull;
+    double raw = int128_to_double(acc[2 * i], acc[2 * i + 1], top - 126) * ws.inv_sqrt_zeta;
+    acc[2 * i] = 0ull;
+    acc[2 * i + 1] = 0ull;
     if (breakdown) raw = 0.0;
     ws.SV[i + (int64_t)(j + 1) * s] = raw * a1;
     // SAV(:, j) = SV(:, 1:j+1) H(1:j+1, j) over the band; H(j+1,j) SV(:,j+1) = raw
@@ -290,7 +303,7 @@ __global__ void __launch_bounds__(DT) k_step_dense(WS ws, int j, int kh, int ubu
     c->hist_n += 1;
     c->sres = sres;
     c->step = j + 1;
-    c->sketches += 1;
+    atomicAdd(&c->sketches, 1);
     if (rank_flag) c->rankfail = 1;
     do_check = (sres < c->tol / c->safety) || (j == ws.m - 1) || breakdown;
     c->check = do_check;

@@ -50,9 +50,10 @@ int update_grid(const WS& ws);
 cudaError_t launch_sketch_col(const WS& ws, const double* x, int j, cudaStream_t st);
 
 // ---- dense_step.cu ----
-// Cycle start: Sr0, beta, SV(:,0), QR of SAU (kh columns).
-cudaError_t launch_cycle_init(const WS& ws, const double* SAU, int kh, unsigned long long* accR,
-                              int persist_safety, cudaStream_t st);
+// Cycle start on the Arnoldi stream: Sr0, beta, SV(:,0), z = Sr0, control flags.
+cudaError_t launch_cycle_head(const WS& ws, int kh, unsigned long long* accR, int persist_safety, cudaStream_t st);
+// Cycle start on the control stream: QR of SAU (kh columns), z and sres.
+cudaError_t launch_cycle_qr(const WS& ws, const double* SAU, int kh, cudaStream_t st);
 // Arnoldi step j, small dense part: h(j+1,j), SV(:,j+1), SAV(:,j), QR update, sres, control.
 cudaError_t launch_step_dense(const WS& ws, int j, int kh, int ubuf, unsigned long long* accR, cudaStream_t st);
 // max |U(:, l)| of kdim columns into ctl->umax[ubuf] (after an import).

@@ -40,8 +40,10 @@ struct Ctl {
   int log_n;      // logged cycles so far in this solve
   int matvecs, sketches;
   int persist_safety;
-  unsigned int counter;   // last-CTA counter for grid reductions
-  unsigned int counter2;
+  unsigned int counter;   // last-CTA counter for grid reductions on the Arnoldi stream
+  unsigned int counter2;  // the same for the reductions of the dense (control) stream
+  int jstop;      // jf of the check that ended the cycle (large while it runs)
+  int bd_dense;   // the dense step of the current column saw H(j+1, j) = 0
   double alpha[M_MAX + 2];                // 1 / ||v_hat_c||
   int vtop[M_MAX + 2];                    // window top for the sketch of v_hat_c
   unsigned long long vmax[M_MAX + 2];     // bits of max |v_hat_c|
@@ -52,6 +54,17 @@ struct Ctl {
   double coef[T_MAX + 1];                 // a_0 (w) and a_1.. (window) for the update
   double hnext_sq;                        // ||v_hat_{j+1}||^2 (reduced in the dense step)
 };
+
+// The Arnoldi kernels of step j run while the dense step and the true-residual
+// check of earlier columns run on a second stream.  The Arnoldi stream waits
+// for the control work of column j - SPEC_LAG before step j, so a check that
+// stopped the cycle at jf <= j - SPEC_LAG + 1 is final when step j starts, and
+// any check still running can only set a larger jf: every CTA of a step sees
+// the same answer.  Steps past the stop compute columns that nothing reads.
+constexpr int SPEC_LAG = 3;
+// Words of the per-cycle block that holds the column accumulators and the tile counters.
+constexpr size_t CYCLE_SCRATCH_WORDS = (size_t)(M_MAX + 2) * 2 * S_MAX + (M_MAX + 2);
+__device__ __forceinline__ bool arnoldi_stopped(const Ctl* c, int j) { return c->jstop <= j - SPEC_LAG + 1; }
 
 // Per-cycle log entry kept on the device, mirrored by sdr_cycle_log.
 struct CycleLog {
@@ -81,6 +94,9 @@ struct WS {
   double* part;             // [grid_max][NPART]
   double* part2;            // [grid_max][NPART] partials of the Arnoldi update
   unsigned long long* acc;  // 128-bit accumulators, acc[2*i] = lo, acc[2*i+1] = hi
+  unsigned long long* accV; // one accumulator block (2 * S_MAX words) per basis column c = 0 .. M_MAX+1
+  int* tctr;                // per-step tile counters of the SpMV (dynamic tile scheduling), M_MAX+2
+  double* part3;            // [grid_max][NPART] partials of the control-stream reductions
   int grid_max;
   // small dense (column-major)
   double* SV;    // s x (m+1)
