@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define SDR_ABI_VERSION 1
+#define SDR_ABI_VERSION 2
 
 typedef struct sdr_handle sdr_handle; /* opaque */
 
@@ -66,7 +66,23 @@ typedef enum {
  *   max_cycles restart cycles per sdr_solve call (>= 1).
  *   persist_safety 0: safety restarts from safety0 every cycle;
  *                  1: it carries over within one sdr_solve call.
+ *   precision  SDR_PREC_F64: everything in float64.
+ *              SDR_PREC_F32_REFINED: the basis V, U, the SpMV, the window
+ *              dots, the Arnoldi update and the sketched vectors are float32
+ *              (float32 accumulation; the sketch sums stay exact), the small
+ *              sketched QR / least squares and the harmonic-Ritz eigenproblem
+ *              stay float64, and sdr_solve wraps the float32 solver in a
+ *              float64 iterative refinement: r = b - A x in float64, solve
+ *              A d = r in float32 to inner_rel_tol, x += d, until
+ *              ||b - A x|| < rel_tol ||b|| (max_cycles bounds the inner
+ *              cycles of each refinement step; at most 40 steps).
+ *   inner_rel_tol  refined form: relative tolerance of each inner solve
+ *              (0 selects 1e-4).
+ *   test_flags bit 0: take the truncated-SVD path of the harmonic-Ritz step
+ *              even when the full-rank certificate holds (for tests).
  */
+#define SDR_PREC_F64 0
+#define SDR_PREC_F32_REFINED 1
 typedef struct {
   int32_t m, k, t, s, zeta;
   uint64_t seed;
@@ -74,7 +90,10 @@ typedef struct {
   double safety0;
   int32_t max_cycles;
   int32_t persist_safety;
-  int32_t reserved[6]; /* must be zero */
+  int32_t precision;
+  int32_t test_flags;
+  double inner_rel_tol;
+  int32_t reserved[4]; /* must be zero */
 } sdr_params;
 
 /* Square CSR matrix; all pointers are device pointers owned by the caller. */
@@ -83,6 +102,8 @@ typedef struct {
   const int32_t* rowptr; /* n + 1 entries */
   const int32_t* col;    /* nnz entries */
   const double* val;     /* nnz entries */
+  const float* val32;    /* nnz entries, float32 copy of val: needed by sdr_solve and
+                            sdr_recycle of an SDR_PREC_F32_REFINED handle, else NULL */
 } sdr_csr;
 
 /* Statistics of the last sdr_solve (host struct filled by the library). */
@@ -96,7 +117,7 @@ typedef struct {
   int32_t recycle_dim;     /* columns of U after the solve */
   int32_t full_svd_cycles; /* cycles that needed the truncated-SVD path */
   int32_t kernel_launches; /* kernels of this library launched by the call */
-  int32_t reserved_i;
+  int32_t refinements;     /* SDR_PREC_F32_REFINED: float64 refinement steps (0 otherwise) */
   double final_res;        /* last true residual norm */
   double tol;              /* rel_tol * ||b|| */
   double final_rel_res;    /* final_res / ||b|| */
@@ -206,9 +227,9 @@ sdr_status sdr_recycle_import(sdr_handle* h, const sdr_csr* A, int64_t n, int32_
 enum {
   SDR_K_SOLVE_INIT = 0,   /* ||b||, max|b|, ||A||_inf at the start of a solve */
   SDR_K_RESIDUAL0,        /* initial residual b - A x0 with its sketch */
-  SDR_K_CYCLE_INIT,       /* S r0, beta, QR of SAU (Algorithm 1 set-up) */
+  SDR_K_CYCLE_INIT,       /* S r0, beta (first launch), QR of SAU (second launch): Algorithm 1 set-up */
   SDR_K_SPMV_DOTS,        /* w = A v_j with truncation-window dots */
-  SDR_K_UPDATE_SKETCH,    /* truncated-Arnoldi update with the fused sketch */
+  SDR_K_UPDATE_SKETCH,    /* truncated-Arnoldi update (the next SpMV sketches its output) */
   SDR_K_STEP_DENSE,       /* QR update of SAW, sketched residual, control */
   SDR_K_CHECK_GEMV,       /* x_trial = x + [U V] y (launched every step, works on checks) */
   SDR_K_CHECK_RESIDUAL,   /* true residual of x_trial (launched every step, works on checks) */
@@ -224,6 +245,7 @@ enum {
   SDR_K_CE_SELECT,        /* cycle end: selection of the k largest |mu| */
   SDR_K_CE_FINISH,        /* cycle end: orthonormal basis Z and P */
   SDR_K_CE_SKETCHES,      /* cycle end: SU, SAU of the new recycle space */
+  SDR_K_REFINE,           /* refined form: float32 right-hand side and the float64 update x += d */
   SDR_K_COUNT
 };
 

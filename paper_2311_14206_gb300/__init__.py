@@ -6,6 +6,8 @@ sketched least-squares solve and sketched harmonic-Ritz recycling, each step
 a hand-written sm_103a kernel.
 """
 from .sdr import (  # noqa: F401
+    SDR_PREC_F32_REFINED,
+    SDR_PREC_F64,
     CSRDevice,
     Solver,
     SdrError,

@@ -50,6 +50,9 @@ struct sdr_handle {
   double* d_tmp = nullptr;  // n_max scratch vector (A u)
   Prof prof;
   int launches = 0;  // kernels launched by the current call
+  int prec = SDR_PREC_F64;   // storage type of the tall arrays: double, or float (refined form)
+  void* rhs32 = nullptr;     // refined form: float32 right-hand side of the inner solve
+  void* dx32 = nullptr;      // refined form: float32 inner solution
 };
 
 namespace {
@@ -84,15 +87,21 @@ int ceil_log2(int64_t v) {
 
 bool csr_ok(const sdr_handle* h, const sdr_csr* A) {
   return A && A->n > 0 && A->n <= h->n_max && A->nnz >= 0 && A->rowptr && A->col && A->val &&
-         A->nnz < ((int64_t)1 << 31);
+         A->nnz < ((int64_t)1 << 31) && (h->prec == SDR_PREC_F64 || A->val32);
 }
 
-CsrDev to_dev(const sdr_csr* A) { return CsrDev{A->n, A->nnz, A->rowptr, A->col, A->val}; }
+CsrDev to_dev(const sdr_csr* A) { return CsrDev{A->n, A->nnz, A->rowptr, A->col, A->val, A->val32}; }
+
+// Column c of a tall array of element type T with leading dimension ld.
+template <typename T>
+T* tall_col(void* base, int64_t ld, int64_t c) {
+  return (T*)base + c * ld;
+}
 
 int* ctl_int_field(Ctl* c, size_t off) { return (int*)((char*)c + off); }
 
 // Kernels issued by each launcher (for the launch count).
-constexpr int kKernelsPerClass[SDR_K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+constexpr int kKernelsPerClass[SDR_K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
 
 cudaError_t prof_begin(sdr_handle* h, int cls, cudaStream_t st) {
   h->launches += kKernelsPerClass[cls];
@@ -177,9 +186,13 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   if (p->s > S_MAX || p->s < p->m + p->k + 2 || p->zeta < 1 || p->zeta > p->s || p->zeta > ZETA_MAX)
     return SDR_ERR_INVALID_ARG;
   if (!(p->rel_tol > 0.0) || !(p->safety0 >= 1.0) || p->max_cycles < 1) return SDR_ERR_INVALID_ARG;
+  if (p->precision != SDR_PREC_F64 && p->precision != SDR_PREC_F32_REFINED) return SDR_ERR_INVALID_ARG;
+  if (!(p->inner_rel_tol >= 0.0 && p->inner_rel_tol < 1.0)) return SDR_ERR_INVALID_ARG;
   if (n_max >= ((int64_t)1 << 31)) return SDR_ERR_INVALID_ARG;
   sdr_handle* h = new sdr_handle();
   h->p = *p;
+  if (!(h->p.inner_rel_tol > 0.0)) h->p.inner_rel_tol = 1e-4;
+  h->prec = p->precision;
   h->n_max = n_max;
   h->st = (cudaStream_t)stream;
   cudaGetDevice(&h->device);
@@ -202,14 +215,25 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   const int64_t N = n_max;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
-  chk(halloc(h, &ws.Vs, (size_t)N * p->m));
-  chk(halloc(h, &ws.R[0], (size_t)N));
-  chk(halloc(h, &ws.R[1], (size_t)N));
-  chk(halloc(h, &ws.Wv, (size_t)N));
-  chk(halloc(h, &ws.Xw, (size_t)N));
-  chk(halloc(h, &ws.U[0], (size_t)N * ws.kmax));
-  chk(halloc(h, &ws.U[1], (size_t)N * ws.kmax));
-  chk(halloc(h, &h->d_tmp, (size_t)N));
+  // tall arrays in the storage type (8 or 4 bytes per element)
+  const size_t esz = h->prec == SDR_PREC_F64 ? sizeof(double) : sizeof(float);
+  auto tall = [&](void** q, size_t count) {
+    unsigned char* b = nullptr;
+    chk(halloc(h, &b, count * esz));
+    *q = b;
+  };
+  tall(&ws.Vs, (size_t)N * p->m);
+  tall(&ws.R[0], (size_t)N);
+  tall(&ws.R[1], (size_t)N);
+  tall(&ws.Wv, (size_t)N);
+  tall(&ws.Xw, (size_t)N);
+  tall(&ws.U[0], (size_t)N * ws.kmax);
+  tall(&ws.U[1], (size_t)N * ws.kmax);
+  chk(halloc(h, &h->d_tmp, (size_t)N));  // float64 scratch (A u, and the outer residual)
+  if (h->prec == SDR_PREC_F32_REFINED) {
+    tall(&h->rhs32, (size_t)N);
+    tall(&h->dx32, (size_t)N);
+  }
   const int tileR = sketch_tile_rows(p->zeta);
   const int64_t ntiles = (N + tileR - 1) / tileR;
   ws.ntiles = (int)ntiles;
@@ -276,7 +300,7 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
     init.safety0 = p->safety0;
     init.safety = p->safety0;
     init.persist_safety = p->persist_safety;
-    init.force_svd = p->reserved[0] == 1 ? 1 : 0;
+    init.force_svd = (p->test_flags & 1) ? 1 : 0;
     chk(cudaMemcpyAsync(ws.ctl, &init, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
   }
   chk(launch_sketch_build(ws, N, h->sk_ent, h->sk_ptr, h->st));
@@ -290,35 +314,48 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   return SDR_OK;
 }
 
-sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x, sdr_stats* stats) {
-  if (!h || !csr_ok(h, A) || !b || !x) return SDR_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// Outcome of a run of restart cycles (one sdr_solve of the float64 solver, or
+// one inner solve of the refined form).
+struct CycleRun {
+  int cycles = 0, full_svd = 0;
+  bool converged = false;
+  sdr_status status = SDR_OK;
+  Ctl hc;
+};
+
+// Restarted GMRES-SDR on A x = b with tall vectors of type T, from the
+// iterate in x, for at most max_cycles cycles; x is overwritten with the
+// result.  tol = rel_tol ||b||.
+template <typename T>
+sdr_status run_cycles(sdr_handle* h, const CsrDev& Ad, const T* b, T* x, double rel_tol, int max_cycles,
+                      CycleRun& out) {
   WS ws = h->ws;
-  ws.n = A->n;
-  const CsrDev Ad = to_dev(A);
+  ws.n = Ad.n;
   cudaStream_t st = h->st, st2 = h->st2;
   const int m = ws.m;
   unsigned long long* accR = ws.acc + 2 * S_MAX;
-  h->launches = 0;
-  // anything a failed earlier call left on the control stream comes first
-  SDR_CK(cudaEventRecord(h->evJoin, st2));
-  SDR_CK(cudaStreamWaitEvent(st, h->evJoin, 0));
-  SDR_LAUNCH(h, SDR_K_SOLVE_INIT, launch_solve_init_x(ws, Ad, b, x, h->p.rel_tol, st));
-  double* xcur = x;
-  double* xoth = ws.Xw;
+  SDR_LAUNCH(h, SDR_K_SOLVE_INIT, launch_solve_init_x<T>(ws, Ad, b, x, rel_tol, st));
+  T* xcur = x;
+  T* xoth = (T*)ws.Xw;
   int rb = 0;
-  SDR_LAUNCH(h, SDR_K_RESIDUAL0, launch_residual(ws, Ad, b, xcur, ws.R[rb], accR, -1, 0, st));
-  Ctl hc;
+  SDR_LAUNCH(h, SDR_K_RESIDUAL0, launch_residual<T>(ws, Ad, b, xcur, (T*)ws.R[rb], accR, -1, 0, st));
+  Ctl& hc = out.hc;
   SDR_CK(cudaMemcpyAsync(&hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   SDR_CK(cudaStreamSynchronize(st));
-  std::vector<const double*> vcol(m + 1);
+  std::vector<const T*> vcol(m + 1);
   int cycles = 0;
   sdr_status status = SDR_OK;
   int full_svd = 0;
   bool converged = hc.converged != 0;
-  while (!converged && cycles < h->p.max_cycles) {
-    vcol[0] = ws.R[rb];
-    for (int c = 1; c <= m; ++c) vcol[c] = ws.Vs + (int64_t)(c - 1) * ws.ldv;
+  while (!converged && cycles < max_cycles) {
+    vcol[0] = (const T*)ws.R[rb];
+    for (int c = 1; c <= m; ++c) vcol[c] = tall_col<T>(ws.Vs, ws.ldv, c - 1);
     const int cu = h->cu, kh = h->kh;
+    const T* Ucur = (const T*)ws.U[cu];
     // Two streams per cycle.  The Arnoldi stream (st) runs the SpMV, sketch
     // and update of every step; the control stream (st2) runs the one-CTA
     // dense step of each column and the true-residual check it may call for.
@@ -333,35 +370,36 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
     for (int j = 0; j <= m; ++j) {
       if (j >= SPEC_LAG) SDR_CK(cudaStreamWaitEvent(st, h->evD[j - SPEC_LAG], 0));
       if (j < m) {
-        SDR_LAUNCH(h, SDR_K_SPMV_DOTS, launch_spmv_dots(ws, Ad, vcol.data(), j, st));
+        SDR_LAUNCH(h, SDR_K_SPMV_DOTS, launch_spmv_dots<T>(ws, Ad, vcol.data(), j, st));
       } else {
-        SDR_LAUNCH(h, SDR_K_SKETCH, launch_sketch_col(ws, vcol[m], m, st));
+        SDR_LAUNCH(h, SDR_K_SKETCH, launch_sketch_col<T>(ws, vcol[m], m, st));
       }
       if (j >= 1) {
         SDR_CK(cudaEventRecord(h->evS[j], st));
         SDR_CK(cudaStreamWaitEvent(st2, h->evS[j], 0));
         SDR_LAUNCH_ON(h, SDR_K_STEP_DENSE, st2, launch_step_dense(ws, j - 1, kh, cu, accR, st2));
         SDR_LAUNCH_ON(h, SDR_K_CHECK_GEMV, st2,
-                      launch_check_gemv(ws, ws.U[cu], vcol.data(), xcur, xoth, kh, j - 1, cu, st2));
+                      launch_check_gemv<T>(ws, Ucur, vcol.data(), xcur, xoth, kh, j - 1, cu, st2));
         SDR_LAUNCH_ON(h, SDR_K_CHECK_RESIDUAL, st2,
-                      launch_residual(ws, Ad, b, xoth, ws.R[1 - rb], accR, j - 1, 1, st2));
+                      launch_residual<T>(ws, Ad, b, xoth, (T*)ws.R[1 - rb], accR, j - 1, 1, st2));
         SDR_CK(cudaEventRecord(h->evD[j - 1], st2));
       }
-      if (j < m) SDR_LAUNCH(h, SDR_K_UPDATE_SKETCH, launch_update_sketch(ws, vcol.data(), (double*)vcol[j + 1], j, st));
+      if (j < m) SDR_LAUNCH(h, SDR_K_UPDATE_SKETCH, launch_update_sketch<T>(ws, vcol.data(), (T*)vcol[j + 1], j, st));
     }
     SDR_CK(cudaEventRecord(h->evJoin, st2));
     SDR_CK(cudaStreamWaitEvent(st, h->evJoin, 0));
     for (int part = 0; part < CYCLE_END_PARTS; ++part)
       SDR_LAUNCH(h, part == 0 ? SDR_K_CYCLE_END : SDR_K_CE_RINV + part - 1,
                  launch_cycle_end_part(part, ws, kh, cu, ws.SU[cu], ws.SAU[cu], ws.SU[1 - cu], ws.SAU[1 - cu], st));
-    SDR_LAUNCH(h, SDR_K_RECYCLE_GEMM, launch_recycle_gemm(ws, ws.U[cu], vcol.data(), ws.U[1 - cu], kh, cu, 1 - cu, st));
+    SDR_LAUNCH(h, SDR_K_RECYCLE_GEMM,
+               launch_recycle_gemm<T>(ws, Ucur, vcol.data(), (T*)ws.U[1 - cu], kh, cu, 1 - cu, st));
     SDR_CK(cudaMemcpyAsync(&hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     SDR_CK(cudaStreamSynchronize(st));
     ++cycles;
     if (hc.jf > 0) {
       h->cu = 1 - cu;
       h->kh = hc.kprime;
-      double* t = xcur;
+      T* t = xcur;
       xcur = xoth;
       xoth = t;
       rb = 1 - rb;
@@ -377,7 +415,88 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
       break;
     }
   }
-  if (xcur != x) SDR_CK(cudaMemcpyAsync(x, xcur, (size_t)A->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (xcur != x) SDR_CK(cudaMemcpyAsync(x, xcur, (size_t)Ad.n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  if (status == SDR_OK && !converged) status = SDR_ERR_NOT_CONVERGED;
+  out.cycles += cycles;
+  out.full_svd += full_svd;
+  out.converged = converged;
+  out.status = status;
+  return SDR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x, sdr_stats* stats) {
+  if (!h || !csr_ok(h, A) || !b || !x) return SDR_ERR_INVALID_ARG;
+  WS ws = h->ws;
+  ws.n = A->n;
+  const CsrDev Ad = to_dev(A);
+  cudaStream_t st = h->st, st2 = h->st2;
+  h->launches = 0;
+  // anything a failed earlier call left on the control stream comes first
+  SDR_CK(cudaEventRecord(h->evJoin, st2));
+  SDR_CK(cudaStreamWaitEvent(st, h->evJoin, 0));
+  CycleRun run;
+  int refinements = 0;
+  double final_res = 0.0, bnorm = 0.0, tol = 0.0;
+  if (h->prec == SDR_PREC_F64) {
+    const sdr_status rs = run_cycles<double>(h, Ad, b, x, h->p.rel_tol, h->p.max_cycles, run);
+    if (rs != SDR_OK) return rs;
+    final_res = run.hc.res;
+    bnorm = run.hc.bnorm;
+    tol = run.hc.tol;
+  } else {
+    // Iterative refinement in float64 around the float32 solver: the outer
+    // residual r = b - A x uses the float64 values; each inner solve of
+    // A d = r runs with float32 storage and arithmetic and keeps the recycle
+    // space (same matrix, new right-hand side: Section 3.6).
+    unsigned long long* accR = ws.acc + 2 * S_MAX;
+    double* r64 = h->d_tmp;
+    SDR_LAUNCH(h, SDR_K_SOLVE_INIT, launch_solve_init_x<double>(ws, Ad, b, x, h->p.rel_tol, st));
+    Ctl hc;
+    SDR_CK(cudaMemcpyAsync(&hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    SDR_CK(cudaStreamSynchronize(st));
+    bnorm = hc.bnorm;
+    tol = hc.tol;
+    const int max_refine = 40;
+    bool conv = false;
+    sdr_status inner_status = SDR_OK;
+    double last_res = INFINITY;
+    for (;;) {
+      SDR_LAUNCH(h, SDR_K_RESIDUAL0, launch_residual<double>(ws, Ad, b, x, r64, accR, -1, 0, st));
+      SDR_CK(cudaMemsetAsync(accR, 0, 2 * S_MAX * sizeof(unsigned long long), st));
+      SDR_CK(cudaMemcpyAsync(&hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+      SDR_CK(cudaStreamSynchronize(st));
+      final_res = hc.res;
+      if (!std::isfinite(final_res)) {
+        inner_status = SDR_ERR_BREAKDOWN;
+        break;
+      }
+      if (final_res < tol) {
+        conv = true;
+        break;
+      }
+      // stop when refinement no longer reduces the residual
+      if (refinements >= max_refine || (refinements > 0 && !(final_res < 0.5 * last_res))) break;
+      last_res = final_res;
+      SDR_LAUNCH(h, SDR_K_REFINE, launch_to_f32(r64, (float*)h->rhs32, (float*)h->dx32, Ad.n, st));
+      const sdr_status rs = run_cycles<float>(h, Ad, (const float*)h->rhs32, (float*)h->dx32, h->p.inner_rel_tol,
+                                              h->p.max_cycles, run);
+      if (rs != SDR_OK) return rs;
+      if (run.status == SDR_ERR_BREAKDOWN || run.status == SDR_ERR_RANK) {
+        inner_status = run.status;
+        break;
+      }
+      SDR_LAUNCH(h, SDR_K_REFINE, launch_add_f32(x, (const float*)h->dx32, Ad.n, st));
+      ++refinements;
+    }
+    run.converged = conv;
+    run.status = conv ? SDR_OK : (inner_status != SDR_OK ? inner_status : SDR_ERR_NOT_CONVERGED);
+    run.hc.res = final_res;
+  }
+  const Ctl& hc = run.hc;
   const int nh = hc.hist_n < HIST_MAX ? hc.hist_n : HIST_MAX;
   const int nl = hc.log_n < LOG_MAX ? hc.log_n : LOG_MAX;
   h->hist.assign(nh, 0.0);
@@ -386,11 +505,10 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
   if (nl) SDR_CK(cudaMemcpyAsync(h->log.data(), ws.log, nl * sizeof(CycleLog), cudaMemcpyDeviceToHost, st));
   SDR_CK(cudaStreamSynchronize(st));
   SDR_CK(prof_collect(h));
-  if (status == SDR_OK && !converged) status = SDR_ERR_NOT_CONVERGED;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
-    stats->cycles = cycles;
-    stats->converged = converged ? 1 : 0;
+    stats->cycles = run.cycles;
+    stats->converged = run.converged ? 1 : 0;
     stats->matvecs = hc.matvecs;
     stats->sketches = hc.sketches;
     int checks = 0;
@@ -398,17 +516,21 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
     stats->true_res_evals = checks;
     stats->arnoldi_steps = hc.hist_n;
     stats->recycle_dim = h->kh;
-    stats->full_svd_cycles = full_svd;
+    stats->full_svd_cycles = run.full_svd;
     stats->kernel_launches = h->launches;
-    stats->final_res = hc.res;
-    stats->tol = hc.tol;
-    stats->bnorm = hc.bnorm;
-    stats->final_rel_res = hc.bnorm > 0.0 ? hc.res / hc.bnorm : hc.res;
+    stats->refinements = refinements;
+    stats->final_res = final_res;
+    stats->tol = tol;
+    stats->bnorm = bnorm;
+    stats->final_rel_res = bnorm > 0.0 ? final_res / bnorm : final_res;
   }
-  return status;
+  return run.status;
 }
 
+}  // extern "C"
+
 // Recompute SAU = S A U column by column (exact variant, Section 3.6).
+template <typename T>
 static sdr_status recompute_sau(sdr_handle* h, const sdr_csr* A, int64_t n) {
   WS ws = h->ws;
   ws.n = n;
@@ -417,11 +539,12 @@ static sdr_status recompute_sau(sdr_handle* h, const sdr_csr* A, int64_t n) {
   int* topG = ctl_int_field(ws.ctl, offsetof(Ctl, accG_top));
   h->launches = 0;
   for (int c = 0; c < h->kh; ++c) {
-    const double* u = ws.U[h->cu] + (int64_t)c * ws.ldv;
+    const T* u = tall_col<T>(ws.U[h->cu], ws.ldv, c);
+    T* au = (T*)h->d_tmp;
     SDR_CK(prof_begin(h, SDR_K_RECYCLE_SAU, h->st));
-    SDR_CK(launch_spmv(Ad, u, h->d_tmp, h->st));
-    SDR_CK(launch_maxabs_top(ws, h->d_tmp, n, topG, h->st));
-    SDR_CK(launch_sketch_vec(ws, h->d_tmp, n, accG, topG, h->st));
+    SDR_CK(launch_spmv<T>(Ad, u, au, h->st));
+    SDR_CK(launch_maxabs_top<T>(ws, au, n, topG, h->st));
+    SDR_CK(launch_sketch_vec<T>(ws, au, n, accG, topG, h->st));
     SDR_CK(launch_sketch_finish(ws, accG, topG, ws.SAU[h->cu] + (int64_t)c * ws.s, h->st));
     SDR_CK(prof_end(h, h->st));
   }
@@ -430,17 +553,18 @@ static sdr_status recompute_sau(sdr_handle* h, const sdr_csr* A, int64_t n) {
   return SDR_OK;
 }
 
+template <typename T>
 static sdr_status recompute_su(sdr_handle* h, int64_t n) {
   WS ws = h->ws;
   ws.n = n;
   unsigned long long* accG = ws.acc + 4 * S_MAX;
   int* topG = ctl_int_field(ws.ctl, offsetof(Ctl, accG_top));
   for (int c = 0; c < h->kh; ++c) {
-    const double* u = ws.U[h->cu] + (int64_t)c * ws.ldv;
+    const T* u = tall_col<T>(ws.U[h->cu], ws.ldv, c);
     SDR_CK(prof_begin(h, SDR_K_SKETCH, h->st));
     h->launches += 2;  // three kernels under one timing bracket
-    SDR_CK(launch_maxabs_top(ws, u, n, topG, h->st));
-    SDR_CK(launch_sketch_vec(ws, u, n, accG, topG, h->st));
+    SDR_CK(launch_maxabs_top<T>(ws, u, n, topG, h->st));
+    SDR_CK(launch_sketch_vec<T>(ws, u, n, accG, topG, h->st));
     SDR_CK(launch_sketch_finish(ws, accG, topG, ws.SU[h->cu] + (int64_t)c * ws.s, h->st));
     SDR_CK(prof_end(h, h->st));
   }
@@ -448,6 +572,8 @@ static sdr_status recompute_su(sdr_handle* h, int64_t n) {
   SDR_CK(prof_collect(h));
   return SDR_OK;
 }
+
+extern "C" {
 
 sdr_status sdr_recycle(sdr_handle* h, const sdr_csr* A_next, int32_t mode) {
   if (!h) return SDR_ERR_INVALID_ARG;
@@ -459,7 +585,8 @@ sdr_status sdr_recycle(sdr_handle* h, const sdr_csr* A_next, int32_t mode) {
   if (mode != 0) return SDR_ERR_INVALID_ARG;
   if (h->kh == 0) return SDR_OK;
   if (!csr_ok(h, A_next)) return SDR_ERR_INVALID_ARG;
-  return recompute_sau(h, A_next, A_next->n);
+  return h->prec == SDR_PREC_F64 ? recompute_sau<double>(h, A_next, A_next->n)
+                                 : recompute_sau<float>(h, A_next, A_next->n);
 }
 
 sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y) {
@@ -471,8 +598,8 @@ sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y) {
   h->launches = 0;
   SDR_CK(prof_begin(h, SDR_K_SKETCH, h->st));
   h->launches += 2;  // three kernels under one timing bracket
-  SDR_CK(launch_maxabs_top(ws, x, n, topG, h->st));
-  SDR_CK(launch_sketch_vec(ws, x, n, accG, topG, h->st));
+  SDR_CK(launch_maxabs_top<double>(ws, x, n, topG, h->st));
+  SDR_CK(launch_sketch_vec<double>(ws, x, n, accG, topG, h->st));
   SDR_CK(launch_sketch_finish(ws, accG, topG, y, h->st));
   SDR_CK(prof_end(h, h->st));
   SDR_CK(cudaStreamSynchronize(h->st));
@@ -523,6 +650,7 @@ sdr_status sdr_recycle_dim(sdr_handle* h, int32_t* kdim) {
 
 sdr_status sdr_recycle_export(sdr_handle* h, int64_t n, double* U, double* SU, double* SAU) {
   if (!h || n <= 0 || n > h->n_max) return SDR_ERR_INVALID_ARG;
+  if (h->prec != SDR_PREC_F64) return SDR_ERR_NOT_IMPLEMENTED;
   const WS& ws = h->ws;
   const int kh = h->kh;
   if (kh == 0) return SDR_OK;
@@ -540,6 +668,7 @@ sdr_status sdr_recycle_export(sdr_handle* h, int64_t n, double* U, double* SU, d
 sdr_status sdr_recycle_import(sdr_handle* h, const sdr_csr* A, int64_t n, int32_t kdim, const double* U,
                               const double* SU, const double* SAU) {
   if (!h || n <= 0 || n > h->n_max || kdim < 0 || kdim > h->ws.kmax) return SDR_ERR_INVALID_ARG;
+  if (h->prec != SDR_PREC_F64) return SDR_ERR_NOT_IMPLEMENTED;
   if (kdim > 0 && !U) return SDR_ERR_INVALID_ARG;
   if (kdim > 0 && !SAU && !csr_ok(h, A)) return SDR_ERR_INVALID_ARG;
   const WS& ws = h->ws;
@@ -550,7 +679,7 @@ sdr_status sdr_recycle_import(sdr_handle* h, const sdr_csr* A, int64_t n, int32_
   {
     WS w2 = h->ws;
     w2.n = n;
-    SDR_CK(launch_umax(w2, ws.U[h->cu], kdim, h->cu, h->st));
+    SDR_CK(launch_umax<double>(w2, (const double*)ws.U[h->cu], kdim, h->cu, h->st));
   }
   if (SU)
     SDR_CK(cudaMemcpyAsync(ws.SU[h->cu], SU, (size_t)ws.s * kdim * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
@@ -559,10 +688,10 @@ sdr_status sdr_recycle_import(sdr_handle* h, const sdr_csr* A, int64_t n, int32_
                            h->st));
   SDR_CK(cudaStreamSynchronize(h->st));
   if (!SU) {
-    sdr_status s = recompute_su(h, n);
+    sdr_status s = recompute_su<double>(h, n);
     if (s != SDR_OK) return s;
   }
-  if (!SAU) return recompute_sau(h, A, n);
+  if (!SAU) return recompute_sau<double>(h, A, n);
   return SDR_OK;
 }
 

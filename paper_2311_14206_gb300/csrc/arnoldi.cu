@@ -17,15 +17,26 @@
 
 namespace sdr {
 
+// Tall vectors (the basis, w, residuals, iterates, U) hold elements of type T:
+// double for the FP64 solver, float for the FP32 inner solver of the refined
+// form, whose SpMV, window dots and updates then also accumulate in FP32.
+template <typename T>
 struct Win {
-  const double* v[T_MAX];  // v_hat_lo .. v_hat_j
+  const T* v[T_MAX];  // v_hat_lo .. v_hat_j
   int lo, nw;
 };
 
-__device__ inline double csr_row_dot(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                     const double* __restrict__ val, const double* __restrict__ x, int64_t r) {
+template <typename T> __device__ __forceinline__ const T* csr_val(const CsrDev& A);
+template <> __device__ __forceinline__ const double* csr_val<double>(const CsrDev& A) { return A.val; }
+template <> __device__ __forceinline__ const float* csr_val<float>(const CsrDev& A) { return A.val32; }
+
+template <typename T>
+__device__ inline T csr_row_dot(const CsrDev& A, const T* __restrict__ x, int64_t r) {
+  const int32_t* __restrict__ rowptr = A.rowptr;
+  const int32_t* __restrict__ col = A.col;
+  const T* __restrict__ val = csr_val<T>(A);
   int p0 = rowptr[r], p1 = rowptr[r + 1];
-  double y = 0.0;
+  T y = 0;
   for (int p = p0; p < p1; ++p) y = fma(val[p], x[col[p]], y);
   return y;
 }
@@ -66,21 +77,22 @@ __device__ inline unsigned long long reduce_parts_max(const double* part, int nb
 // ---------------------------------------------------------------------------
 // Solve start: ||b||, max|b|, max|x0|, ||A||_inf, tol.
 // ---------------------------------------------------------------------------
-__global__ void k_solve_init(WS ws, CsrDev A, const double* __restrict__ b, const double* __restrict__ x,
-                             double rel_tol) {
+template <typename T>
+__global__ void k_solve_init(WS ws, CsrDev A, const T* __restrict__ b, const T* __restrict__ x, double rel_tol) {
   __shared__ double red[32];
   __shared__ unsigned long long redu[32];
   double bb = 0.0;
   unsigned long long bm = 0ull, xm = 0ull, am = 0ull;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.n; r += (int64_t)gridDim.x * blockDim.x) {
-    double v = b[r];
+    double v = (double)b[r];
     bb = fma(v, v, bb);
     unsigned long long u = abs_bits(v);
     bm = u > bm ? u : bm;
-    u = abs_bits(x[r]);
+    u = abs_bits((double)x[r]);
     xm = u > xm ? u : xm;
     double rs = 0.0;
-    for (int p = A.rowptr[r]; p < A.rowptr[r + 1]; ++p) rs += fabs(A.val[p]);
+    const T* __restrict__ av = csr_val<T>(A);
+    for (int p = A.rowptr[r]; p < A.rowptr[r + 1]; ++p) rs += fabs((double)av[p]);
     u = abs_bits(rs);
     am = u > am ? u : am;
   }
@@ -125,9 +137,9 @@ static int grid_rows(int64_t n, int tpb, int gmax) {
   return g < 1 ? 1 : (int)g;
 }
 
-cudaError_t launch_solve_init_x(const WS& ws, CsrDev A, const double* b, const double* x, double rel_tol,
-                                cudaStream_t st) {
-  k_solve_init<<<grid_rows(A.n, 256, ws.grid_max), 256, 0, st>>>(ws, A, b, x, rel_tol);
+template <typename T>
+cudaError_t launch_solve_init_x(const WS& ws, CsrDev A, const T* b, const T* x, double rel_tol, cudaStream_t st) {
+  k_solve_init<T><<<grid_rows(A.n, 256, ws.grid_max), 256, 0, st>>>(ws, A, b, x, rel_tol);
   return cudaGetLastError();
 }
 
@@ -136,8 +148,9 @@ cudaError_t launch_solve_init_x(const WS& ws, CsrDev A, const double* b, const d
 // mode 0: unconditional (solve start).  mode 1: runs only when ctl->check and
 // then applies Algorithm 1's residual control in the last CTA.
 // ---------------------------------------------------------------------------
-__global__ void k_residual(WS ws, CsrDev A, const double* __restrict__ b, const double* __restrict__ x,
-                           double* __restrict__ rout, unsigned long long* accR, int j, int mode,
+template <typename T>
+__global__ void k_residual(WS ws, CsrDev A, const T* __restrict__ b, const T* __restrict__ x,
+                           T* __restrict__ rout, unsigned long long* accR, int j, int mode,
                            double* __restrict__ part, unsigned int* counter) {
   Ctl* c = ws.ctl;
   if (mode == 1 && !c->check) return;
@@ -164,8 +177,9 @@ __global__ void k_residual(WS ws, CsrDev A, const double* __restrict__ b, const 
       double v = 0.0;
       if (i < ncols) {
         int64_t r = r0 + i;
-        v = b[r] - csr_row_dot(A.rowptr, A.col, A.val, x, r);
-        rout[r] = v;
+        const T vt = b[r] - csr_row_dot<T>(A, x, r);
+        rout[r] = vt;
+        v = (double)vt;
         nrm = fma(v, v, nrm);
         unsigned long long u = abs_bits(v);
         rm = u > rm ? u : rm;
@@ -234,17 +248,18 @@ static int grid_tiles(const WS& ws, int64_t n) {
   return g < 1 ? 1 : g;
 }
 
-cudaError_t launch_residual(const WS& ws, CsrDev A, const double* b, const double* x, double* rout,
+template <typename T>
+cudaError_t launch_residual(const WS& ws, CsrDev A, const T* b, const T* x, T* rout,
                             unsigned long long* accR, int j, int mode, cudaStream_t st) {
   size_t sm = sketch_smem_bytes(ws.zeta);
   static bool attr = false;
-  cudaError_t e = set_smem((const void*)k_residual, sketch_smem_bytes(ZETA_MAX), attr);
+  cudaError_t e = set_smem((const void*)k_residual<T>, sketch_smem_bytes(ZETA_MAX), attr);
   if (e != cudaSuccess) return e;
   // the check (mode 1) runs on the control stream beside the Arnoldi kernels:
   // it reduces through its own partials and counter
   double* part = mode == 1 ? ws.part3 : ws.part;
   unsigned int* counter = mode == 1 ? &ws.ctl->counter2 : &ws.ctl->counter;
-  k_residual<<<grid_tiles(ws, A.n), SK_THREADS, sm, st>>>(ws, A, b, x, rout, accR, j, mode, part, counter);
+  k_residual<T><<<grid_tiles(ws, A.n), SK_THREADS, sm, st>>>(ws, A, b, x, rout, accR, j, mode, part, counter);
   return cudaGetLastError();
 }
 
@@ -295,8 +310,8 @@ __device__ void finish_column(const WS& ws, int j, int grid2, double* buf, unsig
 // pipes while the FP64 pipe runs the SpMV).  The last CTA finishes column j
 // and turns the dots into the MGS coefficients H(i, j).
 // ---------------------------------------------------------------------------
-template <int NW, bool SK>  // NW window vectors v_hat_lo .. v_hat_j; SK: sketch v_hat_j
-__global__ void __launch_bounds__(SK_THREADS) k_spmv_dots(WS ws, CsrDev A, Win win, int j, int grid2) {
+template <typename T, int NW, bool SK>  // NW window vectors v_hat_lo .. v_hat_j; SK: sketch v_hat_j
+__global__ void __launch_bounds__(SK_THREADS) k_spmv_dots(WS ws, CsrDev A, Win<T> win, int j, int grid2) {
   Ctl* c = ws.ctl;
   if (arnoldi_stopped(c, j)) return;
   extern __shared__ unsigned char smem[];
@@ -306,19 +321,16 @@ __global__ void __launch_bounds__(SK_THREADS) k_spmv_dots(WS ws, CsrDev A, Win w
   uint16_t* ptr_s = ent_s + tileR * ws.zeta;
   __shared__ double buf[SK_THREADS];
   __shared__ unsigned long long redu[32];
-  const double* __restrict__ x = win.v[NW - 1];
-  double* __restrict__ w = ws.Wv;
+  const T* __restrict__ x = win.v[NW - 1];
+  T* __restrict__ w = (T*)ws.Wv;
   const int top = SK ? c->vtop[j] : 0;
-  double d[NW];
+  T d[NW];
 #pragma unroll
-  for (int a = 0; a < NW; ++a) d[a] = 0.0;
+  for (int a = 0; a < NW; ++a) d[a] = 0;
   unsigned long long wm = 0ull;
   unsigned long long lo[SK_RPT], hi[SK_RPT];
 #pragma unroll
   for (int k = 0; k < SK_RPT; ++k) lo[k] = hi[k] = 0ull;
-  const int32_t* __restrict__ rp = A.rowptr;
-  const int32_t* __restrict__ ci = A.col;
-  const double* __restrict__ va = A.val;
   const int64_t n = A.n;
   const int ntiles = (int)((n + tileR - 1) / tileR);
   // Tiles are handed out by a counter, so CTAs that start late (an SM shared
@@ -337,13 +349,13 @@ __global__ void __launch_bounds__(SK_THREADS) k_spmv_dots(WS ws, CsrDev A, Win w
       double xv = 0.0;
       if (i < ncols) {
         const int64_t r = r0 + i;
-        const double y = csr_row_dot(rp, ci, va, x, r);
+        const T y = csr_row_dot<T>(A, x, r);
         w[r] = y;
 #pragma unroll
         for (int a = 0; a < NW; ++a) d[a] = fma(win.v[a][r], y, d[a]);
-        const unsigned long long u = abs_bits(y);
+        const unsigned long long u = abs_bits((double)y);
         wm = u > wm ? u : wm;
-        if (SK) xv = x[r];
+        if (SK) xv = (double)x[r];
       }
       if (SK) vals[i] = xv;
     }
@@ -357,13 +369,14 @@ __global__ void __launch_bounds__(SK_THREADS) k_spmv_dots(WS ws, CsrDev A, Win w
       if (row < ws.s) atomic_add128(ws.accV + (int64_t)j * 2 * S_MAX + 2 * row, lo[k], hi[k]);
     }
   }
+  double dd[NW];
 #pragma unroll
-  for (int a = 0; a < NW; ++a) d[a] = block_sum_lean(d[a], buf);
+  for (int a = 0; a < NW; ++a) dd[a] = block_sum_lean((double)d[a], buf);
   wm = block_max_u64(wm, redu);
   if (threadIdx.x == 0) {
     double* pp = ws.part + blockIdx.x * NPART;
 #pragma unroll
-    for (int a = 0; a < NW; ++a) pp[a] = d[a];
+    for (int a = 0; a < NW; ++a) pp[a] = dd[a];
     pp[T_MAX] = __longlong_as_double((long long)wm);
   }
   if (last_block(&c->counter)) {
@@ -413,33 +426,35 @@ int update_grid(const WS& ws) {
   return g < 1 ? 1 : g;
 }
 
-template <int NW, bool SK>
-static cudaError_t launch_spmv_t(const WS& ws, CsrDev A, const Win& win, int j, cudaStream_t st) {
+template <typename T, int NW, bool SK>
+static cudaError_t launch_spmv_t(const WS& ws, CsrDev A, const Win<T>& win, int j, cudaStream_t st) {
   static bool attr = false;
-  cudaError_t e = set_smem((const void*)k_spmv_dots<NW, SK>, sketch_smem_bytes(ZETA_MAX), attr);
+  cudaError_t e = set_smem((const void*)k_spmv_dots<T, NW, SK>, sketch_smem_bytes(ZETA_MAX), attr);
   if (e != cudaSuccess) return e;
   const size_t sm = SK ? sketch_smem_bytes(ws.zeta) : 0;
-  k_spmv_dots<NW, SK><<<grid_tiles(ws, A.n), SK_THREADS, sm, st>>>(ws, A, win, j, update_grid(ws));
+  k_spmv_dots<T, NW, SK><<<grid_tiles(ws, A.n), SK_THREADS, sm, st>>>(ws, A, win, j, update_grid(ws));
   return cudaGetLastError();
 }
 
-cudaError_t launch_spmv_dots(const WS& ws, CsrDev A, const double* const* vcol, int j, cudaStream_t st) {
-  Win win;
+template <typename T>
+cudaError_t launch_spmv_dots(const WS& ws, CsrDev A, const T* const* vcol, int j, cudaStream_t st) {
+  Win<T> win;
   win.lo = j - ws.t + 1 > 0 ? j - ws.t + 1 : 0;
   win.nw = j - win.lo + 1;
   for (int a = 0; a < T_MAX; ++a) win.v[a] = a < win.nw ? vcol[win.lo + a] : nullptr;
-  if (j == 0) return launch_spmv_t<1, false>(ws, A, win, j, st);  // S r0 came with r0
+  if (j == 0) return launch_spmv_t<T, 1, false>(ws, A, win, j, st);  // S r0 came with r0
   switch (win.nw) {
-    case 1: return launch_spmv_t<1, true>(ws, A, win, j, st);
-    case 2: return launch_spmv_t<2, true>(ws, A, win, j, st);
-    case 3: return launch_spmv_t<3, true>(ws, A, win, j, st);
-    default: return launch_spmv_t<4, true>(ws, A, win, j, st);
+    case 1: return launch_spmv_t<T, 1, true>(ws, A, win, j, st);
+    case 2: return launch_spmv_t<T, 2, true>(ws, A, win, j, st);
+    case 3: return launch_spmv_t<T, 3, true>(ws, A, win, j, st);
+    default: return launch_spmv_t<T, 4, true>(ws, A, win, j, st);
   }
 }
 
 // S v_hat_j for the last column of a cycle (no SpMV follows it), with the
 // column's finish.
-__global__ void __launch_bounds__(SK_THREADS) k_sketch_col(WS ws, const double* __restrict__ x, int j, int grid2) {
+template <typename T>
+__global__ void __launch_bounds__(SK_THREADS) k_sketch_col(WS ws, const T* __restrict__ x, int j, int grid2) {
   Ctl* c = ws.ctl;
   if (arnoldi_stopped(c, j)) return;
   extern __shared__ unsigned char smem[];
@@ -459,7 +474,7 @@ __global__ void __launch_bounds__(SK_THREADS) k_sketch_col(WS ws, const double* 
     const int64_t r0 = (int64_t)tile * tileR;
     const int ncols = (int)(n - r0 < (int64_t)tileR ? n - r0 : (int64_t)tileR);
     tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
-    for (int i = threadIdx.x; i < tileR; i += blockDim.x) vals[i] = i < ncols ? x[r0 + i] : 0.0;
+    for (int i = threadIdx.x; i < tileR; i += blockDim.x) vals[i] = i < ncols ? (double)x[r0 + i] : 0.0;
     tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
   }
 #pragma unroll
@@ -473,11 +488,12 @@ __global__ void __launch_bounds__(SK_THREADS) k_sketch_col(WS ws, const double* 
   }
 }
 
-cudaError_t launch_sketch_col(const WS& ws, const double* x, int j, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_sketch_col(const WS& ws, const T* x, int j, cudaStream_t st) {
   static bool attr = false;
-  cudaError_t e = set_smem((const void*)k_sketch_col, sketch_smem_bytes(ZETA_MAX), attr);
+  cudaError_t e = set_smem((const void*)k_sketch_col<T>, sketch_smem_bytes(ZETA_MAX), attr);
   if (e != cudaSuccess) return e;
-  k_sketch_col<<<grid_tiles(ws, ws.n), SK_THREADS, sketch_smem_bytes(ws.zeta), st>>>(ws, x, j, update_grid(ws));
+  k_sketch_col<T><<<grid_tiles(ws, ws.n), SK_THREADS, sketch_smem_bytes(ws.zeta), st>>>(ws, x, j, update_grid(ws));
   return cudaGetLastError();
 }
 
@@ -486,27 +502,27 @@ cudaError_t launch_sketch_col(const WS& ws, const double* x, int j, cudaStream_t
 // ||v_hat_{j+1}||^2, its dots with the t-1 newest window vectors and its max
 // magnitude as per-CTA partials (part2).  Pure streaming: many rows per thread.
 // ---------------------------------------------------------------------------
-template <int NW, int NC>  // NW window vectors, NC = t - 1 dots kept for the next window
-__global__ void __launch_bounds__(256) k_update(WS ws, Win win, double* __restrict__ vnext, int j) {
+template <typename T, int NW, int NC>  // NW window vectors, NC = t - 1 dots kept for the next window
+__global__ void __launch_bounds__(256) k_update(WS ws, Win<T> win, T* __restrict__ vnext, int j) {
   Ctl* c = ws.ctl;
   if (arnoldi_stopped(c, j)) return;
   __shared__ double buf[256];
   __shared__ unsigned long long redu[32];
-  double cf[NW + 1];
+  T cf[NW + 1];
 #pragma unroll
-  for (int a = 0; a <= NW; ++a) cf[a] = c->coef[a];
-  const double* __restrict__ w = ws.Wv;
-  double nrm = 0.0;
-  double cr[NC > 0 ? NC : 1];
+  for (int a = 0; a <= NW; ++a) cf[a] = (T)c->coef[a];
+  const T* __restrict__ w = (const T*)ws.Wv;
+  T nrm = 0;
+  T cr[NC > 0 ? NC : 1];
 #pragma unroll
-  for (int q = 0; q < (NC > 0 ? NC : 1); ++q) cr[q] = 0.0;
+  for (int q = 0; q < (NC > 0 ? NC : 1); ++q) cr[q] = 0;
   unsigned long long vm = 0ull;
   const int64_t n = ws.n, stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
-    double wv[NW];
+    T wv[NW];
 #pragma unroll
     for (int a = 0; a < NW; ++a) wv[a] = win.v[a][r];
-    double v = cf[0] * w[r];
+    T v = cf[0] * w[r];
 #pragma unroll
     for (int a = 0; a < NW; ++a) v = fma(-cf[1 + a], wv[a], v);
     vnext[r] = v;
@@ -514,45 +530,47 @@ __global__ void __launch_bounds__(256) k_update(WS ws, Win win, double* __restri
 #pragma unroll
     for (int q = 0; q < NC; ++q)
       if (q < NW) cr[q] = fma(v, wv[NW - 1 - q], cr[q]);
-    const unsigned long long u = abs_bits(v);
+    const unsigned long long u = abs_bits((double)v);
     vm = u > vm ? u : vm;
   }
-  nrm = block_sum_lean(nrm, buf);
+  const double nrm_b = block_sum_lean((double)nrm, buf);
+  double cr_b[NC > 0 ? NC : 1];
 #pragma unroll
-  for (int q = 0; q < NC; ++q) cr[q] = block_sum_lean(cr[q], buf);
+  for (int q = 0; q < NC; ++q) cr_b[q] = block_sum_lean((double)cr[q], buf);
   vm = block_max_u64(vm, redu);
   if (threadIdx.x == 0) {
     double* pp = ws.part2 + blockIdx.x * NPART;
-    pp[0] = nrm;
+    pp[0] = nrm_b;
 #pragma unroll
-    for (int q = 0; q < NC; ++q) pp[1 + q] = cr[q];
+    for (int q = 0; q < NC; ++q) pp[1 + q] = cr_b[q];
     pp[T_MAX] = __longlong_as_double((long long)vm);
   }
 }
 
-template <int NW, int NC>
-static cudaError_t launch_upd(const WS& ws, const Win& win, double* vnext, int j, cudaStream_t st) {
-  k_update<NW, NC><<<update_grid(ws), 256, 0, st>>>(ws, win, vnext, j);
+template <typename T, int NW, int NC>
+static cudaError_t launch_upd(const WS& ws, const Win<T>& win, T* vnext, int j, cudaStream_t st) {
+  k_update<T, NW, NC><<<update_grid(ws), 256, 0, st>>>(ws, win, vnext, j);
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_sketch(const WS& ws, const double* const* vcol, double* vnext, int j, cudaStream_t st) {
-  Win win;
+template <typename T>
+cudaError_t launch_update_sketch(const WS& ws, const T* const* vcol, T* vnext, int j, cudaStream_t st) {
+  Win<T> win;
   win.lo = j - ws.t + 1 > 0 ? j - ws.t + 1 : 0;
   win.nw = j - win.lo + 1;
   for (int a = 0; a < T_MAX; ++a) win.v[a] = a < win.nw ? vcol[win.lo + a] : nullptr;
   const int nc = ws.t - 1;
   switch (win.nw * 10 + nc) {
-    case 10: return launch_upd<1, 0>(ws, win, vnext, j, st);
-    case 11: return launch_upd<1, 1>(ws, win, vnext, j, st);
-    case 12: return launch_upd<1, 2>(ws, win, vnext, j, st);
-    case 13: return launch_upd<1, 3>(ws, win, vnext, j, st);
-    case 21: return launch_upd<2, 1>(ws, win, vnext, j, st);
-    case 22: return launch_upd<2, 2>(ws, win, vnext, j, st);
-    case 23: return launch_upd<2, 3>(ws, win, vnext, j, st);
-    case 32: return launch_upd<3, 2>(ws, win, vnext, j, st);
-    case 33: return launch_upd<3, 3>(ws, win, vnext, j, st);
-    case 43: return launch_upd<4, 3>(ws, win, vnext, j, st);
+    case 10: return launch_upd<T, 1, 0>(ws, win, vnext, j, st);
+    case 11: return launch_upd<T, 1, 1>(ws, win, vnext, j, st);
+    case 12: return launch_upd<T, 1, 2>(ws, win, vnext, j, st);
+    case 13: return launch_upd<T, 1, 3>(ws, win, vnext, j, st);
+    case 21: return launch_upd<T, 2, 1>(ws, win, vnext, j, st);
+    case 22: return launch_upd<T, 2, 2>(ws, win, vnext, j, st);
+    case 23: return launch_upd<T, 2, 3>(ws, win, vnext, j, st);
+    case 32: return launch_upd<T, 3, 2>(ws, win, vnext, j, st);
+    case 33: return launch_upd<T, 3, 3>(ws, win, vnext, j, st);
+    case 43: return launch_upd<T, 4, 3>(ws, win, vnext, j, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -563,12 +581,14 @@ cudaError_t launch_update_sketch(const WS& ws, const double* const* vcol, double
 // in [0.5, 1); all elements then share one fixed-point unit 2^-51, and the
 // coefficients carry the inverse scales (prepared by the dense kernels).
 // ---------------------------------------------------------------------------
+template <typename T>
 struct Cols {
-  const double* v0;  // column 0 of V (the cycle's residual)
-  const double* vs;  // columns 1.. (column c at vs + (c-1)*ldv)
+  const T* v0;  // column 0 of V (the cycle's residual)
+  const T* vs;  // columns 1.. (column c at vs + (c-1)*ldv)
 };
 
-__device__ __forceinline__ const double* wcol(const double* U, const Cols& V, int64_t ld, int kh, int l) {
+template <typename T>
+__device__ __forceinline__ const T* wcol(const T* U, const Cols<T>& V, int64_t ld, int kh, int l) {
   return l < kh ? U + (int64_t)l * ld : (l == kh ? V.v0 : V.vs + (int64_t)(l - kh - 1) * ld);
 }
 
@@ -580,8 +600,9 @@ __device__ __forceinline__ int col_delta(const Ctl* c, int ubuf, int kh, int l) 
 }
 
 // x_trial = x + W y'  (one thread per row).
-__global__ void __launch_bounds__(256) k_check_q(WS ws, const double* __restrict__ U, Cols V,
-                                                 const double* __restrict__ xcur, double* __restrict__ xtrial,
+template <typename T>
+__global__ void __launch_bounds__(256) k_check_q(WS ws, const T* __restrict__ U, Cols<T> V,
+                                                 const T* __restrict__ xcur, T* __restrict__ xtrial,
                                                  int kh, int j, int ubuf) {
   Ctl* c = ws.ctl;
   if (!c->check) return;
@@ -604,27 +625,28 @@ __global__ void __launch_bounds__(256) k_check_q(WS ws, const double* __restrict
     acc.zero();
     int l = 0;
     for (; l + 4 <= d; l += 4) {
-      const double w0 = wcol(U, V, ld, kh, l)[r], w1 = wcol(U, V, ld, kh, l + 1)[r];
-      const double w2 = wcol(U, V, ld, kh, l + 2)[r], w3 = wcol(U, V, ld, kh, l + 3)[r];
+      const double w0 = (double)wcol(U, V, ld, kh, l)[r], w1 = (double)wcol(U, V, ld, kh, l + 1)[r];
+      const double w2 = (double)wcol(U, V, ld, kh, l + 2)[r], w3 = (double)wcol(U, V, ld, kh, l + 3)[r];
       acc.mac(q52(w0, 1022, dl[l]), yq[l]);
       acc.mac(q52(w1, 1022, dl[l + 1]), yq[l + 1]);
       acc.mac(q52(w2, 1022, dl[l + 2]), yq[l + 2]);
       acc.mac(q52(w3, 1022, dl[l + 3]), yq[l + 3]);
     }
-    for (; l < d; ++l) acc.mac(q52(wcol(U, V, ld, kh, l)[r], 1022, dl[l]), yq[l]);
-    const double v = xcur[r] + acc_to_double(acc, sexp);
+    for (; l < d; ++l) acc.mac(q52((double)wcol(U, V, ld, kh, l)[r], 1022, dl[l]), yq[l]);
+    const T v = (T)((double)xcur[r] + acc_to_double(acc, sexp));
     xtrial[r] = v;
-    const unsigned long long u = abs_bits(v);
+    const unsigned long long u = abs_bits((double)v);
     xm = u > xm ? u : xm;
   }
   xm = block_max_u64(xm, redu);
   if (threadIdx.x == 0) atomicMax(&c->xmax, xm);
 }
 
-cudaError_t launch_check_gemv(const WS& ws, const double* U, const double* const* vcol, const double* xcur,
-                              double* xtrial, int kh, int j, int ubuf, cudaStream_t st) {
-  Cols V{vcol[0], ws.Vs};
-  k_check_q<<<grid_rows(ws.n, 256, ws.grid_max), 256, 0, st>>>(ws, U, V, xcur, xtrial, kh, j, ubuf);
+template <typename T>
+cudaError_t launch_check_gemv(const WS& ws, const T* U, const T* const* vcol, const T* xcur,
+                              T* xtrial, int kh, int j, int ubuf, cudaStream_t st) {
+  Cols<T> V{vcol[0], (const T*)ws.Vs};
+  k_check_q<T><<<grid_rows(ws.n, 256, ws.grid_max), 256, 0, st>>>(ws, U, V, xcur, xtrial, kh, j, ubuf);
   return cudaGetLastError();
 }
 
@@ -633,8 +655,9 @@ cudaError_t launch_check_gemv(const WS& ws, const double* U, const double* const
 // columns 8g .. 8g+7 of P'' (read through L1: every lane of a warp reads the
 // same coefficient).
 constexpr int RT = 32;
-__global__ void __launch_bounds__(128, 4) k_recycle_q(WS ws, const double* __restrict__ U, Cols V,
-                                                      double* __restrict__ Unew, int kh, int ucur, int unext) {
+template <typename T>
+__global__ void __launch_bounds__(128, 4) k_recycle_q(WS ws, const T* __restrict__ U, Cols<T> V,
+                                                      T* __restrict__ Unew, int kh, int ucur, int unext) {
   Ctl* c = ws.ctl;
   const int kp = c->kprime, jf = c->jf;
   if (kp <= 0 || jf <= 0) return;
@@ -660,7 +683,7 @@ __global__ void __launch_bounds__(128, 4) k_recycle_q(WS ws, const double* __res
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int l = l0 + u * step;
-        w[u] = (l < d && r < nr) ? wcol(U, V, ld, kh, l)[r0 + r] : 0.0;
+        w[u] = (l < d && r < nr) ? (double)wcol(U, V, ld, kh, l)[r0 + r] : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
@@ -690,9 +713,9 @@ __global__ void __launch_bounds__(128, 4) k_recycle_q(WS ws, const double* __res
         for (int q = 0; q < 8; ++q) {
           const int col = gg * 8 + q;
           if (col < kp) {
-            const double v = acc_to_double(acc[q], -51 + fx[col] - 51);
+            const T v = (T)acc_to_double(acc[q], -51 + fx[col] - 51);
             Unew[r0 + r + (int64_t)col * ld] = v;
-            const unsigned long long u = abs_bits(v);
+            const unsigned long long u = abs_bits((double)v);
             if (gg == g) um[q] = u > um[q] ? u : um[q];
             else atomicMax(&c->umax[unext][col], u);
           }
@@ -711,28 +734,71 @@ __global__ void __launch_bounds__(128, 4) k_recycle_q(WS ws, const double* __res
   }
 }
 
-cudaError_t launch_recycle_gemm(const WS& ws, const double* U, const double* const* vcol, double* Unew, int kh,
+template <typename T>
+cudaError_t launch_recycle_gemm(const WS& ws, const T* U, const T* const* vcol, T* Unew, int kh,
                                 int ucur, int unext, cudaStream_t st) {
-  Cols V{vcol[0], ws.Vs};
+  Cols<T> V{vcol[0], (const T*)ws.Vs};
   const size_t sm = (size_t)D_MAX * RT * sizeof(Q52);
   static bool attr = false;
-  cudaError_t e = set_smem((const void*)k_recycle_q, sm, attr);
+  cudaError_t e = set_smem((const void*)k_recycle_q<T>, sm, attr);
   if (e != cudaSuccess) return e;
   const int nsm = ws.grid_max / 8;
-  k_recycle_q<<<nsm * 4, 128, sm, st>>>(ws, U, V, Unew, kh, ucur, unext);
+  k_recycle_q<T><<<nsm * 4, 128, sm, st>>>(ws, U, V, Unew, kh, ucur, unext);
   return cudaGetLastError();
 }
 
-__global__ void k_spmv(CsrDev A, const double* __restrict__ x, double* __restrict__ y) {
+template <typename T>
+__global__ void k_spmv(CsrDev A, const T* __restrict__ x, T* __restrict__ y) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.n; r += (int64_t)gridDim.x * blockDim.x)
-    y[r] = csr_row_dot(A.rowptr, A.col, A.val, x, r);
+    y[r] = csr_row_dot<T>(A, x, r);
 }
 
-cudaError_t launch_spmv(CsrDev A, const double* x, double* y, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_spmv(CsrDev A, const T* x, T* y, cudaStream_t st) {
   int64_t g = (A.n + 255) / 256;
   if (g > 4096) g = 4096;
-  k_spmv<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(A, x, y);
+  k_spmv<T><<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(A, x, y);
   return cudaGetLastError();
 }
+
+// Refined form: the float32 right-hand side of an inner solve, and the float64
+// update of the outer iterate.
+__global__ void k_to_f32(const double* __restrict__ r64, float* __restrict__ r32, float* __restrict__ d32,
+                         int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    r32[i] = (float)r64[i];
+    d32[i] = 0.f;
+  }
+}
+
+__global__ void k_add_f32(double* __restrict__ x64, const float* __restrict__ d32, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x64[i] += (double)d32[i];
+}
+
+cudaError_t launch_to_f32(const double* r64, float* r32, float* d32, int64_t n, cudaStream_t st) {
+  k_to_f32<<<grid_rows(n, 256, 4096), 256, 0, st>>>(r64, r32, d32, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_f32(double* x64, const float* d32, int64_t n, cudaStream_t st) {
+  k_add_f32<<<grid_rows(n, 256, 4096), 256, 0, st>>>(x64, d32, n);
+  return cudaGetLastError();
+}
+
+#define SDR_INSTANTIATE_ARNOLDI(T)                                                                          \
+  template cudaError_t launch_solve_init_x<T>(const WS&, CsrDev, const T*, const T*, double, cudaStream_t);   \
+  template cudaError_t launch_residual<T>(const WS&, CsrDev, const T*, const T*, T*, unsigned long long*, int, \
+                                          int, cudaStream_t);                                                 \
+  template cudaError_t launch_spmv_dots<T>(const WS&, CsrDev, const T* const*, int, cudaStream_t);            \
+  template cudaError_t launch_update_sketch<T>(const WS&, const T* const*, T*, int, cudaStream_t);            \
+  template cudaError_t launch_check_gemv<T>(const WS&, const T*, const T* const*, const T*, T*, int, int, int, \
+                                            cudaStream_t);                                                    \
+  template cudaError_t launch_recycle_gemm<T>(const WS&, const T*, const T* const*, T*, int, int, int,        \
+                                              cudaStream_t);                                                  \
+  template cudaError_t launch_spmv<T>(CsrDev, const T*, T*, cudaStream_t);                                    \
+  template cudaError_t launch_sketch_col<T>(const WS&, const T*, int, cudaStream_t);
+SDR_INSTANTIATE_ARNOLDI(double)
+SDR_INSTANTIATE_ARNOLDI(float)
 
 }  // namespace sdr

@@ -349,27 +349,32 @@ __global__ void __launch_bounds__(DT) k_step_dense(WS ws, int j, int kh, int ubu
 }
 
 // max |U(:, l)| per column into ctl->umax[ubuf][l].
-__global__ void k_umax(WS ws, const double* __restrict__ U, int kdim, int ubuf) {
+template <typename T>
+__global__ void k_umax(WS ws, const T* __restrict__ U, int kdim, int ubuf) {
   __shared__ unsigned long long redu[32];
   const int l = blockIdx.y;
   unsigned long long m = 0ull;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ws.n; r += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long u = abs_bits(U[r + (int64_t)l * ws.ldv]);
+    const unsigned long long u = abs_bits((double)U[r + (int64_t)l * ws.ldv]);
     m = u > m ? u : m;
   }
   m = block_max_u64(m, redu);
   if (threadIdx.x == 0 && m) atomicMax(&ws.ctl->umax[ubuf][l], m);
 }
 
-cudaError_t launch_umax(const WS& ws, const double* U, int kdim, int ubuf, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_umax(const WS& ws, const T* U, int kdim, int ubuf, cudaStream_t st) {
   if (kdim <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(&ws.ctl->umax[ubuf][0], 0, sizeof(unsigned long long) * K_MAX, st);
   if (e != cudaSuccess) return e;
   int gx = (int)((ws.n + 255) / 256);
   if (gx > 64) gx = 64;
-  k_umax<<<dim3(gx, kdim), 256, 0, st>>>(ws, U, kdim, ubuf);
+  k_umax<T><<<dim3(gx, kdim), 256, 0, st>>>(ws, U, kdim, ubuf);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_umax<double>(const WS&, const double*, int, int, cudaStream_t);
+template cudaError_t launch_umax<float>(const WS&, const float*, int, int, cudaStream_t);
 
 cudaError_t launch_step_dense(const WS& ws, int j, int kh, int ubuf, unsigned long long* accR, cudaStream_t st) {
   k_step_dense<<<1, DT, 0, st>>>(ws, j, kh, ubuf, update_grid(ws), accR);

@@ -80,12 +80,13 @@ struct WS {
   uint64_t seed;
   double inv_sqrt_zeta;
   int win_bits;     // log2 bound on terms per sketch row (window headroom)
-  // tall arrays (n_max rows)
-  double* Vs;       // columns 1..m of V (column c at Vs + (c-1)*ldv); column 0 is the residual
-  double* R[2];     // residual buffers
-  double* Wv;       // SpMV output w
-  double* Xw;       // workspace iterate
-  double* U[2];     // recycle bases, kmax columns each
+  // tall arrays (n_max rows) of the solver's storage type (double, or float
+  // for the refined form's inner solver); kernels cast them to that type
+  void* Vs;         // columns 1..m of V (column c at Vs + (c-1)*ldv); column 0 is the residual
+  void* R[2];       // residual buffers
+  void* Wv;         // SpMV output w
+  void* Xw;         // workspace iterate
+  void* U[2];       // recycle bases, kmax columns each
   // sketch tables
   const uint16_t* sk_ent;  // per tile: zeta*TILE_R entries (offset | sign<<15)
   const uint16_t* sk_ptr;  // per tile: s+1 row pointers

@@ -93,7 +93,8 @@ cudaError_t launch_sketch_build(const WS& ws, int64_t n, uint16_t* ent, uint16_t
 }
 
 // Generic S x with the window top read from device memory.
-__global__ void k_sketch_vec(WS ws, const double* __restrict__ x, int64_t n, unsigned long long* acc,
+template <typename T>
+__global__ void k_sketch_vec(WS ws, const T* __restrict__ x, int64_t n, unsigned long long* acc,
                              const int* top_dev) {
   extern __shared__ unsigned char smem[];
   const int tileR = sketch_tile_rows(ws.zeta);
@@ -110,7 +111,7 @@ __global__ void k_sketch_vec(WS ws, const double* __restrict__ x, int64_t n, uns
     const int64_t r0 = (int64_t)tile * tileR;
     const int ncols = (int)(n - r0 < (int64_t)tileR ? n - r0 : (int64_t)tileR);
     tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
-    for (int i = threadIdx.x; i < tileR; i += blockDim.x) vals[i] = i < ncols ? x[r0 + i] : 0.0;
+    for (int i = threadIdx.x; i < tileR; i += blockDim.x) vals[i] = i < ncols ? (double)x[r0 + i] : 0.0;
     tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, red, top, lo, hi);
   }
 #pragma unroll
@@ -120,12 +121,13 @@ __global__ void k_sketch_vec(WS ws, const double* __restrict__ x, int64_t n, uns
   }
 }
 
-cudaError_t launch_sketch_vec(const WS& ws, const double* x, int64_t n, unsigned long long* acc,
+template <typename T>
+cudaError_t launch_sketch_vec(const WS& ws, const T* x, int64_t n, unsigned long long* acc,
                               const int* top_dev, cudaStream_t st) {
   size_t sm = sketch_smem_bytes(ws.zeta);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_sketch_vec, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_sketch_vec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sketch_smem_bytes(ZETA_MAX));
     if (e != cudaSuccess) return e;
     attr = true;
@@ -134,7 +136,7 @@ cudaError_t launch_sketch_vec(const WS& ws, const double* x, int64_t n, unsigned
   int ntiles = (int)((n + tileR - 1) / tileR);
   int grid = ntiles < ws.grid_max ? ntiles : ws.grid_max;
   if (grid < 1) grid = 1;
-  k_sketch_vec<<<grid, SK_THREADS, sm, st>>>(ws, x, n, acc, top_dev);
+  k_sketch_vec<T><<<grid, SK_THREADS, sm, st>>>(ws, x, n, acc, top_dev);
   return cudaGetLastError();
 }
 
@@ -155,12 +157,13 @@ cudaError_t launch_sketch_finish(const WS& ws, unsigned long long* acc, const in
 
 // max|x| over a vector -> window top for a sketch of x (one CTA-level pass +
 // last-CTA finish through an atomicMax on the bit pattern).
-__global__ void k_maxabs_top(WS ws, const double* __restrict__ x, int64_t n, unsigned long long* scratch,
+template <typename T>
+__global__ void k_maxabs_top(WS ws, const T* __restrict__ x, int64_t n, unsigned long long* scratch,
                              int* top_dev) {
   __shared__ unsigned long long red[32];
   unsigned long long mb = 0ull;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    unsigned long long b = abs_bits(x[i]);
+    unsigned long long b = abs_bits((double)x[i]);
     mb = b > mb ? b : mb;
   }
   mb = block_max_u64(mb, red);
@@ -181,14 +184,22 @@ __global__ void k_maxabs_top(WS ws, const double* __restrict__ x, int64_t n, uns
   }
 }
 
-cudaError_t launch_maxabs_top(const WS& ws, const double* x, int64_t n, int* top_dev, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_maxabs_top(const WS& ws, const T* x, int64_t n, int* top_dev, cudaStream_t st) {
   // scratch: two u64 words right after the 2*S_MAX words of the second accumulator block
   unsigned long long* scratch = ws.acc + 6 * S_MAX;
   int grid = (int)((n + 255) / 256);
   if (grid > ws.grid_max) grid = ws.grid_max;
   if (grid < 1) grid = 1;
-  k_maxabs_top<<<grid, 256, 0, st>>>(ws, x, n, scratch, top_dev);
+  k_maxabs_top<T><<<grid, 256, 0, st>>>(ws, x, n, scratch, top_dev);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_sketch_vec<double>(const WS&, const double*, int64_t, unsigned long long*, const int*,
+                                               cudaStream_t);
+template cudaError_t launch_sketch_vec<float>(const WS&, const float*, int64_t, unsigned long long*, const int*,
+                                              cudaStream_t);
+template cudaError_t launch_maxabs_top<double>(const WS&, const double*, int64_t, int*, cudaStream_t);
+template cudaError_t launch_maxabs_top<float>(const WS&, const float*, int64_t, int*, cudaStream_t);
 
 }  // namespace sdr

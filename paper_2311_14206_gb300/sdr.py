@@ -25,19 +25,24 @@ class sdr_params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("k", ctypes.c_int32), ("t", ctypes.c_int32), ("s", ctypes.c_int32),
                 ("zeta", ctypes.c_int32), ("seed", ctypes.c_uint64), ("rel_tol", ctypes.c_double),
                 ("safety0", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("persist_safety", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("precision", ctypes.c_int32), ("test_flags", ctypes.c_int32), ("inner_rel_tol", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+SDR_PREC_F64 = 0
+SDR_PREC_F32_REFINED = 1
 
 
 class sdr_csr(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
-                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("val32", ctypes.c_void_p)]
 
 
 class sdr_stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int32), ("converged", ctypes.c_int32), ("matvecs", ctypes.c_int32),
                 ("sketches", ctypes.c_int32), ("true_res_evals", ctypes.c_int32), ("arnoldi_steps", ctypes.c_int32),
                 ("recycle_dim", ctypes.c_int32), ("full_svd_cycles", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int32), ("reserved_i", ctypes.c_int32), ("final_res", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int32), ("refinements", ctypes.c_int32), ("final_res", ctypes.c_double),
                 ("tol", ctypes.c_double), ("final_rel_res", ctypes.c_double), ("bnorm", ctypes.c_double)]
 
     def as_dict(self):
@@ -46,7 +51,8 @@ class sdr_stats(ctypes.Structure):
 
 KERNEL_CLASSES = ["solve_init", "residual0", "cycle_init", "spmv_dots", "update_sketch", "step_dense",
                   "check_gemv", "check_residual", "ce_formC", "recycle_gemm", "recycle_sau", "sketch",
-                  "ce_rinv", "ce_M", "ce_svd", "ce_eig", "ce_invit", "ce_select", "ce_finish", "ce_sketches"]
+                  "ce_rinv", "ce_M", "ce_svd", "ce_eig", "ce_invit", "ce_select", "ce_finish", "ce_sketches",
+                  "refine"]
 
 
 class sdr_kernel_time(ctypes.Structure):
@@ -119,31 +125,41 @@ def _stream():
 
 @dataclass
 class CSRDevice:
-    """Square CSR matrix held in torch CUDA tensors (int32 / int32 / float64)."""
+    """Square CSR matrix held in torch CUDA tensors (int32 / int32 / float64,
+    plus an optional float32 copy of the values for the refined form)."""
 
     n: int
     rowptr: torch.Tensor
     col: torch.Tensor
     val: torch.Tensor
+    val32: torch.Tensor = None
 
     @classmethod
-    def from_numpy(cls, A, device="cuda"):
+    def from_numpy(cls, A, device="cuda", with_f32=False):
+        val = torch.as_tensor(A.val, dtype=torch.float64).to(device)
         return cls(A.n, torch.as_tensor(A.rowptr, dtype=torch.int32).to(device),
-                   torch.as_tensor(A.col, dtype=torch.int32).to(device),
-                   torch.as_tensor(A.val, dtype=torch.float64).to(device))
+                   torch.as_tensor(A.col, dtype=torch.int32).to(device), val,
+                   val.to(torch.float32) if with_f32 else None)
 
     def c_struct(self) -> sdr_csr:
         for t, dt in ((self.rowptr, torch.int32), (self.col, torch.int32), (self.val, torch.float64)):
             if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
                 raise TypeError("CSR arrays must be contiguous CUDA tensors (int32, int32, float64)")
+        v32 = 0
+        if self.val32 is not None:
+            if not self.val32.is_cuda or self.val32.dtype != torch.float32 or not self.val32.is_contiguous():
+                raise TypeError("val32 must be a contiguous float32 CUDA tensor")
+            v32 = self.val32.data_ptr()
         return sdr_csr(self.n, int(self.val.numel()), self.rowptr.data_ptr(), self.col.data_ptr(),
-                       self.val.data_ptr())
+                       self.val.data_ptr(), v32)
 
 
 def make_params(m, k, t, s, zeta, seed, rel_tol, safety0=1.4, max_cycles=200, persist_safety=0,
-                force_svd=False) -> sdr_params:
+                force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0) -> sdr_params:
     p = sdr_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety)
-    p.reserved[0] = 1 if force_svd else 0
+    p.precision = precision
+    p.test_flags = 1 if force_svd else 0
+    p.inner_rel_tol = inner_rel_tol
     return p
 
 
@@ -248,8 +264,9 @@ class Solver:
     """Convenience wrapper owning one handle (GMRES-SDR for one system size)."""
 
     def __init__(self, n_max, m, k, t, s, zeta=8, seed=231114206, rel_tol=1e-8, safety0=1.4, max_cycles=200,
-                 persist_safety=0, force_svd=False):
-        self.params = make_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety, force_svd)
+                 persist_safety=0, force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0):
+        self.params = make_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety, force_svd,
+                                  precision, inner_rel_tol)
         self.n_max, self.s = n_max, s
         self.h = sdr_create(self.params, n_max)
 
