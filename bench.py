@@ -14,6 +14,13 @@ event time of its launches in the timed region.  cpu_baseline = the FP64 CPU
 oracle on a bounded sample of the same workload (single thread).
 
 --impl reference runs the oracle instead (host cores only).
+
+--workload cd3d_256_seq20_fp32ir measures the refined form instead: 3D
+convection-diffusion 256^3 (N = 16,777,216), the same perturbed sequence,
+m = 80, k = 20, s = 400, true relative residual 1e-10, solved by the float64
+GPU path and by the float32 solver inside float64 refinement on the same
+systems; value = the refined form's ms per system, with the float64 path's
+time and the relative difference of the two solutions beside it.
 """
 import argparse
 import json
@@ -247,6 +254,83 @@ def run_gpu(args, rank, world):
     return result
 
 
+# --------------------------------------------------------------------------- refined form
+F32IR = dict(workload="cd3d_256_seq20_fp32ir", n=256, conv=(20.0, 10.0, 5.0), systems=20, eps=1e-3,
+             m=80, k=20, t=2, s=400, zeta=8, rel_tol=1e-10, inner_rel_tol=1e-4, seed=231114206)
+
+
+def run_form_f32ir(args):
+    """Time-to-1e-10 per system: float64 GPU path vs float32 + float64 refinement."""
+    import torch
+    import workloads as W
+    import paper_2311_14206_gb300 as P
+
+    cfg = F32IR
+    dev = torch.device("cuda")
+    A0, dvec, diag_pos = make_inputs(cfg)
+    N, nnz = A0.n, A0.nnz
+    rowptr = torch.as_tensor(A0.rowptr, device=dev)
+    col = torch.as_tensor(A0.col, device=dev)
+    nsys = args.warmup + args.steps
+    vals = [torch.as_tensor(system_values(A0, dvec, diag_pos, i + 1, cfg["eps"]), device=dev) for i in range(nsys)]
+    mats = [P.CSRDevice(N, rowptr, col, v, v.to(torch.float32)) for v in vals]
+    bs = [torch.as_tensor(W.rhs(N, i), device=dev) for i in range(nsys)]
+    stream = torch.cuda.current_stream()
+    out = {}
+    xs = {}
+    for name, prec in (("fp64", P.SDR_PREC_F64), ("f32_refined", P.SDR_PREC_F32_REFINED)):
+        solver = P.Solver(N, cfg["m"], cfg["k"], cfg["t"], cfg["s"], cfg["zeta"], cfg["seed"], cfg["rel_tol"],
+                          precision=prec, inner_rel_tol=cfg["inner_rel_tol"])
+        x = torch.zeros(N, dtype=torch.float64, device=dev)
+        stats_list = []
+        clocks = ClockSampler()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        xs[name] = []
+        for i in range(nsys):
+            if i == args.warmup:
+                torch.cuda.synchronize()
+                clocks.start()
+                e0.record(stream)
+            if i > 0:
+                solver.recycle(mats[i], 0)
+            x.zero_()
+            st, stats = P.sdr_solve(solver.h, mats[i], bs[i], x)
+            if st != 0:
+                raise RuntimeError(f"{name} system {i}: status {st} {stats}")
+            if i >= args.warmup:
+                stats_list.append(stats)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                xs[name].append(x.clone())
+                e0b = torch.cuda.Event(enable_timing=True)
+                e0b.record(stream)
+                out.setdefault(name + "_ms", []).append(e0.elapsed_time(e1))
+                e0 = e0b
+        ck = clocks.stop()
+        out[name] = dict(ms_per_system=sum(out[name + "_ms"]) / len(out[name + "_ms"]), clocks=ck,
+                         cycles=sum(s_["cycles"] for s_ in stats_list) / len(stats_list),
+                         refinements=sum(s_["refinements"] for s_ in stats_list) / len(stats_list),
+                         arnoldi_steps=sum(s_["arnoldi_steps"] for s_ in stats_list) / len(stats_list),
+                         final_rel_res=max(s_["final_rel_res"] for s_ in stats_list))
+        solver.close()
+    errs = [float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(xs["f32_refined"], xs["fp64"])]
+    f32, f64 = out["f32_refined"], out["fp64"]
+    return dict(
+        metric="time-to-1e-10 true relative residual per system, float32 solver in float64 refinement",
+        value=f32["ms_per_system"], unit="ms/system", n_gpus=1, steps=args.steps, warmup=args.warmup,
+        ms_per_step=f32["ms_per_system"], higher_is_better=False, scaling="weak", vs_baseline=None,
+        dtype="f32 (inner) / f64 (refinement, sketched QR, eigenproblem)", data="synthetic",
+        config=dict(workload=cfg["workload"], N=N, nnz=nnz, m=cfg["m"], k=cfg["k"], t=cfg["t"], s=cfg["s"],
+                    zeta=cfg["zeta"], rel_tol=cfg["rel_tol"], inner_rel_tol=cfg["inner_rel_tol"],
+                    recycling="exact", l2="inputs larger than L2"),
+        fp64_gpu=dict(ms_per_system=f64["ms_per_system"], cycles=f64["cycles"], arnoldi_steps=f64["arnoldi_steps"],
+                      final_rel_res=f64["final_rel_res"]),
+        refined=dict(refinements=f32["refinements"], inner_cycles=f32["cycles"], final_rel_res=f32["final_rel_res"]),
+        speedup_vs_fp64=f64["ms_per_system"] / f32["ms_per_system"],
+        x_rel_diff_vs_fp64=dict(max=max(errs), mean=sum(errs) / len(errs)),
+        clocks=f32["clocks"])
+
+
 # --------------------------------------------------------------------------- oracle arm
 ORACLE_SAMPLE_STEPS = 12
 
@@ -322,6 +406,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--breakdown", action="store_true", help="print the per-kernel-class times to stderr")
+    ap.add_argument("--workload", default=WORKLOAD["workload"], choices=[WORKLOAD["workload"], F32IR["workload"]])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -336,6 +421,10 @@ def main():
         torch.distributed.init_process_group("nccl")
     import __graft_entry__ as g
     g.build()
+    if args.workload == F32IR["workload"]:
+        if rank == 0:
+            print(json.dumps(run_form_f32ir(args)), flush=True)
+        return
     res = run_gpu(args, rank, world)
     ms_per_system = res["ms"] / res["systems"]
     if world > 1:
