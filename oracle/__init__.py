@@ -12,4 +12,4 @@ Modules:
               driver of Section 3.6 (exact and inexact recycling)
   adjoint  -- gradients of L = ||x(theta) - x_t||^2 through A(theta) x = b
 """
-from . import sketch, sdr  # noqa: F401
+from . import adjoint, sketch, sdr  # noqa: F401
