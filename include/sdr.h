@@ -200,6 +200,33 @@ sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y);
 sdr_status sdr_sketch_noalloc(const double* x, int64_t n, int32_t s, int32_t zeta, uint64_t seed, double* y,
                               void* stream);
 
+/* ---- Differentiable solve (the adjoint form) ----------------------------
+ * For x = A^{-1} b and a scalar loss L(x), the adjoint method gives
+ * dL/db = lambda with A^T lambda = dL/dx, and dL/dA_ij = -lambda_i x_j on the
+ * stored entries.  The paper has no counterpart: these calls serve the
+ * transposed solves that a gradient needs, each carried out by sdr_solve on a
+ * second handle whose recycle space (Section 3.6) persists from call to call.
+ *
+ * Transposed sparsity pattern of A (A: host pointer to a CSR descriptor of
+ * device arrays).  rowptrT (n+1), colT (nnz), perm (nnz): device outputs;
+ * the values of A^T are val[perm[q]], q = 0..nnz-1, and each row of colT is
+ * sorted by column (deterministic).  work: device scratch of 2n int32.
+ * Column indices must lie in [0, n).  Asynchronous on stream.
+ * Errors: INVALID_ARG (null pointer, n or nnz out of int32 range), CUDA. */
+sdr_status sdr_csr_transpose(const sdr_csr* A, int32_t* rowptrT, int32_t* colT, int32_t* perm, int32_t* work,
+                             void* stream);
+
+/* out[q] = val[perm[q]] for q < nnz (device pointers; perm from
+ * sdr_csr_transpose).  Asynchronous on stream.  Errors: INVALID_ARG, CUDA. */
+sdr_status sdr_gather_values(const double* val, const int32_t* perm, int64_t nnz, double* out, void* stream);
+
+/* grad[p] = -lambda[i] * x[col[p]] for every stored entry p of row i of A
+ * (host CSR descriptor of device arrays; lambda, x: device, n entries;
+ * grad: device, nnz entries, written).  Asynchronous on stream.
+ * Errors: INVALID_ARG, CUDA. */
+sdr_status sdr_value_gradient(const sdr_csr* A, const double* lambda, const double* x, double* grad,
+                              void* stream);
+
 /* Sketched residual norms of every Arnoldi step of the last sdr_solve, in
  * order, and the per-cycle log.  sres: host pointer with room for cap_steps
  * doubles (may be NULL).  log: host pointer with room for cap_cycles entries

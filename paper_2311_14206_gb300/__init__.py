@@ -26,3 +26,4 @@ from .sdr import (  # noqa: F401
     sdr_sketch_noalloc,
     sdr_solve,
 )
+from .adjoint import AdjointPair, SDRSolve  # noqa: F401,E402

@@ -92,6 +92,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sdr_recycle_import": ([vp, P(sdr_csr), i64, i32, vp, vp, vp], i32),
         "sdr_profile": ([vp, i32], i32),
         "sdr_profile_get": ([vp, P(sdr_kernel_time), i32, P(i32)], i32),
+        "sdr_csr_transpose": ([P(sdr_csr), vp, vp, vp, vp, vp], i32),
+        "sdr_gather_values": ([vp, vp, i64, vp, vp], i32),
+        "sdr_value_gradient": ([P(sdr_csr), vp, vp, vp, vp], i32),
         "sdr_status_string": ([i32], ctypes.c_char_p),
         "sdr_abi_version": ([], i32),
     }
