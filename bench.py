@@ -15,6 +15,11 @@ oracle on a bounded sample of the same workload (single thread).
 
 --impl reference runs the oracle instead (host cores only).
 
+--workload vcdiff_512_adjoint measures the adjoint form: ten gradient-descent
+steps on L = ||x(theta) - x_t||^2 for the 512 x 512 variable-coefficient
+operator, each a forward and an adjoint solve, with recycled spaces and from
+cold starts.
+
 --workload cd3d_256_seq20_fp32ir measures the refined form instead: 3D
 convection-diffusion 256^3 (N = 16,777,216), the same perturbed sequence,
 m = 80, k = 20, s = 400, true relative residual 1e-10, solved by the float64
@@ -331,6 +336,75 @@ def run_form_f32ir(args):
         clocks=f32["clocks"])
 
 
+# --------------------------------------------------------------------------- adjoint form
+ADJ = dict(workload="vcdiff_512_adjoint", n=512, conv=(10.0, 10.0), theta_sd=0.5, opt_steps=10,
+           m=60, k=15, t=2, s=300, zeta=8, rel_tol=1e-8, seed=231114206, lr=0.05)
+
+
+def run_form_adjoint(args):
+    """Ten gradient-descent steps on L = ||x(theta) - x_t||^2 at 512 x 512: each
+    step a forward and an adjoint GMRES-SDR solve (autograd through SDRSolve),
+    with the recycle spaces carried from step to step, and the same steps with
+    every solve started from an empty recycle space."""
+    import torch
+    import workloads as W
+    import paper_2311_14206_gb300 as P
+    from paper_2311_14206_gb300.adjoint import solve
+    from workloads.vcdiff_torch import vcdiff_pattern, vcdiff_values
+
+    cfg = ADJ
+    n = cfg["n"]
+    N = n * n
+    rp, cl = vcdiff_pattern(n)
+    rp = torch.as_tensor(rp, device="cuda")
+    cl = torch.as_tensor(cl, device="cuda")
+    theta0 = torch.as_tensor(W.theta_field(n, cfg["theta_sd"]), device="cuda")
+    b = torch.as_tensor(W.rhs(N, 0), device="cuda")
+    x_t = torch.as_tensor(W.target_field(N) / (n + 1) ** 2, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    for mode in ("recycled", "cold"):
+        pair = P.AdjointPair(N, rp, cl, cfg["m"], cfg["k"], cfg["t"], cfg["s"], cfg["zeta"], cfg["seed"],
+                             cfg["rel_tol"])
+        theta = theta0.clone()
+        step_ms, losses, cyc = [], [], []
+        scale = None
+        for it in range(args.warmup + cfg["opt_steps"]):
+            if mode == "cold":
+                pair.fwd.recycle(None, 2)
+                pair.adj.recycle(None, 2)
+            th = theta.clone().requires_grad_(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            x = solve(vcdiff_values(n, th), b, pair)
+            L = torch.sum((x - x_t) ** 2)
+            L.backward()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            g = th.grad
+            if scale is None:
+                scale = float(g.abs().max())
+            with torch.no_grad():
+                theta -= cfg["lr"] * g / scale
+            if it >= args.warmup:
+                step_ms.append(e0.elapsed_time(e1))
+                losses.append(float(L.detach()))
+                cyc.append(pair.last_stats["forward"]["cycles"] + pair.last_stats["adjoint"]["cycles"])
+        pair.close()
+        out[mode] = dict(ms_per_opt_step=sum(step_ms) / len(step_ms), loss_first=losses[0], loss_last=losses[-1],
+                         cycles_per_opt_step=sum(cyc) / len(cyc))
+    r, c = out["recycled"], out["cold"]
+    return dict(
+        metric="time per optimisation step (forward + adjoint solve to 1e-8) with recycled spaces",
+        value=r["ms_per_opt_step"], unit="ms/step", n_gpus=1, steps=cfg["opt_steps"], warmup=args.warmup,
+        ms_per_step=r["ms_per_opt_step"], higher_is_better=False, scaling="weak", vs_baseline=None,
+        dtype="f64", data="synthetic",
+        config=dict(workload=cfg["workload"], N=N, m=cfg["m"], k=cfg["k"], t=cfg["t"], s=cfg["s"], zeta=cfg["zeta"],
+                    rel_tol=cfg["rel_tol"], optimiser=f"gradient descent, step {cfg['lr']} / max|g_0|"),
+        recycled=r, cold_start=c, speedup_vs_cold=c["ms_per_opt_step"] / r["ms_per_opt_step"])
+
+
 # --------------------------------------------------------------------------- oracle arm
 ORACLE_SAMPLE_STEPS = 12
 
@@ -406,7 +480,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--breakdown", action="store_true", help="print the per-kernel-class times to stderr")
-    ap.add_argument("--workload", default=WORKLOAD["workload"], choices=[WORKLOAD["workload"], F32IR["workload"]])
+    ap.add_argument("--workload", default=WORKLOAD["workload"],
+                    choices=[WORKLOAD["workload"], F32IR["workload"], ADJ["workload"]])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -421,9 +496,10 @@ def main():
         torch.distributed.init_process_group("nccl")
     import __graft_entry__ as g
     g.build()
-    if args.workload == F32IR["workload"]:
+    if args.workload in (F32IR["workload"], ADJ["workload"]):
         if rank == 0:
-            print(json.dumps(run_form_f32ir(args)), flush=True)
+            fn = run_form_f32ir if args.workload == F32IR["workload"] else run_form_adjoint
+            print(json.dumps(fn(args)), flush=True)
         return
     res = run_gpu(args, rank, world)
     ms_per_system = res["ms"] / res["systems"]
