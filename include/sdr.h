@@ -79,7 +79,12 @@ typedef enum {
  *   inner_rel_tol  refined form: relative tolerance of each inner solve
  *              (0 selects 1e-4).
  *   test_flags bit 0: take the truncated-SVD path of the harmonic-Ritz step
- *              even when the full-rank certificate holds (for tests).
+ *              even when the full-rank certificate holds (for tests);
+ *              bit 1: launch every kernel directly instead of replaying each
+ *              restart cycle from a captured CUDA graph.  With graphs (the
+ *              default) sdr_solve first copies A, b and x into buffers the
+ *              handle owns, so that one graph per cycle state serves every
+ *              later solve of the same size.
  */
 #define SDR_PREC_F64 0
 #define SDR_PREC_F32_REFINED 1
@@ -156,6 +161,25 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
  * Returns OK, NOT_CONVERGED (x holds the last iterate), BREAKDOWN, RANK,
  * INVALID_ARG or CUDA. */
 sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x, sdr_stats* stats);
+
+/* Solve count independent systems, one per handle (each handle with its own
+ * stream and recycle space; a handle appears at most once): A_i x_i = b_i
+ * exactly as sdr_solve would, but driven in lockstep.  In each round the
+ * library issues one restart cycle of every unfinished system (on the
+ * handles' streams, so the systems' kernels run concurrently) and then reads
+ * every issued cycle's outcome; a handle's cycle is replayed from a CUDA graph
+ * captured on first use.
+ *   hs: host array of count handles (SDR_PREC_F64).  As: host array of count
+ *   CSR descriptors.  bs, xs: host arrays of count device pointers.
+ *   stats: host array of count entries, or NULL.
+ * Returns OK when every system converged, else the first non-OK status of
+ * the systems in order (INVALID_ARG / NOT_IMPLEMENTED before any work). */
+sdr_status sdr_solve_batch(int32_t count, sdr_handle* const* hs, const sdr_csr* As, const double* const* bs,
+                           double* const* xs, sdr_stats* stats);
+
+/* sdr_recycle for count handles (mode as in sdr_recycle), the SAU
+ * recomputations of all handles issued before any is waited for. */
+sdr_status sdr_recycle_batch(int32_t count, sdr_handle* const* hs, const sdr_csr* As, int32_t mode);
 
 /* Prepare the recycle space for the next system in a sequence (Section 3.6).
  *   mode 0 (exact): keep U and SU, recompute SAU = S A_next U with k products

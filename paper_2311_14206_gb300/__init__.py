@@ -24,6 +24,8 @@ from .sdr import (  # noqa: F401
     sdr_recycle_import,
     sdr_sketch,
     sdr_sketch_noalloc,
+    sdr_recycle_batch,
     sdr_solve,
+    sdr_solve_batch,
 )
 from .adjoint import AdjointPair, SDRSolve  # noqa: F401,E402

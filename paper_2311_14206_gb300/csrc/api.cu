@@ -9,6 +9,7 @@
 #include <cstring>
 #include <cmath>
 #include <cstddef>
+#include <memory>
 #include <vector>
 
 #include "../../include/sdr.h"
@@ -33,7 +34,9 @@ struct Prof {
 struct sdr_handle {
   sdr_params p;
   int64_t n_max;
-  cudaStream_t st;   // the caller's stream: Arnoldi kernels and everything outside a cycle
+  cudaStream_t ust;  // the caller's stream: every call is ordered after earlier work on it
+  cudaStream_t st = nullptr;   // the handle's main stream: Arnoldi kernels and everything outside a cycle
+  cudaEvent_t evIn = nullptr, evOut = nullptr;  // fork from / join into the caller's stream
   cudaStream_t st2 = nullptr;  // control stream: dense steps and true-residual checks
   std::vector<cudaEvent_t> evS;  // evS[j]: step j's SpMV (column j sketched and finished)
   std::vector<cudaEvent_t> evD;  // evD[j]: dense step j and its check
@@ -53,6 +56,25 @@ struct sdr_handle {
   int prec = SDR_PREC_F64;   // storage type of the tall arrays: double, or float (refined form)
   void* rhs32 = nullptr;     // refined form: float32 right-hand side of the inner solve
   void* dx32 = nullptr;      // refined form: float32 inner solution
+  Ctl* hc = nullptr;         // pinned host copy of the control block, read after each cycle
+  // Cycle graphs.  A cycle's launch sequence depends only on (kh, cu, rb) and
+  // on the buffers it touches; the caller's A, b and x are first copied into
+  // handle-owned staging buffers so that one captured graph per state serves
+  // every later solve of the same size.
+  bool use_graphs = true;
+  int32_t* st_rowptr = nullptr;
+  int32_t* st_col = nullptr;
+  double* st_val = nullptr;
+  float* st_val32 = nullptr;
+  int64_t st_nnz_cap = 0;
+  double* st_b = nullptr;
+  double* st_x = nullptr;
+  struct GraphEntry {
+    int64_t n, nnz;
+    int kh, cu, rb, xpar, kernels;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
 };
 
 namespace {
@@ -145,7 +167,25 @@ cudaError_t prof_collect(sdr_handle* h) {
   } while (0)
 #define SDR_LAUNCH(h, cls, call) SDR_LAUNCH_ON(h, cls, (h)->st, call)
 
+// A call's work runs on the handle's own streams (a legacy default stream
+// cannot be captured into a graph); it starts after the work already queued
+// on the caller's stream and the caller's stream waits for it on return.
+struct StreamGuard {
+  sdr_handle* h;
+  explicit StreamGuard(sdr_handle* hh) : h(hh) {
+    if (cudaEventRecord(h->evIn, h->ust) == cudaSuccess) cudaStreamWaitEvent(h->st, h->evIn, 0);
+  }
+  ~StreamGuard() {
+    if (cudaEventRecord(h->evOut, h->st) == cudaSuccess) cudaStreamWaitEvent(h->ust, h->evOut, 0);
+  }
+  StreamGuard(const StreamGuard&) = delete;
+  StreamGuard& operator=(const StreamGuard&) = delete;
+};
+
 }  // namespace
+
+template <typename T>
+static sdr_status issue_sau(sdr_handle* h, const sdr_csr* A, int64_t n);
 
 extern "C" {
 
@@ -173,7 +213,16 @@ sdr_status sdr_destroy(sdr_handle* h) {
   for (cudaEvent_t e : h->evD) cudaEventDestroy(e);
   if (h->evFork) cudaEventDestroy(h->evFork);
   if (h->evJoin) cudaEventDestroy(h->evJoin);
+  if (h->st) cudaStreamSynchronize(h->st);
   if (h->st2) cudaStreamDestroy(h->st2);
+  if (h->st) cudaStreamDestroy(h->st);
+  if (h->evIn) cudaEventDestroy(h->evIn);
+  if (h->evOut) cudaEventDestroy(h->evOut);
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  if (h->hc) cudaFreeHost(h->hc);
+  cudaFree(h->st_col);
+  cudaFree(h->st_val);
+  cudaFree(h->st_val32);
   for (void* q : h->allocs) cudaFree(q);
   delete h;
   return SDR_OK;
@@ -194,7 +243,7 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   if (!(h->p.inner_rel_tol > 0.0)) h->p.inner_rel_tol = 1e-4;
   h->prec = p->precision;
   h->n_max = n_max;
-  h->st = (cudaStream_t)stream;
+  h->ust = (cudaStream_t)stream;
   cudaGetDevice(&h->device);
   WS& ws = h->ws;
   ws.n = n_max;
@@ -234,6 +283,11 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
     tall(&h->rhs32, (size_t)N);
     tall(&h->dx32, (size_t)N);
   }
+  chk(halloc(h, &h->st_rowptr, (size_t)N + 1));
+  chk(halloc(h, &h->st_b, (size_t)N));
+  chk(halloc(h, &h->st_x, (size_t)N));
+  chk(cudaMallocHost((void**)&h->hc, sizeof(Ctl)));
+  h->use_graphs = (p->test_flags & 2) == 0;
   const int tileR = sketch_tile_rows(p->zeta);
   const int64_t ntiles = (N + tileR - 1) / tileR;
   ws.ntiles = (int)ntiles;
@@ -247,7 +301,10 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   chk(halloc(h, &ws.accV, CYCLE_SCRATCH_WORDS));
   ws.tctr = (int*)(ws.accV + (size_t)(M_MAX + 2) * 2 * S_MAX);
   chk(halloc(h, &ws.part3, (size_t)ws.grid_max * 2 * NPART));
+  chk(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
   chk(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking));
+  chk(cudaEventCreateWithFlags(&h->evIn, cudaEventDisableTiming));
+  chk(cudaEventCreateWithFlags(&h->evOut, cudaEventDisableTiming));
   chk(cudaEventCreateWithFlags(&h->evFork, cudaEventDisableTiming));
   chk(cudaEventCreateWithFlags(&h->evJoin, cudaEventDisableTiming));
   for (int j = 0; j <= M_MAX + 1 && e == cudaSuccess; ++j) {
@@ -318,185 +375,263 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
 
 namespace {
 
-// Outcome of a run of restart cycles (one sdr_solve of the float64 solver, or
-// one inner solve of the refined form).
+// State of a run of restart cycles (one sdr_solve of the float64 solver, or
+// one inner solve of the refined form), advanced one cycle at a time so that
+// a batch of handles can be driven in lockstep.
+template <typename T>
 struct CycleRun {
+  sdr_handle* h = nullptr;
+  WS ws;
+  CsrDev Ad;
+  const T* b = nullptr;
+  T* x = nullptr;
+  T* xcur = nullptr;
+  T* xoth = nullptr;
+  int rb = 0;
+  int max_cycles = 0;
   int cycles = 0, full_svd = 0;
-  bool converged = false;
+  bool converged = false, active = false;
   sdr_status status = SDR_OK;
-  Ctl hc;
+  Ctl hc;  // control block after the last completed cycle
 };
+
+// One cycle's launches (Algorithm 1): the Arnoldi kernels on st, the dense
+// step and the true-residual check of each column on st2, the cycle end on st.
+// Two streams per cycle: the dense step of column j-1 needs step j's SpMV
+// (which sketches and finishes column j); step j waits for the control work
+// of column j - SPEC_LAG, so it knows whether an earlier check ended the cycle.
+template <typename T>
+sdr_status issue_cycle(sdr_handle* h, const WS& ws, const CsrDev& Ad, const T* b, T* xcur, T* xoth, int rb,
+                       int cu, int kh) {
+  cudaStream_t st = h->st, st2 = h->st2;
+  const int m = ws.m;
+  unsigned long long* accR = ws.acc + 2 * S_MAX;
+  const T* vcol[M_MAX + 1];
+  vcol[0] = (const T*)ws.R[rb];
+  for (int c = 1; c <= m; ++c) vcol[c] = tall_col<T>(ws.Vs, ws.ldv, c - 1);
+  const T* Ucur = (const T*)ws.U[cu];
+  SDR_CK(cudaMemsetAsync(ws.accV, 0, CYCLE_SCRATCH_WORDS * sizeof(unsigned long long), st));
+  SDR_LAUNCH(h, SDR_K_CYCLE_INIT, launch_cycle_head(ws, kh, accR, h->p.persist_safety, st));
+  SDR_CK(cudaEventRecord(h->evFork, st));
+  SDR_CK(cudaStreamWaitEvent(st2, h->evFork, 0));
+  SDR_LAUNCH_ON(h, SDR_K_CYCLE_INIT, st2, launch_cycle_qr(ws, ws.SAU[cu], kh, st2));
+  for (int j = 0; j <= m; ++j) {
+    if (j >= SPEC_LAG) SDR_CK(cudaStreamWaitEvent(st, h->evD[j - SPEC_LAG], 0));
+    if (j < m) {
+      SDR_LAUNCH(h, SDR_K_SPMV_DOTS, launch_spmv_dots<T>(ws, Ad, vcol, j, st));
+    } else {
+      SDR_LAUNCH(h, SDR_K_SKETCH, launch_sketch_col<T>(ws, vcol[m], m, st));
+    }
+    if (j >= 1) {
+      SDR_CK(cudaEventRecord(h->evS[j], st));
+      SDR_CK(cudaStreamWaitEvent(st2, h->evS[j], 0));
+      SDR_LAUNCH_ON(h, SDR_K_STEP_DENSE, st2, launch_step_dense(ws, j - 1, kh, cu, accR, st2));
+      SDR_LAUNCH_ON(h, SDR_K_CHECK_GEMV, st2, launch_check_gemv<T>(ws, Ucur, vcol, xcur, xoth, kh, j - 1, cu, st2));
+      SDR_LAUNCH_ON(h, SDR_K_CHECK_RESIDUAL, st2,
+                    launch_residual<T>(ws, Ad, b, xoth, (T*)ws.R[1 - rb], accR, j - 1, 1, st2));
+      SDR_CK(cudaEventRecord(h->evD[j - 1], st2));
+    }
+    if (j < m) SDR_LAUNCH(h, SDR_K_UPDATE_SKETCH, launch_update_sketch<T>(ws, vcol, (T*)vcol[j + 1], j, st));
+  }
+  SDR_CK(cudaEventRecord(h->evJoin, st2));
+  SDR_CK(cudaStreamWaitEvent(st, h->evJoin, 0));
+  for (int part = 0; part < CYCLE_END_PARTS; ++part)
+    SDR_LAUNCH(h, part == 0 ? SDR_K_CYCLE_END : SDR_K_CE_RINV + part - 1,
+               launch_cycle_end_part(part, ws, kh, cu, ws.SU[cu], ws.SAU[cu], ws.SU[1 - cu], ws.SAU[1 - cu], st));
+  SDR_LAUNCH(h, SDR_K_RECYCLE_GEMM, launch_recycle_gemm<T>(ws, Ucur, vcol, (T*)ws.U[1 - cu], kh, cu, 1 - cu, st));
+  return SDR_OK;
+}
+
+// Issue one cycle, through a cached CUDA graph when the handle uses graphs
+// and per-launch profiling is off.
+template <typename T>
+sdr_status launch_cycle(CycleRun<T>& r) {
+  sdr_handle* h = r.h;
+  const int cu = h->cu, kh = h->kh;
+  const int xpar = r.xcur == r.x ? 0 : 1;
+  if (!h->use_graphs || h->prof.on) return issue_cycle<T>(h, r.ws, r.Ad, r.b, r.xcur, r.xoth, r.rb, cu, kh);
+  for (auto& g : h->graphs) {
+    if (g.n == r.Ad.n && g.nnz == r.Ad.nnz && g.kh == kh && g.cu == cu && g.rb == r.rb && g.xpar == xpar) {
+      h->launches += g.kernels;
+      return cuda_status(cudaGraphLaunch(g.exec, h->st));
+    }
+  }
+  const int before = h->launches;
+  SDR_CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+  const sdr_status s1 = issue_cycle<T>(h, r.ws, r.Ad, r.b, r.xcur, r.xoth, r.rb, cu, kh);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e1 = cudaStreamEndCapture(h->st, &graph);
+  if (s1 != SDR_OK || e1 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return s1 != SDR_OK ? s1 : cuda_status(e1);
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  SDR_CK(e2);
+  sdr_handle::GraphEntry g{r.Ad.n, r.Ad.nnz, kh, cu, r.rb, xpar, h->launches - before, exec};
+  h->graphs.push_back(g);
+  return cuda_status(cudaGraphLaunch(exec, h->st));
+}
+
+// Solve start: ||b||, tol, r0 = b - A x with S r0; the control block is
+// copied to the pinned host copy (read by run_complete_init).
+template <typename T>
+sdr_status run_begin(CycleRun<T>& r, sdr_handle* h, const CsrDev& Ad, const T* b, T* x, double rel_tol,
+                     int max_cycles) {
+  r.h = h;
+  r.ws = h->ws;
+  r.ws.n = Ad.n;
+  r.Ad = Ad;
+  r.b = b;
+  r.x = x;
+  r.xcur = x;
+  r.xoth = (T*)r.ws.Xw;
+  r.rb = 0;
+  r.max_cycles = max_cycles;
+  r.active = false;
+  r.converged = false;
+  r.status = SDR_OK;
+  unsigned long long* accR = r.ws.acc + 2 * S_MAX;
+  SDR_LAUNCH(h, SDR_K_SOLVE_INIT, launch_solve_init_x<T>(r.ws, Ad, b, x, rel_tol, h->st));
+  SDR_LAUNCH(h, SDR_K_RESIDUAL0, launch_residual<T>(r.ws, Ad, b, x, (T*)r.ws.R[0], accR, -1, 0, h->st));
+  SDR_CK(cudaMemcpyAsync(h->hc, r.ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st));
+  return SDR_OK;
+}
+
+template <typename T>
+sdr_status run_complete_init(CycleRun<T>& r) {
+  SDR_CK(cudaStreamSynchronize(r.h->st));
+  r.hc = *r.h->hc;
+  r.converged = r.hc.converged != 0;
+  r.active = !r.converged && r.cycles < r.max_cycles;
+  return SDR_OK;
+}
+
+template <typename T>
+sdr_status run_issue(CycleRun<T>& r) {
+  const sdr_status s = launch_cycle<T>(r);
+  if (s != SDR_OK) return s;
+  SDR_CK(cudaMemcpyAsync(r.h->hc, r.ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, r.h->st));
+  return SDR_OK;
+}
+
+// Read the cycle's outcome and advance the host state (buffer parities,
+// recycle dimension, convergence).
+template <typename T>
+sdr_status run_complete(CycleRun<T>& r) {
+  sdr_handle* h = r.h;
+  SDR_CK(cudaStreamSynchronize(h->st));
+  r.hc = *h->hc;
+  const Ctl& hc = r.hc;
+  ++r.cycles;
+  if (hc.jf > 0) {
+    h->cu = 1 - h->cu;
+    h->kh = hc.kprime;
+    T* t = r.xcur;
+    r.xcur = r.xoth;
+    r.xoth = t;
+    r.rb = 1 - r.rb;
+    if (hc.svd_path) ++r.full_svd;
+  }
+  r.converged = hc.converged != 0;
+  if (!r.converged && (hc.bd_dense || !std::isfinite(hc.res))) r.status = SDR_ERR_BREAKDOWN;
+  r.active = !r.converged && r.status == SDR_OK && r.cycles < r.max_cycles;
+  return SDR_OK;
+}
+
+template <typename T>
+sdr_status run_finish(CycleRun<T>& r) {
+  if (r.xcur != r.x)
+    SDR_CK(cudaMemcpyAsync(r.x, r.xcur, (size_t)r.Ad.n * sizeof(T), cudaMemcpyDeviceToDevice, r.h->st));
+  if (r.status == SDR_OK && !r.converged) r.status = SDR_ERR_NOT_CONVERGED;
+  return SDR_OK;
+}
 
 // Restarted GMRES-SDR on A x = b with tall vectors of type T, from the
 // iterate in x, for at most max_cycles cycles; x is overwritten with the
 // result.  tol = rel_tol ||b||.
 template <typename T>
 sdr_status run_cycles(sdr_handle* h, const CsrDev& Ad, const T* b, T* x, double rel_tol, int max_cycles,
-                      CycleRun& out) {
-  WS ws = h->ws;
-  ws.n = Ad.n;
-  cudaStream_t st = h->st, st2 = h->st2;
-  const int m = ws.m;
-  unsigned long long* accR = ws.acc + 2 * S_MAX;
-  SDR_LAUNCH(h, SDR_K_SOLVE_INIT, launch_solve_init_x<T>(ws, Ad, b, x, rel_tol, st));
-  T* xcur = x;
-  T* xoth = (T*)ws.Xw;
-  int rb = 0;
-  SDR_LAUNCH(h, SDR_K_RESIDUAL0, launch_residual<T>(ws, Ad, b, xcur, (T*)ws.R[rb], accR, -1, 0, st));
-  Ctl& hc = out.hc;
-  SDR_CK(cudaMemcpyAsync(&hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-  SDR_CK(cudaStreamSynchronize(st));
-  std::vector<const T*> vcol(m + 1);
-  int cycles = 0;
-  sdr_status status = SDR_OK;
-  int full_svd = 0;
-  bool converged = hc.converged != 0;
-  while (!converged && cycles < max_cycles) {
-    vcol[0] = (const T*)ws.R[rb];
-    for (int c = 1; c <= m; ++c) vcol[c] = tall_col<T>(ws.Vs, ws.ldv, c - 1);
-    const int cu = h->cu, kh = h->kh;
-    const T* Ucur = (const T*)ws.U[cu];
-    // Two streams per cycle.  The Arnoldi stream (st) runs the SpMV, sketch
-    // and update of every step; the control stream (st2) runs the one-CTA
-    // dense step of each column and the true-residual check it may call for.
-    // The dense step of column j-1 needs step j's SpMV (which sketches and
-    // finishes column j); step j waits for the control work of column
-    // j - SPEC_LAG, so it knows whether an earlier check ended the cycle.
-    SDR_CK(cudaMemsetAsync(ws.accV, 0, CYCLE_SCRATCH_WORDS * sizeof(unsigned long long), st));
-    SDR_LAUNCH(h, SDR_K_CYCLE_INIT, launch_cycle_head(ws, kh, accR, h->p.persist_safety, st));
-    SDR_CK(cudaEventRecord(h->evFork, st));
-    SDR_CK(cudaStreamWaitEvent(st2, h->evFork, 0));
-    SDR_LAUNCH_ON(h, SDR_K_CYCLE_INIT, st2, launch_cycle_qr(ws, ws.SAU[cu], kh, st2));
-    for (int j = 0; j <= m; ++j) {
-      if (j >= SPEC_LAG) SDR_CK(cudaStreamWaitEvent(st, h->evD[j - SPEC_LAG], 0));
-      if (j < m) {
-        SDR_LAUNCH(h, SDR_K_SPMV_DOTS, launch_spmv_dots<T>(ws, Ad, vcol.data(), j, st));
-      } else {
-        SDR_LAUNCH(h, SDR_K_SKETCH, launch_sketch_col<T>(ws, vcol[m], m, st));
-      }
-      if (j >= 1) {
-        SDR_CK(cudaEventRecord(h->evS[j], st));
-        SDR_CK(cudaStreamWaitEvent(st2, h->evS[j], 0));
-        SDR_LAUNCH_ON(h, SDR_K_STEP_DENSE, st2, launch_step_dense(ws, j - 1, kh, cu, accR, st2));
-        SDR_LAUNCH_ON(h, SDR_K_CHECK_GEMV, st2,
-                      launch_check_gemv<T>(ws, Ucur, vcol.data(), xcur, xoth, kh, j - 1, cu, st2));
-        SDR_LAUNCH_ON(h, SDR_K_CHECK_RESIDUAL, st2,
-                      launch_residual<T>(ws, Ad, b, xoth, (T*)ws.R[1 - rb], accR, j - 1, 1, st2));
-        SDR_CK(cudaEventRecord(h->evD[j - 1], st2));
-      }
-      if (j < m) SDR_LAUNCH(h, SDR_K_UPDATE_SKETCH, launch_update_sketch<T>(ws, vcol.data(), (T*)vcol[j + 1], j, st));
-    }
-    SDR_CK(cudaEventRecord(h->evJoin, st2));
-    SDR_CK(cudaStreamWaitEvent(st, h->evJoin, 0));
-    for (int part = 0; part < CYCLE_END_PARTS; ++part)
-      SDR_LAUNCH(h, part == 0 ? SDR_K_CYCLE_END : SDR_K_CE_RINV + part - 1,
-                 launch_cycle_end_part(part, ws, kh, cu, ws.SU[cu], ws.SAU[cu], ws.SU[1 - cu], ws.SAU[1 - cu], st));
-    SDR_LAUNCH(h, SDR_K_RECYCLE_GEMM,
-               launch_recycle_gemm<T>(ws, Ucur, vcol.data(), (T*)ws.U[1 - cu], kh, cu, 1 - cu, st));
-    SDR_CK(cudaMemcpyAsync(&hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    SDR_CK(cudaStreamSynchronize(st));
-    ++cycles;
-    if (hc.jf > 0) {
-      h->cu = 1 - cu;
-      h->kh = hc.kprime;
-      T* t = xcur;
-      xcur = xoth;
-      xoth = t;
-      rb = 1 - rb;
-      if (hc.svd_path) ++full_svd;
-    }
-    converged = hc.converged != 0;
-    if (!converged && hc.bd_dense) {
-      status = SDR_ERR_BREAKDOWN;
-      break;
-    }
-    if (!converged && !std::isfinite(hc.res)) {
-      status = SDR_ERR_BREAKDOWN;
-      break;
-    }
+                      CycleRun<T>& r) {
+  sdr_status s = run_begin<T>(r, h, Ad, b, x, rel_tol, max_cycles);
+  if (s == SDR_OK) s = run_complete_init<T>(r);
+  while (s == SDR_OK && r.active) {
+    s = run_issue<T>(r);
+    if (s == SDR_OK) s = run_complete<T>(r);
   }
-  if (xcur != x) SDR_CK(cudaMemcpyAsync(x, xcur, (size_t)Ad.n * sizeof(T), cudaMemcpyDeviceToDevice, st));
-  if (status == SDR_OK && !converged) status = SDR_ERR_NOT_CONVERGED;
-  out.cycles += cycles;
-  out.full_svd += full_svd;
-  out.converged = converged;
-  out.status = status;
+  if (s == SDR_OK) s = run_finish<T>(r);
+  return s;
+}
+
+// Copy the caller's matrix into the handle's staging buffers (graphs are
+// captured against them).  Reallocates when nnz grows.
+sdr_status stage_matrix(sdr_handle* h, const sdr_csr* A, CsrDev& out) {
+  if (A->nnz > h->st_nnz_cap) {
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    cudaFree(h->st_col);
+    cudaFree(h->st_val);
+    cudaFree(h->st_val32);
+    h->st_col = nullptr;
+    h->st_val = nullptr;
+    h->st_val32 = nullptr;
+    h->st_nnz_cap = 0;
+    const size_t cap = (size_t)(A->nnz > 0 ? A->nnz : 1);
+    SDR_CK(cudaMalloc(&h->st_col, cap * sizeof(int32_t)));
+    SDR_CK(cudaMalloc(&h->st_val, cap * sizeof(double)));
+    if (h->prec == SDR_PREC_F32_REFINED) SDR_CK(cudaMalloc(&h->st_val32, cap * sizeof(float)));
+    h->st_nnz_cap = (int64_t)cap;
+  }
+  cudaStream_t st = h->st;
+  SDR_CK(cudaMemcpyAsync(h->st_rowptr, A->rowptr, (size_t)(A->n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  if (A->nnz > 0) {
+    SDR_CK(cudaMemcpyAsync(h->st_col, A->col, (size_t)A->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    SDR_CK(cudaMemcpyAsync(h->st_val, A->val, (size_t)A->nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (h->prec == SDR_PREC_F32_REFINED)
+      SDR_CK(cudaMemcpyAsync(h->st_val32, A->val32, (size_t)A->nnz * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  }
+  out = CsrDev{A->n, A->nnz, h->st_rowptr, h->st_col, h->st_val, h->st_val32};
   return SDR_OK;
 }
 
-}  // namespace
+// Per-solve bookkeeping shared by sdr_solve and sdr_solve_batch.
+struct SolveCtx {
+  CycleRun<double> run;
+  CsrDev Ad;
+  const double* b = nullptr;
+  double* x = nullptr;       // the iterate the cycles work on (staging or the caller's)
+  double* x_user = nullptr;  // the caller's x
+};
 
-extern "C" {
-
-sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x, sdr_stats* stats) {
-  if (!h || !csr_ok(h, A) || !b || !x) return SDR_ERR_INVALID_ARG;
-  WS ws = h->ws;
-  ws.n = A->n;
-  const CsrDev Ad = to_dev(A);
-  cudaStream_t st = h->st, st2 = h->st2;
+sdr_status solve_begin_f64(sdr_handle* h, const sdr_csr* A, const double* b, double* x, SolveCtx& c) {
+  cudaStream_t st = h->st;
   h->launches = 0;
   // anything a failed earlier call left on the control stream comes first
-  SDR_CK(cudaEventRecord(h->evJoin, st2));
+  SDR_CK(cudaEventRecord(h->evJoin, h->st2));
   SDR_CK(cudaStreamWaitEvent(st, h->evJoin, 0));
-  CycleRun run;
-  int refinements = 0;
-  double final_res = 0.0, bnorm = 0.0, tol = 0.0;
-  if (h->prec == SDR_PREC_F64) {
-    const sdr_status rs = run_cycles<double>(h, Ad, b, x, h->p.rel_tol, h->p.max_cycles, run);
-    if (rs != SDR_OK) return rs;
-    final_res = run.hc.res;
-    bnorm = run.hc.bnorm;
-    tol = run.hc.tol;
+  c.x_user = x;
+  if (h->use_graphs && !h->prof.on) {
+    const sdr_status s = stage_matrix(h, A, c.Ad);
+    if (s != SDR_OK) return s;
+    SDR_CK(cudaMemcpyAsync(h->st_b, b, (size_t)A->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    SDR_CK(cudaMemcpyAsync(h->st_x, x, (size_t)A->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    c.b = h->st_b;
+    c.x = h->st_x;
   } else {
-    // Iterative refinement in float64 around the float32 solver: the outer
-    // residual r = b - A x uses the float64 values; each inner solve of
-    // A d = r runs with float32 storage and arithmetic and keeps the recycle
-    // space (same matrix, new right-hand side: Section 3.6).
-    unsigned long long* accR = ws.acc + 2 * S_MAX;
-    double* r64 = h->d_tmp;
-    SDR_LAUNCH(h, SDR_K_SOLVE_INIT, launch_solve_init_x<double>(ws, Ad, b, x, h->p.rel_tol, st));
-    Ctl hc;
-    SDR_CK(cudaMemcpyAsync(&hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    SDR_CK(cudaStreamSynchronize(st));
-    bnorm = hc.bnorm;
-    tol = hc.tol;
-    const int max_refine = 40;
-    bool conv = false;
-    sdr_status inner_status = SDR_OK;
-    double last_res = INFINITY;
-    for (;;) {
-      SDR_LAUNCH(h, SDR_K_RESIDUAL0, launch_residual<double>(ws, Ad, b, x, r64, accR, -1, 0, st));
-      SDR_CK(cudaMemsetAsync(accR, 0, 2 * S_MAX * sizeof(unsigned long long), st));
-      SDR_CK(cudaMemcpyAsync(&hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-      SDR_CK(cudaStreamSynchronize(st));
-      final_res = hc.res;
-      if (!std::isfinite(final_res)) {
-        inner_status = SDR_ERR_BREAKDOWN;
-        break;
-      }
-      if (final_res < tol) {
-        conv = true;
-        break;
-      }
-      // stop when refinement no longer reduces the residual
-      if (refinements >= max_refine || (refinements > 0 && !(final_res < 0.5 * last_res))) break;
-      last_res = final_res;
-      SDR_LAUNCH(h, SDR_K_REFINE, launch_to_f32(r64, (float*)h->rhs32, (float*)h->dx32, Ad.n, st));
-      const sdr_status rs = run_cycles<float>(h, Ad, (const float*)h->rhs32, (float*)h->dx32, h->p.inner_rel_tol,
-                                              h->p.max_cycles, run);
-      if (rs != SDR_OK) return rs;
-      if (run.status == SDR_ERR_BREAKDOWN || run.status == SDR_ERR_RANK) {
-        inner_status = run.status;
-        break;
-      }
-      SDR_LAUNCH(h, SDR_K_REFINE, launch_add_f32(x, (const float*)h->dx32, Ad.n, st));
-      ++refinements;
-    }
-    run.converged = conv;
-    run.status = conv ? SDR_OK : (inner_status != SDR_OK ? inner_status : SDR_ERR_NOT_CONVERGED);
-    run.hc.res = final_res;
+    c.Ad = to_dev(A);
+    c.b = b;
+    c.x = x;
   }
-  const Ctl& hc = run.hc;
+  return run_begin<double>(c.run, h, c.Ad, c.b, c.x, h->p.rel_tol, h->p.max_cycles);
+}
+
+sdr_status solve_end(sdr_handle* h, const CycleRun<double>* run_f64, const Ctl& hc, int cycles, int full_svd,
+                     bool converged, int refinements, double final_res, double bnorm, double tol,
+                     sdr_stats* stats) {
+  (void)run_f64;
+  cudaStream_t st = h->st;
+  const WS& ws = h->ws;
   const int nh = hc.hist_n < HIST_MAX ? hc.hist_n : HIST_MAX;
   const int nl = hc.log_n < LOG_MAX ? hc.log_n : LOG_MAX;
   h->hist.assign(nh, 0.0);
@@ -507,8 +642,8 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
   SDR_CK(prof_collect(h));
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
-    stats->cycles = run.cycles;
-    stats->converged = run.converged ? 1 : 0;
+    stats->cycles = cycles;
+    stats->converged = converged ? 1 : 0;
     stats->matvecs = hc.matvecs;
     stats->sketches = hc.sketches;
     int checks = 0;
@@ -516,7 +651,7 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
     stats->true_res_evals = checks;
     stats->arnoldi_steps = hc.hist_n;
     stats->recycle_dim = h->kh;
-    stats->full_svd_cycles = run.full_svd;
+    stats->full_svd_cycles = full_svd;
     stats->kernel_launches = h->launches;
     stats->refinements = refinements;
     stats->final_res = final_res;
@@ -524,14 +659,184 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
     stats->bnorm = bnorm;
     stats->final_rel_res = bnorm > 0.0 ? final_res / bnorm : final_res;
   }
-  return run.status;
+  return SDR_OK;
+}
+
+sdr_status solve_finish_f64(sdr_handle* h, SolveCtx& c, sdr_stats* stats) {
+  SDR_CK(cudaGetLastError());
+  sdr_status s = run_finish<double>(c.run);
+  if (s != SDR_OK) return s;
+  if (c.x != c.x_user)
+    SDR_CK(cudaMemcpyAsync(c.x_user, c.x, (size_t)c.Ad.n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  const Ctl& hc = c.run.hc;
+  s = solve_end(h, &c.run, hc, c.run.cycles, c.run.full_svd, c.run.converged, 0, hc.res, hc.bnorm, hc.tol, stats);
+  return s != SDR_OK ? s : c.run.status;
+}
+
+}  // namespace
+
+extern "C" {
+
+sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x, sdr_stats* stats) {
+  if (!h || !csr_ok(h, A) || !b || !x) return SDR_ERR_INVALID_ARG;
+  StreamGuard guard(h);
+  if (h->prec == SDR_PREC_F64) {
+    SolveCtx c;
+    sdr_status s = solve_begin_f64(h, A, b, x, c);
+    if (s == SDR_OK) s = run_complete_init<double>(c.run);
+    while (s == SDR_OK && c.run.active) {
+      s = run_issue<double>(c.run);
+      if (s == SDR_OK) s = run_complete<double>(c.run);
+    }
+    if (s != SDR_OK) return s;
+    return solve_finish_f64(h, c, stats);
+  }
+  // Iterative refinement in float64 around the float32 solver: the outer
+  // residual r = b - A x uses the float64 values; each inner solve of
+  // A d = r runs with float32 storage and arithmetic and keeps the recycle
+  // space (same matrix, new right-hand side: Section 3.6).
+  WS ws = h->ws;
+  ws.n = A->n;
+  cudaStream_t st = h->st;
+  h->launches = 0;
+  SDR_CK(cudaEventRecord(h->evJoin, h->st2));
+  SDR_CK(cudaStreamWaitEvent(st, h->evJoin, 0));
+  CsrDev Ad;
+  if (h->use_graphs && !h->prof.on) {
+    const sdr_status s = stage_matrix(h, A, Ad);
+    if (s != SDR_OK) return s;
+  } else {
+    Ad = to_dev(A);
+  }
+  unsigned long long* accR = ws.acc + 2 * S_MAX;
+  double* r64 = h->d_tmp;
+  SDR_LAUNCH(h, SDR_K_SOLVE_INIT, launch_solve_init_x<double>(ws, Ad, b, x, h->p.rel_tol, st));
+  SDR_CK(cudaMemcpyAsync(h->hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  SDR_CK(cudaStreamSynchronize(st));
+  const double bnorm = h->hc->bnorm, tol = h->hc->tol;
+  const int max_refine = 40;
+  bool conv = false;
+  sdr_status status = SDR_OK;
+  double last_res = INFINITY, final_res = 0.0;
+  int refinements = 0, cycles = 0, full_svd = 0;
+  CycleRun<float> run;
+  for (;;) {
+    SDR_LAUNCH(h, SDR_K_RESIDUAL0, launch_residual<double>(ws, Ad, b, x, r64, accR, -1, 0, st));
+    SDR_CK(cudaMemsetAsync(accR, 0, 2 * S_MAX * sizeof(unsigned long long), st));
+    SDR_CK(cudaMemcpyAsync(h->hc, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    SDR_CK(cudaStreamSynchronize(st));
+    final_res = h->hc->res;
+    if (!std::isfinite(final_res)) {
+      status = SDR_ERR_BREAKDOWN;
+      break;
+    }
+    if (final_res < tol) {
+      conv = true;
+      break;
+    }
+    // stop when refinement no longer reduces the residual
+    if (refinements >= max_refine || (refinements > 0 && !(final_res < 0.5 * last_res))) break;
+    last_res = final_res;
+    SDR_LAUNCH(h, SDR_K_REFINE, launch_to_f32(r64, (float*)h->rhs32, (float*)h->dx32, Ad.n, st));
+    run = CycleRun<float>();
+    const sdr_status rs = run_cycles<float>(h, Ad, (const float*)h->rhs32, (float*)h->dx32, h->p.inner_rel_tol,
+                                            h->p.max_cycles, run);
+    if (rs != SDR_OK) return rs;
+    cycles += run.cycles;
+    full_svd += run.full_svd;
+    if (run.status == SDR_ERR_BREAKDOWN || run.status == SDR_ERR_RANK) {
+      status = run.status;
+      break;
+    }
+    SDR_LAUNCH(h, SDR_K_REFINE, launch_add_f32(x, (const float*)h->dx32, Ad.n, st));
+    ++refinements;
+  }
+  if (status == SDR_OK && !conv) status = SDR_ERR_NOT_CONVERGED;
+  const sdr_status s = solve_end(h, nullptr, run.hc, cycles, full_svd, conv, refinements, final_res, bnorm, tol,
+                                 stats);
+  return s != SDR_OK ? s : status;
+}
+
+sdr_status sdr_solve_batch(int32_t count, sdr_handle* const* hs, const sdr_csr* As, const double* const* bs,
+                           double* const* xs, sdr_stats* stats) {
+  if (count < 0 || (count > 0 && (!hs || !As || !bs || !xs))) return SDR_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || !csr_ok(hs[i], &As[i]) || !bs[i] || !xs[i]) return SDR_ERR_INVALID_ARG;
+    if (hs[i]->prec != SDR_PREC_F64) return SDR_ERR_NOT_IMPLEMENTED;
+    for (int q = 0; q < i; ++q)
+      if (hs[q] == hs[i]) return SDR_ERR_INVALID_ARG;
+  }
+  std::vector<std::unique_ptr<StreamGuard>> guards;
+  for (int i = 0; i < count; ++i) guards.emplace_back(new StreamGuard(hs[i]));
+  std::vector<SolveCtx> ctx(count);
+  for (int i = 0; i < count; ++i) {
+    const sdr_status s = solve_begin_f64(hs[i], &As[i], bs[i], xs[i], ctx[i]);
+    if (s != SDR_OK) return s;
+  }
+  for (int i = 0; i < count; ++i) {
+    const sdr_status s = run_complete_init<double>(ctx[i].run);
+    if (s != SDR_OK) return s;
+  }
+  // Lockstep rounds: one cycle of every unfinished system is issued (each on
+  // its handle's streams, so the systems' kernels run concurrently), then
+  // every issued cycle is completed.
+  for (;;) {
+    bool any = false;
+    for (int i = 0; i < count; ++i) {
+      if (!ctx[i].run.active) continue;
+      any = true;
+      const sdr_status s = run_issue<double>(ctx[i].run);
+      if (s != SDR_OK) return s;
+    }
+    if (!any) break;
+    for (int i = 0; i < count; ++i) {
+      if (!ctx[i].run.active) continue;
+      const sdr_status s = run_complete<double>(ctx[i].run);
+      if (s != SDR_OK) return s;
+    }
+  }
+  sdr_status worst = SDR_OK;
+  for (int i = 0; i < count; ++i) {
+    const sdr_status s = solve_finish_f64(hs[i], ctx[i], stats ? &stats[i] : nullptr);
+    if (s == SDR_ERR_CUDA) return s;
+    if (s != SDR_OK && worst == SDR_OK) worst = s;
+  }
+  return worst;
+}
+
+sdr_status sdr_recycle_batch(int32_t count, sdr_handle* const* hs, const sdr_csr* As, int32_t mode) {
+  if (count < 0 || (count > 0 && (!hs || (mode == 0 && !As)))) return SDR_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return SDR_ERR_INVALID_ARG;
+    if (mode == 0 && hs[i]->kh > 0 && !csr_ok(hs[i], &As[i])) return SDR_ERR_INVALID_ARG;
+  }
+  std::vector<std::unique_ptr<StreamGuard>> guards;
+  for (int i = 0; i < count; ++i) guards.emplace_back(new StreamGuard(hs[i]));
+  for (int i = 0; i < count; ++i) {
+    sdr_handle* h = hs[i];
+    if (mode == 2) {
+      h->kh = 0;
+    } else if (mode == 0 && h->kh > 0) {
+      const sdr_status s = h->prec == SDR_PREC_F64 ? issue_sau<double>(h, &As[i], As[i].n)
+                                                   : issue_sau<float>(h, &As[i], As[i].n);
+      if (s != SDR_OK) return s;
+    } else if (mode != 1 && mode != 0) {
+      return SDR_ERR_INVALID_ARG;
+    }
+  }
+  for (int i = 0; i < count; ++i) {
+    SDR_CK(cudaStreamSynchronize(hs[i]->st));
+    SDR_CK(prof_collect(hs[i]));
+  }
+  return SDR_OK;
 }
 
 }  // extern "C"
 
-// Recompute SAU = S A U column by column (exact variant, Section 3.6).
+// Recompute SAU = S A U column by column (exact variant, Section 3.6);
+// issue_sau only enqueues the work on the handle's stream.
 template <typename T>
-static sdr_status recompute_sau(sdr_handle* h, const sdr_csr* A, int64_t n) {
+static sdr_status issue_sau(sdr_handle* h, const sdr_csr* A, int64_t n) {
   WS ws = h->ws;
   ws.n = n;
   const CsrDev Ad = to_dev(A);
@@ -548,6 +853,13 @@ static sdr_status recompute_sau(sdr_handle* h, const sdr_csr* A, int64_t n) {
     SDR_CK(launch_sketch_finish(ws, accG, topG, ws.SAU[h->cu] + (int64_t)c * ws.s, h->st));
     SDR_CK(prof_end(h, h->st));
   }
+  return SDR_OK;
+}
+
+template <typename T>
+static sdr_status recompute_sau(sdr_handle* h, const sdr_csr* A, int64_t n) {
+  const sdr_status s = issue_sau<T>(h, A, n);
+  if (s != SDR_OK) return s;
   SDR_CK(cudaStreamSynchronize(h->st));
   SDR_CK(prof_collect(h));
   return SDR_OK;
@@ -577,6 +889,7 @@ extern "C" {
 
 sdr_status sdr_recycle(sdr_handle* h, const sdr_csr* A_next, int32_t mode) {
   if (!h) return SDR_ERR_INVALID_ARG;
+  StreamGuard guard(h);
   if (mode == 2) {
     h->kh = 0;
     return SDR_OK;
@@ -591,6 +904,7 @@ sdr_status sdr_recycle(sdr_handle* h, const sdr_csr* A_next, int32_t mode) {
 
 sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y) {
   if (!h || !x || !y || n <= 0 || n > h->n_max) return SDR_ERR_INVALID_ARG;
+  StreamGuard guard(h);
   WS ws = h->ws;
   ws.n = n;
   unsigned long long* accG = ws.acc + 4 * S_MAX;
@@ -651,6 +965,7 @@ sdr_status sdr_recycle_dim(sdr_handle* h, int32_t* kdim) {
 sdr_status sdr_recycle_export(sdr_handle* h, int64_t n, double* U, double* SU, double* SAU) {
   if (!h || n <= 0 || n > h->n_max) return SDR_ERR_INVALID_ARG;
   if (h->prec != SDR_PREC_F64) return SDR_ERR_NOT_IMPLEMENTED;
+  StreamGuard guard(h);
   const WS& ws = h->ws;
   const int kh = h->kh;
   if (kh == 0) return SDR_OK;
@@ -670,6 +985,7 @@ sdr_status sdr_recycle_import(sdr_handle* h, const sdr_csr* A, int64_t n, int32_
   if (!h || n <= 0 || n > h->n_max || kdim < 0 || kdim > h->ws.kmax) return SDR_ERR_INVALID_ARG;
   if (h->prec != SDR_PREC_F64) return SDR_ERR_NOT_IMPLEMENTED;
   if (kdim > 0 && !U) return SDR_ERR_INVALID_ARG;
+  StreamGuard guard(h);
   if (kdim > 0 && !SAU && !csr_ok(h, A)) return SDR_ERR_INVALID_ARG;
   const WS& ws = h->ws;
   h->kh = kdim;

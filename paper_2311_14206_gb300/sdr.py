@@ -93,6 +93,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sdr_profile": ([vp, i32], i32),
         "sdr_profile_get": ([vp, P(sdr_kernel_time), i32, P(i32)], i32),
         "sdr_csr_transpose": ([P(sdr_csr), vp, vp, vp, vp, vp], i32),
+        "sdr_solve_batch": ([i32, P(vp), P(sdr_csr), P(vp), P(vp), P(sdr_stats)], i32),
+        "sdr_recycle_batch": ([i32, P(vp), P(sdr_csr), i32], i32),
         "sdr_gather_values": ([vp, vp, i64, vp, vp], i32),
         "sdr_value_gradient": ([P(sdr_csr), vp, vp, vp, vp], i32),
         "sdr_status_string": ([i32], ctypes.c_char_p),
@@ -158,10 +160,10 @@ class CSRDevice:
 
 
 def make_params(m, k, t, s, zeta, seed, rel_tol, safety0=1.4, max_cycles=200, persist_safety=0,
-                force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0) -> sdr_params:
+                force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0, graphs=True) -> sdr_params:
     p = sdr_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety)
     p.precision = precision
-    p.test_flags = 1 if force_svd else 0
+    p.test_flags = (1 if force_svd else 0) | (0 if graphs else 2)
     p.inner_rel_tol = inner_rel_tol
     return p
 
@@ -184,6 +186,32 @@ def sdr_solve(h, A: CSRDevice, b: torch.Tensor, x: torch.Tensor, allow_not_conve
     st = lib.sdr_solve(h, ctypes.byref(csr), _ptr(b), _ptr(x), ctypes.byref(stats))
     _check(st, "sdr_solve", ok=(0, 4) if allow_not_converged else (0,))
     return st, stats.as_dict()
+
+
+def sdr_solve_batch(handles, As, bs, xs, allow_not_converged=True):
+    """Solve len(handles) independent systems in lockstep (one handle, stream and
+    recycle space each); x arrays are overwritten.  Returns (status, [stats])."""
+    lib = load_library()
+    cnt = len(handles)
+    H = (ctypes.c_void_p * cnt)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    C = (sdr_csr * cnt)(*[A.c_struct() for A in As])
+    for t in list(bs) + list(xs):
+        if t.dtype != torch.float64 or not t.is_cuda:
+            raise TypeError("b and x must be float64 CUDA tensors")
+    B = (ctypes.c_void_p * cnt)(*[b.data_ptr() for b in bs])
+    X = (ctypes.c_void_p * cnt)(*[x.data_ptr() for x in xs])
+    S = (sdr_stats * cnt)()
+    st = lib.sdr_solve_batch(cnt, H, C, B, X, S)
+    _check(st, "sdr_solve_batch", ok=(0, 4) if allow_not_converged else (0,))
+    return st, [S[i].as_dict() for i in range(cnt)]
+
+
+def sdr_recycle_batch(handles, As, mode=0):
+    lib = load_library()
+    cnt = len(handles)
+    H = (ctypes.c_void_p * cnt)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    C = (sdr_csr * cnt)(*[A.c_struct() for A in As]) if As is not None else None
+    return _check(lib.sdr_recycle_batch(cnt, H, C, mode), "sdr_recycle_batch")
 
 
 def sdr_recycle(h, A_next: CSRDevice = None, mode: int = 0):
@@ -267,11 +295,14 @@ class Solver:
     """Convenience wrapper owning one handle (GMRES-SDR for one system size)."""
 
     def __init__(self, n_max, m, k, t, s, zeta=8, seed=231114206, rel_tol=1e-8, safety0=1.4, max_cycles=200,
-                 persist_safety=0, force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0):
+                 persist_safety=0, force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0, graphs=True,
+                 stream=None):
         self.params = make_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety, force_svd,
-                                  precision, inner_rel_tol)
+                                  precision, inner_rel_tol, graphs)
         self.n_max, self.s = n_max, s
-        self.h = sdr_create(self.params, n_max)
+        self.stream = stream  # a torch.cuda.Stream the handle issues on (None: the current stream)
+        self.h = sdr_create(self.params, n_max,
+                            ctypes.c_void_p(stream.cuda_stream) if stream is not None else None)
 
     def solve(self, A: CSRDevice, b: torch.Tensor, x: torch.Tensor = None):
         if x is None:
