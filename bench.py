@@ -20,6 +20,9 @@ steps on L = ||x(theta) - x_t||^2 for the 512 x 512 variable-coefficient
 operator, each a forward and an adjoint solve, with recycled spaces and from
 cold starts.
 
+--workload cd2d_batch64 measures the batched form: 64 independent 2D systems
+(sides U{32..512}) x 5-system sequences, solved in lockstep and one at a time.
+
 --workload cd3d_256_seq20_fp32ir measures the refined form instead: 3D
 convection-diffusion 256^3 (N = 16,777,216), the same perturbed sequence,
 m = 80, k = 20, s = 400, true relative residual 1e-10, solved by the float64
@@ -418,6 +421,98 @@ def run_form_adjoint(args):
         recycled=r, cold_start=c, speedup_vs_cold=c["ms_per_opt_step"] / r["ms_per_opt_step"])
 
 
+# --------------------------------------------------------------------------- batched form
+BATCH = dict(workload="cd2d_batch64", count=64, nmin=32, nmax=512, seq=5, eps=1e-3,
+             m=40, k=10, t=2, s=100, zeta=8, rel_tol=1e-8, seed=231114206)
+
+
+def run_form_batch(args):
+    """64 independent 2D systems (sides U{32..512}, convection U[1,50]^2), each a
+    5-system perturbed sequence with its own recycle space: all systems solved
+    in lockstep by sdr_solve_batch (one stream pair per handle, cycles replayed
+    from CUDA graphs), against the same solves issued one system at a time."""
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_2311_14206_gb300 as P
+
+    cfg = BATCH
+    specs = W.batch_systems(cfg["count"], cfg["nmin"], cfg["nmax"])
+    mats, rhs, sizes = [], [], []
+    for i, (n, conv) in enumerate(specs):
+        A0 = W.make_cd2d(n, conv)
+        dvec = W.diag_perturbation(A0.n, tag=i)
+        rows = np.repeat(np.arange(A0.n), np.diff(A0.rowptr.astype(np.int64)))
+        dpos = np.nonzero(A0.col.astype(np.int64) == rows)[0]
+        rp = torch.as_tensor(A0.rowptr, device="cuda")
+        cl = torch.as_tensor(A0.col, device="cuda")
+        seq = []
+        for j in range(cfg["seq"]):
+            v = A0.val.copy()
+            v[dpos] += (j + 1) * cfg["eps"] * dvec
+            seq.append(P.CSRDevice(A0.n, rp, cl, torch.as_tensor(v, device="cuda")))
+        mats.append(seq)
+        rhs.append([torch.as_tensor(W.rhs(A0.n, 1000 * i + j), device="cuda") for j in range(cfg["seq"])])
+        sizes.append(A0.n)
+    out = {}
+    for mode in ("batched", "one_at_a_time"):
+        hs = [P.Solver(N, cfg["m"], cfg["k"], cfg["t"], cfg["s"], cfg["zeta"], cfg["seed"], cfg["rel_tol"],
+                       stream=torch.cuda.Stream()) for N in sizes]
+        xs = [torch.zeros(N, dtype=torch.float64, device="cuda") for N in sizes]
+        handles = [h.h for h in hs]
+
+        def run_seq(record):
+            cyc, worst, conv = 0, 0.0, 0
+            for j in range(cfg["seq"]):
+                A_j = [m_[j] for m_ in mats]
+                b_j = [r_[j] for r_ in rhs]
+                for x in xs:
+                    x.zero_()
+                if mode == "batched":
+                    if j > 0:
+                        P.sdr_recycle_batch(handles, A_j, 0)
+                    st, stats = P.sdr_solve_batch(handles, A_j, b_j, xs)
+                else:
+                    stats = []
+                    for i, h in enumerate(hs):
+                        if j > 0:
+                            h.recycle(A_j[i], 0)
+                        _, st1 = P.sdr_solve(h.h, A_j[i], b_j[i], xs[i])
+                        stats.append(st1)
+                if record:
+                    cyc += sum(s_["cycles"] for s_ in stats)
+                    worst = max(worst, max(s_["final_rel_res"] for s_ in stats))
+                    conv += sum(s_["converged"] for s_ in stats)
+            return cyc, worst, conv
+
+        # warm-up: capture every handle's cycle graphs on the first system, then drop the recycle spaces
+        run_seq(False)
+        P.sdr_recycle_batch(handles, None, 2)
+        torch.cuda.synchronize()
+        clocks = ClockSampler()
+        clocks.start()
+        t0 = time.perf_counter()
+        cyc, worst, conv = run_seq(True)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out[mode] = dict(total_s=wall, ms_per_solve=1e3 * wall / (cfg["count"] * cfg["seq"]), cycles=cyc,
+                         converged_solves=conv, solves=cfg["count"] * cfg["seq"], max_final_rel_res=worst,
+                         clocks=clocks.stop())
+        for h in hs:
+            h.close()
+    b_, s_ = out["batched"], out["one_at_a_time"]
+    return dict(
+        metric="time per system solve to 1e-8, 64 independent systems x 5-system sequences",
+        value=b_["ms_per_solve"], unit="ms/solve", n_gpus=1, steps=1, warmup=1, ms_per_step=1e3 * b_["total_s"],
+        higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+        config=dict(workload=cfg["workload"], systems=cfg["count"], sequence=cfg["seq"],
+                    N_total=int(sum(sizes)), N_min=int(min(sizes)), N_max=int(max(sizes)), m=cfg["m"], k=cfg["k"],
+                    t=cfg["t"], s=cfg["s"], zeta=cfg["zeta"], rel_tol=cfg["rel_tol"],
+                    timing="host wall clock around the whole sequence (the solves synchronise every cycle)"),
+        batched=b_, one_at_a_time=s_, speedup_vs_one_at_a_time=s_["total_s"] / b_["total_s"],
+        clocks=b_["clocks"])
+
+
 # --------------------------------------------------------------------------- oracle arm
 ORACLE_SAMPLE_STEPS = 12
 
@@ -494,7 +589,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--breakdown", action="store_true", help="print the per-kernel-class times to stderr")
     ap.add_argument("--workload", default=WORKLOAD["workload"],
-                    choices=[WORKLOAD["workload"], F32IR["workload"], ADJ["workload"]])
+                    choices=[WORKLOAD["workload"], F32IR["workload"], ADJ["workload"], BATCH["workload"]])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -509,9 +604,10 @@ def main():
         torch.distributed.init_process_group("nccl")
     import __graft_entry__ as g
     g.build()
-    if args.workload in (F32IR["workload"], ADJ["workload"]):
+    if args.workload in (F32IR["workload"], ADJ["workload"], BATCH["workload"]):
         if rank == 0:
-            fn = run_form_f32ir if args.workload == F32IR["workload"] else run_form_adjoint
+            fn = {F32IR["workload"]: run_form_f32ir, ADJ["workload"]: run_form_adjoint,
+                  BATCH["workload"]: run_form_batch}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     res = run_gpu(args, rank, world)
