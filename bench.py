@@ -134,7 +134,12 @@ def run_gpu(args, rank, world):
     import workloads as W
     import paper_2311_14206_gb300 as P
 
-    cfg = WORKLOAD
+    cfg = dict(WORKLOAD)
+    if args.n:  # a smaller grid of the same workload (profiler captures)
+        cfg["n"] = args.n
+        cfg["workload"] = f"cd3d_{args.n}_seq{cfg['systems']}"
+    if args.systems:
+        cfg["systems"] = args.systems
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = torch.device("cuda")
     A0, dvec, diag_pos = make_inputs(cfg)
@@ -271,7 +276,7 @@ def run_gpu(args, rank, world):
                                 peak_kind=peak_kind, unit="GB/s", frac=achieved / hbm,
                                 bytes_per_launch=rb / max(rl, 1), launches=rl, ms_per_launch=rms / max(rl, 1),
                                 traffic=None),
-                  systems=systems, agg=agg_timed, N=N, nnz=nnz)
+                  systems=systems, agg=agg_timed, N=N, nnz=nnz, workload=cfg["workload"])
     return result
 
 
@@ -588,6 +593,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--breakdown", action="store_true", help="print the per-kernel-class times to stderr")
+    ap.add_argument("--n", type=int, default=0, help="grid side of a smaller case of the default workload "
+                    "(for profiler captures; the bench line names it)")
+    ap.add_argument("--systems", type=int, default=0, help="systems of the sequence kept on the device")
     ap.add_argument("--workload", default=WORKLOAD["workload"],
                     choices=[WORKLOAD["workload"], F32IR["workload"], ADJ["workload"], BATCH["workload"]])
     args = ap.parse_args()
@@ -626,7 +634,7 @@ def main():
             metric=METRIC, value=ms_per_system, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
             ms_per_step=res["ms"] / res["systems"], higher_is_better=False, scaling="weak", vs_baseline=None,
             dtype="f64", data="synthetic",
-            config=dict(workload=WORKLOAD["workload"], N=res["N"], nnz=res["nnz"], m=100, k=20, t=2, s=480,
+            config=dict(workload=res["workload"], N=res["N"], nnz=res["nnz"], m=100, k=20, t=2, s=480,
                         zeta=8, systems=20, rel_tol=1e-8, recycling="exact", l2="inputs larger than L2",
                         parallelism=f"replicas{world}"),
             roofline=dict(bound=rf["bound"], achieved=rf["achieved"], peak=rf["peak"], unit=rf["unit"],

@@ -650,7 +650,7 @@ cudaError_t launch_check_gemv(const WS& ws, const T* U, const T* const* vcol, co
   return cudaGetLastError();
 }
 
-// U_new = W P' for the kprime recycle columns.  A CTA stages RT rows of W as
+// U_new = W P' for W wider than the shared-memory tile of k_recycle_rb.  A CTA stages RT rows of W as
 // fixed-point values in shared memory; thread (r, g) accumulates row r against
 // columns 8g .. 8g+7 of P'' (read through L1: every lane of a warp reads the
 // same coefficient).
@@ -734,16 +734,173 @@ __global__ void __launch_bounds__(128, 4) k_recycle_q(WS ws, const T* __restrict
   }
 }
 
+// U_new = W P' for the kprime recycle columns (W = [U, V(:, 0:jf)]), as an
+// exact integer product on the 32-bit multiply-add pipe.  Two CTAs share an
+// SM (one stages its tile while the other multiplies) and walk over tiles of
+// RB_ROWS rows: the tile of W is quantised into shared memory once (column l
+// scaled by 2^delta_l, unit 2^-51), and warp w computes columns
+// w*CPT .. w*CPT+CPT-1 of the tile, lane i the rows i and i+32.  Each product X Y of 52-bit integers
+// X = xh 2^26 + xl, Y = yh 2^26 + yl takes three 32x32->64 multiply-adds
+// (Karatsuba): xh yh, xl yl and (xh + xl)(yh + yl); the cross term is their
+// difference.  Every sum is exact (|terms| < 2^54, at most D_MAX of them), so
+// the result equals the exactly rounded product of the quantised operands.
+constexpr int RB_ROWS = 64;
+constexpr int RB_RPL = RB_ROWS / 32;  // rows per lane
+constexpr int RB_THREADS = 256;
+
+struct __align__(16) YK {
+  int hi, lo, sum, pad;
+};
+
+template <typename T, int CPT>
+__global__ void __launch_bounds__(RB_THREADS, 2) k_recycle_rb(WS ws, const T* __restrict__ U, Cols<T> V,
+                                                               T* __restrict__ Unew, int kh, int ucur, int unext,
+                                                               int dcap) {
+  Ctl* c = ws.ctl;
+  const int kp = c->kprime, jf = c->jf;
+  if (kp <= 0 || jf <= 0) return;
+  const int d = kh + jf;
+  constexpr int NCOL = 8 * CPT;
+  if (d > dcap || kp > NCOL) {  // cannot happen (d <= kh + m, kp <= k + 1): refuse rather than overrun
+    if (threadIdx.x == 0 && blockIdx.x == 0) c->rankfail = 1;
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char smraw[];
+  YK* ytab = (YK*)smraw;                                      // [dcap][NCOL]
+  Q52* xq = (Q52*)(smraw + (size_t)dcap * NCOL * sizeof(YK));  // [dcap][RB_ROWS]
+  __shared__ int dl[D_MAX];
+  __shared__ int fx[NCOL];
+  for (int l = threadIdx.x; l < d; l += blockDim.x) dl[l] = col_delta(c, ucur, kh, l);
+  for (int q = threadIdx.x; q < NCOL; q += blockDim.x) fx[q] = q < kp ? ws.Pexp[q] : 0;
+  for (int idx = threadIdx.x; idx < d * NCOL; idx += blockDim.x) {
+    const int l = idx / NCOL, q = idx % NCOL;
+    YK y{0, 0, 0, 0};
+    if (q < kp) {
+      const unsigned long long b = ws.Pq[l + (int64_t)q * D_MAX];  // packed (hi << 32) | lo
+      y.hi = (int)(b >> 32);
+      y.lo = (int)(unsigned)(b & 0xFFFFFFFFull);
+      y.sum = y.hi + y.lo;
+    }
+    ytab[idx] = y;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t ld = ws.ldv, n = ws.n;
+  const int64_t ntiles = (n + RB_ROWS - 1) / RB_ROWS;
+  unsigned long long um[CPT];
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) um[q] = 0ull;
+  const bool active = w * CPT < kp;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * RB_ROWS;
+    const int nr = (int)(n - r0 < RB_ROWS ? n - r0 : RB_ROWS);
+    // stage the tile: eight loads in flight per thread before any is converted
+    for (int base = threadIdx.x; base < d * RB_ROWS; base += 8 * RB_THREADS) {
+      double wv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * RB_THREADS;
+        const int l = idx / RB_ROWS, r = idx % RB_ROWS;
+        wv[u] = (idx < d * RB_ROWS && r < nr) ? (double)wcol(U, V, ld, kh, l)[r0 + r] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * RB_THREADS;
+        if (idx < d * RB_ROWS) xq[idx] = q52(wv[u], 1022, dl[idx / RB_ROWS]);
+      }
+    }
+    __syncthreads();
+    if (active) {
+      long long hh[RB_RPL][CPT], mm[RB_RPL][CPT];
+      unsigned long long ll[RB_RPL][CPT];
+#pragma unroll
+      for (int i = 0; i < RB_RPL; ++i)
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) hh[i][q] = mm[i][q] = 0, ll[i][q] = 0ull;
+      const YK* yrow = ytab + w * CPT;
+      const Q52* xrow = xq + lane;
+#pragma unroll 2
+      for (int l = 0; l < d; ++l) {
+        Q52 x[RB_RPL];
+        int xs[RB_RPL];
+#pragma unroll
+        for (int i = 0; i < RB_RPL; ++i) {
+          x[i] = xrow[l * RB_ROWS + 32 * i];
+          xs[i] = x[i].hi + (int)x[i].lo;
+        }
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+          const YK y = yrow[l * NCOL + q];
+#pragma unroll
+          for (int i = 0; i < RB_RPL; ++i) {
+            asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(hh[i][q]) : "r"(x[i].hi), "r"(y.hi));
+            asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(ll[i][q]) : "r"(x[i].lo), "r"(y.lo));
+            asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(mm[i][q]) : "r"(xs[i]), "r"(y.sum));
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) {
+        const int col = w * CPT + q;
+        if (col >= kp) continue;
+#pragma unroll
+        for (int i = 0; i < RB_RPL; ++i) {
+          const int r = lane + 32 * i;
+          if (r >= nr) continue;
+          const long long mid = mm[i][q] - hh[i][q] - (long long)ll[i][q];
+          unsigned long long lo = ll[i][q], hi = 0ull;
+          add_shifted128(lo, hi, mid, 26);
+          add_shifted128(lo, hi, hh[i][q], 52);
+          const T v = (T)i128_to_double(lo, hi, -51 + fx[col] - 51);
+          Unew[r0 + r + (int64_t)col * ld] = v;
+          const unsigned long long u = abs_bits((double)v);
+          um[q] = u > um[q] ? u : um[q];
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) {
+    const int col = w * CPT + q;
+    const unsigned long long u = warp_max_u64(um[q]);
+    if (lane == 0 && col < kp && u) atomicMax(&c->umax[unext][col], u);
+  }
+}
+
+// Shared memory of k_recycle_rb for dcap columns of W and NCOL of P.
+static size_t recycle_rb_smem(int dcap, int ncol) {
+  return (size_t)dcap * ncol * sizeof(YK) + (size_t)dcap * RB_ROWS * sizeof(Q52);
+}
+constexpr size_t RB_SMEM_MAX = 112 * 1024;  // two CTAs per SM
+
 template <typename T>
 cudaError_t launch_recycle_gemm(const WS& ws, const T* U, const T* const* vcol, T* Unew, int kh,
                                 int ucur, int unext, cudaStream_t st) {
   Cols<T> V{vcol[0], (const T*)ws.Vs};
-  const size_t sm = (size_t)D_MAX * RT * sizeof(Q52);
-  static bool attr = false;
-  cudaError_t e = set_smem((const void*)k_recycle_q<T>, sm, attr);
-  if (e != cudaSuccess) return e;
   const int nsm = ws.grid_max / 8;
-  k_recycle_q<T><<<nsm * 4, 128, sm, st>>>(ws, U, V, Unew, kh, ucur, unext);
+  const int dcap = kh + ws.m;  // W has kh + jf <= kh + m columns; kprime <= k + 1 = kmax
+  const int grid = 2 * nsm;
+  if (ws.kmax <= 24 && recycle_rb_smem(dcap, 24) <= RB_SMEM_MAX) {
+    const size_t sm = recycle_rb_smem(dcap, 24);
+    static bool attr = false;
+    cudaError_t e = set_smem((const void*)k_recycle_rb<T, 3>, RB_SMEM_MAX, attr);
+    if (e != cudaSuccess) return e;
+    k_recycle_rb<T, 3><<<grid, RB_THREADS, sm, st>>>(ws, U, V, Unew, kh, ucur, unext, dcap);
+  } else if (recycle_rb_smem(dcap, 32) <= RB_SMEM_MAX) {
+    const size_t sm = recycle_rb_smem(dcap, 32);
+    static bool attr = false;
+    cudaError_t e = set_smem((const void*)k_recycle_rb<T, 4>, RB_SMEM_MAX, attr);
+    if (e != cudaSuccess) return e;
+    k_recycle_rb<T, 4><<<grid, RB_THREADS, sm, st>>>(ws, U, V, Unew, kh, ucur, unext, dcap);
+  } else {
+    // wide W (kh + m beyond the shared-memory tile): the row-per-thread kernel
+    const size_t sm = (size_t)D_MAX * RT * sizeof(Q52);
+    static bool attr = false;
+    cudaError_t e = set_smem((const void*)k_recycle_q<T>, sm, attr);
+    if (e != cudaSuccess) return e;
+    k_recycle_q<T><<<nsm * 4, 128, sm, st>>>(ws, U, V, Unew, kh, ucur, unext);
+  }
   return cudaGetLastError();
 }
 

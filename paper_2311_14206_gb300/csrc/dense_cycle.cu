@@ -431,7 +431,7 @@ __device__ bool hqr_f32_warp(float* H, int ldh, int n, float* wr, float* wi) {
           q = HF(H, ldh, k + 1, k - 1);
           r = (k != nn - 1) ? HF(H, ldh, k + 2, k - 1) : 0.f;
           x = fabsf(p) + fabsf(q) + fabsf(r);
-          if (x != 0.f) { const float inv = 1.f / x; p *= inv; q *= inv; r *= inv; }
+          if (x != 0.f) { const float inv = __fdividef(1.f, x); p *= inv; q *= inv; r *= inv; }
         }
         const float s = copysignf(sqrtf(p * p + q * q + r * r), p);
         __syncwarp();
@@ -444,7 +444,9 @@ __device__ bool hqr_f32_warp(float* H, int ldh, int n, float* wr, float* wi) {
             }
           }
           p += s;
-          const float is = 1.f / s, ip = 1.f / p;
+          // the values only locate the eigenvalues (refined in FP64 later):
+          // approximate reciprocals are enough
+          const float is = __fdividef(1.f, s), ip = __fdividef(1.f, p);
           const float xx = p * is, yy = q * is, zz = r * is, qq = q * ip, rq = r * ip;
           __syncwarp();
           for (int jj = k + lane; jj <= nn; jj += 32) {
