@@ -41,6 +41,49 @@ __device__ inline T csr_row_dot(const CsrDev& A, const T* __restrict__ x, int64_
   return y;
 }
 
+// Two CSR rows at once (either may be absent): the column indices and values
+// of both rows are loaded in chunks of eight before the gathers and the
+// products, so a thread keeps two rows' worth of loads in flight.  Each row's
+// sum is formed in column order exactly as in csr_row_dot.
+template <typename T>
+__device__ __forceinline__ void csr_row_pair(const CsrDev& A, const T* __restrict__ x, int64_t ra, bool va_,
+                                             int64_t rb, bool vb_, T& ya, T& yb) {
+  const int32_t* __restrict__ rp = A.rowptr;
+  const int32_t* __restrict__ ci = A.col;
+  const T* __restrict__ av = csr_val<T>(A);
+  int a0 = va_ ? rp[ra] : 0, a1 = va_ ? rp[ra + 1] : 0;
+  int b0 = vb_ ? rp[rb] : 0, b1 = vb_ ? rp[rb + 1] : 0;
+  constexpr int U = 8;
+  T sa = 0, sb = 0;
+  while (a0 < a1 || b0 < b1) {
+    int ca[U], cb[U];
+    T pa[U], pb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool ua = a0 + u < a1, ub = b0 + u < b1;
+      ca[u] = ua ? ci[a0 + u] : -1;
+      pa[u] = ua ? av[a0 + u] : (T)0;
+      cb[u] = ub ? ci[b0 + u] : -1;
+      pb[u] = ub ? av[b0 + u] : (T)0;
+    }
+    T xa[U], xb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      xa[u] = ca[u] >= 0 ? x[ca[u]] : (T)0;
+      xb[u] = cb[u] >= 0 ? x[cb[u]] : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (ca[u] >= 0) sa = fma(pa[u], xa[u], sa);
+      if (cb[u] >= 0) sb = fma(pb[u], xb[u], sb);
+    }
+    a0 += U;
+    b0 += U;
+  }
+  ya = sa;
+  yb = sb;
+}
+
 // Last CTA of a grid: returns true in exactly one CTA after every CTA has
 // published its partials (threadfence + counter; the counter is re-armed).
 __device__ inline bool last_block(unsigned int* counter) {
@@ -311,7 +354,7 @@ __device__ void finish_column(const WS& ws, int j, int grid2, double* buf, unsig
 // and turns the dots into the MGS coefficients H(i, j).
 // ---------------------------------------------------------------------------
 template <typename T, int NW, bool SK>  // NW window vectors v_hat_lo .. v_hat_j; SK: sketch v_hat_j
-__global__ void __launch_bounds__(SK_THREADS) k_spmv_dots(WS ws, CsrDev A, Win<T> win, int j, int grid2) {
+__global__ void __launch_bounds__(SK_THREADS, 3) k_spmv_dots(WS ws, CsrDev A, Win<T> win, int j, int grid2) {
   Ctl* c = ws.ctl;
   if (arnoldi_stopped(c, j)) return;
   extern __shared__ unsigned char smem[];
@@ -345,19 +388,38 @@ __global__ void __launch_bounds__(SK_THREADS) k_spmv_dots(WS ws, CsrDev A, Win<T
     const int64_t r0 = (int64_t)tile * tileR;
     const int ncols = (int)(n - r0 < (int64_t)tileR ? n - r0 : (int64_t)tileR);
     if (SK) tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
-    for (int i = threadIdx.x; i < tileR; i += blockDim.x) {
-      double xv = 0.0;
-      if (i < ncols) {
-        const int64_t r = r0 + i;
-        const T y = csr_row_dot<T>(A, x, r);
-        w[r] = y;
+    // two rows per thread at a time (i and i + blockDim.x), so that each
+    // thread has both rows' loads in flight
+    for (int i = threadIdx.x; i < tileR; i += 2 * blockDim.x) {
+      const int ib = i + blockDim.x;
+      const bool va_ = i < ncols, vb_ = ib < ncols;
+      const int64_t ra = r0 + i, rb = r0 + ib;
+      T wa[NW], wb[NW];
 #pragma unroll
-        for (int a = 0; a < NW; ++a) d[a] = fma(win.v[a][r], y, d[a]);
-        const unsigned long long u = abs_bits((double)y);
-        wm = u > wm ? u : wm;
-        if (SK) xv = (double)x[r];
+      for (int a = 0; a < NW; ++a) {
+        wa[a] = va_ ? win.v[a][ra] : (T)0;
+        wb[a] = vb_ ? win.v[a][rb] : (T)0;
       }
-      if (SK) vals[i] = xv;
+      T ya = 0, yb = 0;
+      csr_row_pair<T>(A, x, ra, va_, rb, vb_, ya, yb);
+      if (va_) {
+        w[ra] = ya;
+#pragma unroll
+        for (int a = 0; a < NW; ++a) d[a] = fma(wa[a], ya, d[a]);
+        const unsigned long long u = abs_bits((double)ya);
+        wm = u > wm ? u : wm;
+      }
+      if (vb_) {
+        w[rb] = yb;
+#pragma unroll
+        for (int a = 0; a < NW; ++a) d[a] = fma(wb[a], yb, d[a]);
+        const unsigned long long u = abs_bits((double)yb);
+        wm = u > wm ? u : wm;
+      }
+      if (SK) {
+        vals[i] = va_ ? (double)x[ra] : 0.0;
+        if (ib < tileR) vals[ib] = vb_ ? (double)x[rb] : 0.0;
+      }
     }
     if (SK) tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
     __syncthreads();  // next_tile is published
@@ -432,7 +494,11 @@ static cudaError_t launch_spmv_t(const WS& ws, CsrDev A, const Win<T>& win, int 
   cudaError_t e = set_smem((const void*)k_spmv_dots<T, NW, SK>, sketch_smem_bytes(ZETA_MAX), attr);
   if (e != cudaSuccess) return e;
   const size_t sm = SK ? sketch_smem_bytes(ws.zeta) : 0;
-  k_spmv_dots<T, NW, SK><<<grid_tiles(ws, A.n), SK_THREADS, sm, st>>>(ws, A, win, j, update_grid(ws));
+  // three CTAs per SM are resident (register budget); tiles are handed out by a counter
+  int g = grid_tiles(ws, A.n);
+  const int g3 = 3 * (ws.grid_max / 8);
+  if (g > g3) g = g3;
+  k_spmv_dots<T, NW, SK><<<g, SK_THREADS, sm, st>>>(ws, A, win, j, update_grid(ws));
   return cudaGetLastError();
 }
 
