@@ -52,7 +52,11 @@ UNIT = "ms/system"
 # a per-system time.  Measured on the GPU arm (the oracle's cycle counts agree within
 # one cycle per system in the parity tests); overwritten by the GPU arm's own count
 # whenever it runs in the same process.
-STEP_EQUIV_PER_SYSTEM = 700
+STEP_EQUIV_PER_SYSTEM = 400
+# DRAM bytes (read + write) per row of one k_spmv_dots launch, from the ncu capture in
+# profiles/spmv_dots_cd3d_96.md (107.0 MB per launch at 884,736 rows); set to None when the
+# kernel changes until it is captured again.
+SPMV_DRAM_BYTES_PER_ROW = 107.0e6 / 884736
 
 
 def peaks():
@@ -271,12 +275,24 @@ def run_gpu(args, rank, world):
         agg_timed["steps"] += s_["arnoldi_steps"]
         agg_timed["checks"] += s_["true_res_evals"]
         agg_timed["cycles"] += s_["cycles"]
+    # Whole-job algorithmic HBM bytes of the timed region: per Arnoldi step the SpMV
+    # (matrix, x, window, w) and the update (w, window, v_hat); per check the tall
+    # GEMV over [U V] and the residual (matrix, b, x_trial, r); per cycle the recycle
+    # product ([U V] read, U_new written); per system the exact SAU (k SpMVs).
+    d_avg = agg_timed["steps"] / max(agg_timed["cycles"], 1) + cfg["k"]
+    job_bytes = (agg_timed["steps"] * (mat_bytes + vec * (t + 1) + vec * (t + 2))
+                 + agg_timed["checks"] * (vec * (d_avg + 2) + mat_bytes + 3 * vec)
+                 + agg_timed["cycles"] * vec * (d_avg + cfg["k"] + 1)
+                 + systems * cfg["k"] * (mat_bytes + 2 * vec))
+    cycle_gbs = job_bytes / (ms * 1e-3) / 1e9
     result = dict(ms=ms, wall=wall, clocks=ck, prof=prof, e2e_ms=e2e_ms, h2d=h2d, d2h=d2h, launches=launches,
                   roofline=dict(kernel=rf_name, bound=bound, achieved=achieved, peak=hbm,
                                 peak_kind=peak_kind, unit="GB/s", frac=achieved / hbm,
                                 bytes_per_launch=rb / max(rl, 1), launches=rl, ms_per_launch=rms / max(rl, 1),
-                                traffic=None),
-                  systems=systems, agg=agg_timed, N=N, nnz=nnz, workload=cfg["workload"])
+                                traffic=(SPMV_DRAM_BYTES_PER_ROW * N if rf_name == "spmv_dots" else None)),
+                  systems=systems, agg=agg_timed, N=N, nnz=nnz, workload=cfg["workload"],
+                  cycle_hbm=dict(achieved=cycle_gbs, unit="GB/s", frac_of_measured=cycle_gbs / hbm,
+                                 frac_of_8tbs=cycle_gbs / 8000.0, bytes_per_system=job_bytes / systems))
     return result
 
 
@@ -644,6 +660,7 @@ def main():
             clocks=res["clocks"],
             e2e=dict(value=res["e2e_ms"], unit=UNIT, h2d_bytes_per_step=res["h2d"], d2h_bytes_per_step=res["d2h"]),
             gpu_launches=res["launches"],
+            cycle_hbm=res["cycle_hbm"],
             cpu_baseline=cpu,
             per_system=dict(arnoldi_steps=agg["steps"] / res["systems"], checks=agg["checks"] / res["systems"],
                             cycles=agg["cycles"] / res["systems"], svd_path_cycles=agg["svd"]),
