@@ -428,6 +428,28 @@ def run_form_adjoint(args):
                 step_ms.append(e0.elapsed_time(e1))
                 losses.append(float(L.detach()))
                 cyc.append(pair.last_stats["forward"]["cycles"] + pair.last_stats["adjoint"]["cycles"])
+        if args.breakdown and mode == "recycled":
+            # one more step with CUDA events around every launch (not part of the timing)
+            P.sdr_profile(pair.fwd.h, True)
+            P.sdr_profile(pair.adj.h, True)
+            th = theta.clone().requires_grad_(True)
+            x = solve(vcdiff_values(n, th), b, pair)
+            torch.sum((x - x_t) ** 2).backward()
+            torch.cuda.synchronize()
+            for name, hh in (("forward", pair.fwd.h), ("adjoint", pair.adj.h)):
+                prof = P.sdr_profile_get(hh)
+                tot = sum(v[1] for v in prof.values())
+                _, logs = P.sdr_get_history(hh)
+                sw = [g_["svd_sweeps"] for g_ in logs if g_["flags"] & 1]
+                print(f"{name} solve: {pair.last_stats[name]['cycles']} cycles, "
+                      f"{pair.last_stats[name]['arnoldi_steps']} steps, truncated-SVD cycles {len(sw)}, "
+                      f"Jacobi sweeps {sum(sw) / max(len(sw), 1):.1f} mean / {max(sw) if sw else 0} max, "
+                      f"ell {[g_['ell'] for g_ in logs][:6]}", file=sys.stderr)
+                for k_, (n_, t_) in sorted(prof.items(), key=lambda kv: -kv[1][1])[:10]:
+                    print(f"  {k_:16s} launches {n_:7d}  {t_:10.2f} ms  {100 * t_ / max(tot, 1e-9):5.1f}%  "
+                          f"{1e3 * t_ / max(n_, 1):9.2f} us/launch", file=sys.stderr)
+            P.sdr_profile(pair.fwd.h, False)
+            P.sdr_profile(pair.adj.h, False)
         pair.close()
         out[mode] = dict(ms_per_opt_step=sum(step_ms) / len(step_ms), loss_first=losses[0], loss_last=losses[-1],
                          cycles_per_opt_step=sum(cyc) / len(cyc))

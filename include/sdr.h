@@ -138,7 +138,7 @@ typedef struct {
   int32_t kprime;      /* recycle columns produced */
   int32_t kh;          /* recycle columns used by the cycle */
   int32_t flags;       /* bit 0: truncated-SVD path taken; bit 1: breakdown */
-  int32_t pad;
+  int32_t svd_sweeps;  /* Jacobi sweeps of the truncated-SVD path (0 when not taken) */
   double res;          /* true residual at the cycle's last check */
   double sres;         /* sketched residual at the cycle's last step */
   double safety;       /* safety factor after the cycle */

@@ -16,6 +16,8 @@
 // QR for the eigenvalues, inverse iteration with the Hessenberg matrix for the
 // selected eigenvectors, back-transformation, and an orthonormal real basis of
 // their span (real and imaginary parts of complex pairs).
+#include <cooperative_groups.h>
+
 #include "launch.cuh"
 #include "eidot.cuh"
 
@@ -180,78 +182,232 @@ __global__ void k_ce_M(WS ws, int kh) {
 // ---------------------------------------------------------------------------
 // Truncated-SVD path: one-sided Jacobi (Hestenes) on R, then
 // M_l = S_l^{-1} U_l^T C V_l and V_l kept for P = V_l Z.
+//
+// The rotations run on a cluster of SVD_CTAS CTAs (one per SM, so the FP64
+// pipes of all of them work); a half-warp rotates one column pair, so the
+// warp-uniform scalar work of a rotation (divisions, square roots) is shared
+// by two pairs.  Column c of the working matrix and of V lives
+// in the shared memory of CTA c mod SVD_CTAS and is reached by every CTA of
+// the cluster through distributed shared memory.  In each round of the
+// round-robin ordering the d/2 disjoint column pairs are spread over all
+// warps of the cluster, and a cluster barrier separates the rounds.  A pair
+// is rotated when |a_p . a_q| > d eps ||a_p|| ||a_q|| (the one-sided Jacobi
+// threshold) and neither column has fallen below the truncation level; the
+// sweeps stop when a sweep rotates nothing.  Each sweep visits the columns in
+// order of decreasing norm (de Rijk's ordering), which cuts the number of
+// sweeps.
 // ---------------------------------------------------------------------------
+constexpr int SVD_CTAS = 8;
+constexpr int SVD_COLS = (D_MAX + SVD_CTAS - 1) / SVD_CTAS;  // columns per CTA
+
+size_t ce_svd_smem() { return (size_t)2 * SVD_COLS * LDD * sizeof(double); }
+
 __global__ void __launch_bounds__(512) k_ce_svd(WS ws, int kh) {
   Ctl* c = ws.ctl;
   if (c->jf <= 0 || !c->svd_path) return;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
   const int d = kh + c->jf;
   CeLayout L = ce_layout(ws.dscr);
-  double* A = L.As;   // working matrix (d x d)
-  double* V = L.Vh;   // right singular vectors
+  extern __shared__ __align__(16) double svd_sm[];
+  double* Aloc = svd_sm;                       // [SVD_COLS][LDD]: columns rank, rank + SVD_CTAS, ...
+  double* Vloc = svd_sm + SVD_COLS * LDD;
   __shared__ double sig[D_MAX];
   __shared__ int order[D_MAX];
-  __shared__ int rotated;
+  __shared__ unsigned long long redu[32];
+  __shared__ int sweep_flag[2];                // rank 0's copy: a rotation happened in that sweep
+  __shared__ double cnorm[D_MAX];              // rank 0's copy: squared column norms at a sweep's start
+  __shared__ int perm[D_MAX];                  // visiting order of the sweep (rank 0's copy, then local)
   const int ld = ws.dmax;
-  for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
-    const int i = idx % d, jj = idx / d;
-    A[i + (int64_t)jj * LDD] = i <= jj ? ws.Rf[i + (int64_t)jj * ld] : 0.0;
-    V[i + (int64_t)jj * LDD] = (i == jj) ? 1.0 : 0.0;
+  for (int idx = threadIdx.x; idx < SVD_COLS * d; idx += blockDim.x) {
+    const int q = idx / d, i = idx % d;
+    const int col = rank + q * SVD_CTAS;
+    if (col < d) {
+      Aloc[q * LDD + i] = i <= col ? ws.Rf[i + (int64_t)col * ld] : 0.0;
+      Vloc[q * LDD + i] = i == col ? 1.0 : 0.0;
+    }
   }
-  __syncthreads();
-  const int dd = d + (d & 1);  // even number of players; index d (if odd) is a dummy
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // largest column norm of R: sigma_1 lies within a factor sqrt(d) of it
+  double cm = 0.0;
+  for (int jj = threadIdx.x; jj < d; jj += blockDim.x) {
+    double a = 0.0;
+    for (int i = 0; i <= jj; ++i) a = fma(ws.Rf[i + (int64_t)jj * ld], ws.Rf[i + (int64_t)jj * ld], a);
+    cm = a > cm ? a : cm;
+  }
+  cm = __longlong_as_double((long long)block_max_u64((unsigned long long)__double_as_longlong(cm), redu));
   const double eps = 2.220446049250313e-16;
+  const double tol = (double)d * eps;
+  const double negl = cm * tol * tol;  // squared norm below which a column is treated as zero (truncation level)
+  if (threadIdx.x < 2) sweep_flag[threadIdx.x] = 0;
+  cluster.sync();
+  int* flag0 = cluster.map_shared_rank(&sweep_flag[0], 0);
+  auto colA = [&](int col) { return cluster.map_shared_rank(Aloc, col % SVD_CTAS) + (col / SVD_CTAS) * LDD; };
+  auto colV = [&](int col) { return cluster.map_shared_rank(Vloc, col % SVD_CTAS) + (col / SVD_CTAS) * LDD; };
+  const int dd = d + (d & 1);  // even number of players; index d (if odd) is a dummy
+  const int lane = threadIdx.x & 31;
+  const int hl = lane & 15;                            // lane within the half-warp
+  const int gw = rank * (blockDim.x >> 4) + (threadIdx.x >> 4), nw = SVD_CTAS * (blockDim.x >> 4);  // half-warps
+  const int nit = (d + 15) >> 4;                       // elements per lane (uniform)
+  int sweeps = 0;
+  double* cnorm0 = cluster.map_shared_rank(cnorm, 0);
+  int* perm0 = cluster.map_shared_rank(perm, 0);
   for (int sweep = 0; sweep < 60; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
+    const int par = sweep & 1;
+    int rotated = 0;
+    // de Rijk: order the columns by decreasing norm (ties by index)
+    for (int q = threadIdx.x >> 5; q < SVD_COLS; q += blockDim.x >> 5) {
+      const int col = rank + q * SVD_CTAS;
+      if (col < d) {
+        double a = 0.0;
+        for (int i = lane; i < d; i += 32) a = fma(Aloc[q * LDD + i], Aloc[q * LDD + i], a);
+        a = warp_sum(a);
+        if (lane == 0) cnorm0[col] = a;
+      }
+    }
+    cluster.sync();
+    if (rank == 0) {
+      for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        const double ni = cnorm[i];
+        int r = 0;
+        for (int j2 = 0; j2 < d; ++j2) {
+          const double nj = cnorm[j2];
+          r += (nj > ni || (nj == ni && j2 < i)) ? 1 : 0;
+        }
+        perm[r] = i;
+      }
+    }
+    cluster.sync();
+    if (rank != 0)
+      for (int i = threadIdx.x; i < d; i += blockDim.x) perm[i] = perm0[i];
     __syncthreads();
     for (int round = 0; round < dd - 1; ++round) {
-      for (int k = wid; k < dd / 2; k += nw) {
-        int a, b;
-        if (k == 0) {
-          a = 0;
-          b = 1 + (round % (dd - 1));
+      // both half-warps of a warp run the loop the same number of times
+      const int kbase = gw - (gw & 1);
+      for (int k0 = kbase; k0 < dd / 2; k0 += nw) {
+        const int k = k0 + (gw & 1);
+        int a = 0, b = d;
+        if (k < dd / 2) {
+          if (k == 0) {
+            a = 0;
+            b = 1 + (round % (dd - 1));
+          } else {
+            a = 1 + ((k + round) % (dd - 1));
+            b = 1 + ((dd - 1 - k + round) % (dd - 1));
+          }
+          if (a > b) { int tmp = a; a = b; b = tmp; }
+        }
+        const bool live = b < d;  // a real pair (b == d is the dummy player, or no pair)
+        if (live) {
+          a = perm[a];
+          b = perm[b];
         } else {
-          a = 1 + ((k + round) % (dd - 1));
-          b = 1 + ((dd - 1 - k + round) % (dd - 1));
+          a = 0;
+          b = 0;
         }
-        if (a > b) { int tmp = a; a = b; b = tmp; }
-        if (b >= d) continue;
-        double* ap = A + (int64_t)a * LDD;
-        double* aq = A + (int64_t)b * LDD;
+        double* ap = colA(a);
+        double* aq = colA(b);
+        double* vp = colV(a);
+        double* vq = colV(b);
+        // every load of the pair (both columns of A and of V, remote shared
+        // memory of up to four CTAs) is issued before any store, so they
+        // overlap instead of waiting for one another
+        double xa[D_MAX / 16], xb[D_MAX / 16], ya[D_MAX / 16], yb[D_MAX / 16];
+#pragma unroll
+        for (int u = 0; u < D_MAX / 16; ++u) {
+          const int i = hl + 16 * u;
+          const bool in = live && u < nit && i < d;
+          xa[u] = in ? ap[i] : 0.0;
+          xb[u] = in ? aq[i] : 0.0;
+          ya[u] = in ? vp[i] : 0.0;
+          yb[u] = in ? vq[i] : 0.0;
+        }
         double al = 0.0, be = 0.0, ga = 0.0;
-        for (int i = lane; i < d; i += 32) {
-          al = fma(ap[i], ap[i], al);
-          be = fma(aq[i], aq[i], be);
-          ga = fma(ap[i], aq[i], ga);
+#pragma unroll
+        for (int u = 0; u < D_MAX / 16; ++u) {
+          if (u < nit) {
+            al = fma(xa[u], xa[u], al);
+            be = fma(xb[u], xb[u], be);
+            ga = fma(xa[u], xb[u], ga);
+          }
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (!(fabs(ga) > eps * sqrt(al * be)) || al == 0.0 || be == 0.0) continue;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-        double* vp = V + (int64_t)a * LDD;
-        double* vq = V + (int64_t)b * LDD;
-        for (int i = lane; i < d; i += 32) {
-          const double x1 = ap[i], x2 = aq[i];
-          ap[i] = cs * x1 - sn * x2;
-          aq[i] = sn * x1 + cs * x2;
-          const double y1 = vp[i], y2 = vq[i];
-          vp[i] = cs * y1 - sn * y2;
-          vq[i] = sn * y1 + cs * y2;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {  // sums within each half-warp
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (lane == 0) rotated = 1;
+        const bool rot = live && (ga * ga > tol * tol * al * be) && al > negl && be > negl;
+        if (!__any_sync(0xffffffffu, rot)) continue;
+        // The rotation angle needs only single precision (an inexact angle
+        // still gives an exactly orthogonal rotation, and the next sweep
+        // removes what it leaves); the cosine is refined to double precision
+        // so that cs^2 + sn^2 = 1 to rounding.  FP64 division and square root
+        // are long instruction sequences on this GPU, the FP32 ones are not.
+        const double num = be - al, den = 2.0 * (rot ? ga : 1.0);
+        // scale both by a power of two so the FP32 casts stay in range
+        const int en = (int)(((unsigned long long)__double_as_longlong(num) >> 52) & 0x7FF);
+        const int ed = (int)(((unsigned long long)__double_as_longlong(den) >> 52) & 0x7FF);
+        int e = (en > ed ? en : ed) - 1023;
+        e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+        const double sc = __longlong_as_double((long long)((unsigned long long)(1023 - e) << 52));
+        const float zf = __fdividef((float)(num * sc), (float)(den * sc));
+        const float az = fabsf(zf);
+        const float tf = az > 1e18f ? copysignf(0.5f / az, zf)
+                                    : copysignf(1.0f, zf) / (az + sqrtf(fmaf(zf, zf, 1.0f)));
+        const double t = (double)tf;
+        // cs = 1 / sqrt(1 + t^2): FP32 estimate, three Newton steps y <- y (3 - x y^2) / 2
+        const double xq = fma(t, t, 1.0);
+        double cs = (double)rsqrtf((float)xq);
+#pragma unroll
+        for (int it = 0; it < 3; ++it) cs = cs * fma(-0.5 * xq, cs * cs, 1.5);
+        const double sn = cs * t;
+        if (rot) {
+#pragma unroll
+          for (int u = 0; u < D_MAX / 16; ++u) {
+            const int i = hl + 16 * u;
+            if (u < nit && i < d) {
+              ap[i] = cs * xa[u] - sn * xb[u];
+              aq[i] = sn * xa[u] + cs * xb[u];
+              vp[i] = cs * ya[u] - sn * yb[u];
+              vq[i] = sn * ya[u] + cs * yb[u];
+            }
+          }
+          rotated = 1;
+        }
       }
-      __syncthreads();
+      cluster.sync();
     }
-    if (!rotated) break;
-    __syncthreads();
+    if (rotated && hl == 0) atomicOr(flag0 + par, 1);
+    if (rank == 0 && threadIdx.x == 0) sweep_flag[1 - par] = 0;  // the next sweep's flag (nobody reads it yet)
+    cluster.sync();
+    const int any = *(volatile int*)(flag0 + par);
+    cluster.sync();  // every CTA has read the flag before rank 0 clears it in the sweep after next
+    sweeps = sweep + 1;
+    if (!any) break;
   }
+  // every CTA writes its columns back for the rest of the step, run by rank 0
+  double* A = L.As;   // working matrix (d x d)
+  double* V = L.Vh;   // right singular vectors
+  for (int idx = threadIdx.x; idx < SVD_COLS * d; idx += blockDim.x) {
+    const int q = idx / d, i = idx % d;
+    const int col = rank + q * SVD_CTAS;
+    if (col < d) {
+      A[i + (int64_t)col * LDD] = Aloc[q * LDD + i];
+      V[i + (int64_t)col * LDD] = Vloc[q * LDD + i];
+    }
+  }
+  __threadfence();
+  cluster.sync();
+  if (rank == 0 && threadIdx.x == 0) c->svd_sweeps = sweeps;
+  if (rank != 0) return;
   // singular values and ordering (descending)
-  for (int i = wid; i < d; i += nw) {
+  for (int i = threadIdx.x >> 5; i < d; i += blockDim.x >> 5) {
     double a = 0.0;
-    for (int r = lane; r < d; r += 32) a = fma(A[r + (int64_t)i * LDD], A[r + (int64_t)i * LDD], a);
+    for (int r = lane; r < d; r += 32) {
+      const double ar = __ldcg(A + r + (int64_t)i * LDD);
+      a = fma(ar, ar, a);
+    }
     a = warp_sum(a);
     if (lane == 0) sig[i] = sqrt(a);
   }
@@ -277,7 +433,7 @@ __global__ void __launch_bounds__(512) k_ce_svd(WS ws, int kh) {
     const int i = idx % d, q = idx / d;
     const double* vc = V + (int64_t)order[q] * LDD;
     double a = 0.0;
-    for (int l = 0; l < d; ++l) a = fma(L.C[i + (int64_t)l * LDD], vc[l], a);
+    for (int l = 0; l < d; ++l) a = fma(L.C[i + (int64_t)l * LDD], __ldcg(vc + l), a);
     T1[i + (int64_t)q * LDD] = a;
   }
   __syncthreads();
@@ -286,14 +442,14 @@ __global__ void __launch_bounds__(512) k_ce_svd(WS ws, int kh) {
     const double si = sig[order[i]];
     const double* uc = A + (int64_t)order[i] * LDD;
     double a = 0.0;
-    for (int l = 0; l < d; ++l) a = fma(uc[l], T1[l + (int64_t)q * LDD], a);
+    for (int l = 0; l < d; ++l) a = fma(__ldcg(uc + l), T1[l + (int64_t)q * LDD], a);
     L.M[i + (int64_t)q * LDD] = a / (si * si);  // U_l = A_l / sigma, then S^{-1}
   }
   __syncthreads();
   // keep V_l (ordered) in the columns of As for P = V_l Z
   for (int idx = threadIdx.x; idx < d * ell; idx += blockDim.x) {
     const int i = idx % d, q = idx / d;
-    T1[i + (int64_t)q * LDD] = V[i + (int64_t)order[q] * LDD];
+    T1[i + (int64_t)q * LDD] = __ldcg(V + i + (int64_t)order[q] * LDD);
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < d * ell; idx += blockDim.x) {
@@ -925,7 +1081,7 @@ __global__ void __launch_bounds__(512) k_ce_finish(WS ws, int kh, int ucur) {
       g.kprime = kp;
       g.kh = kh;
       g.flags = (c->svd_path ? 1 : 0) | (c->breakdown ? 2 : 0) | (c->rankfail ? 4 : 0);
-      g.pad = 0;
+      g.svd_sweeps = c->svd_path ? c->svd_sweeps : 0;
       g.res = c->res;
       g.sres = c->sres;
       g.safety = c->safety;
@@ -971,7 +1127,30 @@ cudaError_t launch_cycle_end_part(int part, const WS& ws, int kh, int ucur, cons
     case 0: k_ce_formC<<<dmax_now, 256, 0, st>>>(ws, SU, kh); break;
     case 1: k_ce_rinv<<<dmax_now, 32, 0, st>>>(ws, kh); break;
     case 2: k_ce_M<<<dmax_now, 256, 0, st>>>(ws, kh); break;
-    case 3: k_ce_svd<<<1, 512, 0, st>>>(ws, kh); break;
+    case 3: {
+      static bool attr_done = false;
+      if (!attr_done) {
+        const cudaError_t ea = cudaFuncSetAttribute(k_ce_svd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)ce_svd_smem());
+        if (ea != cudaSuccess) return ea;
+        attr_done = true;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(SVD_CTAS, 1, 1);
+      cfg.blockDim = dim3(512, 1, 1);
+      cfg.dynamicSmemBytes = ce_svd_smem();
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = SVD_CTAS;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, k_ce_svd, ws, kh);
+      if (e != cudaSuccess) return e;
+      break;
+    }
     case 4: k_ce_eig<<<1, 512, ce_eig_smem(), st>>>(ws); break;
     case 5: k_ce_invit<<<KC, 256, 0, st>>>(ws); break;
     case 6: k_ce_select<<<1, 256, 0, st>>>(ws); break;

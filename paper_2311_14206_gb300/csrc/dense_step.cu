@@ -312,21 +312,49 @@ __global__ void __launch_bounds__(DT) k_step_dense(WS ws, int j, int kh, int ubu
   __syncthreads();
   if (!do_check) return;
   for (int i = threadIdx.x; i < 2 * s; i += blockDim.x) accR[i] = 0ull;
-  // y_tilde = R(0:p+1, 0:p+1)^{-1} z(0:p+1) by column-oriented back substitution
-  __shared__ double yv;
-  for (int i = p; i >= 0; --i) {
-    if (threadIdx.x == 0) {
-      const double rii = ws.Rf[i + (int64_t)i * ws.dmax];
-      double y = (rii != 0.0 && isfinite(rii)) ? sm.z[i] / rii : 0.0;
-      if (!(rii != 0.0)) c->rankfail = 1;
-      ws.ytil[i] = y;
-      yv = y;
-    }
-    __syncthreads();
-    const double y = yv;
-    for (int l = threadIdx.x; l < i; l += blockDim.x) sm.z[l] = fma(-ws.Rf[l + (int64_t)i * ws.dmax], y, sm.z[l]);
-    __syncthreads();
+  // y_tilde = R(0:p+1, 0:p+1)^{-1} z(0:p+1) by column-oriented back substitution.
+  // The reciprocals of the diagonal are formed in parallel first (an FP64
+  // division is a long sequence on this GPU); then one warp runs the
+  // substitution, each lane owning rows lane + 32 q and loading the next
+  // column of R while the current one is applied.
+  double* invd = sm.u2;  // D_MAX doubles, free at this point
+  for (int i = threadIdx.x; i <= p; i += blockDim.x) {
+    const double rii = ws.Rf[i + (int64_t)i * ws.dmax];
+    const bool ok = rii != 0.0 && isfinite(rii);
+    invd[i] = ok ? 1.0 / rii : 0.0;
+    if (!ok) c->rankfail = 1;
   }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    constexpr int NQ = (D_MAX + 31) / 32;
+    const double* __restrict__ Rf = ws.Rf;
+    const int64_t ldr = ws.dmax;
+    double cur[NQ], nxt[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int l = lane + 32 * q;
+      cur[q] = l < p ? Rf[l + (int64_t)p * ldr] : 0.0;
+    }
+    for (int i = p; i >= 0; --i) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int l = lane + 32 * q;
+        nxt[q] = (i >= 1 && l < i - 1) ? Rf[l + (int64_t)(i - 1) * ldr] : 0.0;
+      }
+      __syncwarp();
+      const double y = sm.z[i] * invd[i];
+      if (lane == 0) ws.ytil[i] = y;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int l = lane + 32 * q;
+        if (l < i) sm.z[l] = fma(-cur[q], y, sm.z[l]);
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) cur[q] = nxt[q];
+    }
+  }
+  __syncthreads();
   // fixed-point coefficients for the check GEMV: y''_l = y'_l 2^(E_l) with
   // y'_l = y_l (U part) or y_l alpha_l (V part) and 2^(-E_l) the column scale
   unsigned long long mb = 0ull;

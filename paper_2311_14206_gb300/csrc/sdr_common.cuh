@@ -36,6 +36,7 @@ struct Ctl {
   int accG_top;   // window top of the general-purpose sketch accumulators
   int force_svd;  // test switch: always take the truncated-SVD path
   int ell, kprime, svd_path;
+  int svd_sweeps; // Jacobi sweeps of the last truncated-SVD path
   int hist_n;     // logged steps so far in this solve
   int log_n;      // logged cycles so far in this solve
   int matvecs, sketches;
@@ -68,7 +69,7 @@ __device__ __forceinline__ bool arnoldi_stopped(const Ctl* c, int j) { return c-
 
 // Per-cycle log entry kept on the device, mirrored by sdr_cycle_log.
 struct CycleLog {
-  int steps, checks, converged, ell, kprime, kh, flags, pad;
+  int steps, checks, converged, ell, kprime, kh, flags, svd_sweeps;
   double res, sres, safety;
 };
 

@@ -62,7 +62,7 @@ class sdr_kernel_time(ctypes.Structure):
 class sdr_cycle_log(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int32), ("checks", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("ell", ctypes.c_int32), ("kprime", ctypes.c_int32), ("kh", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("pad", ctypes.c_int32), ("res", ctypes.c_double),
+                ("flags", ctypes.c_int32), ("svd_sweeps", ctypes.c_int32), ("res", ctypes.c_double),
                 ("sres", ctypes.c_double), ("safety", ctypes.c_double)]
 
 
