@@ -349,6 +349,20 @@ def run_form_f32ir(args):
                 out.setdefault(name + "_ms", []).append(e0.elapsed_time(e1))
                 e0 = e0b
         ck = clocks.stop()
+        if args.breakdown:
+            # one more system with CUDA events around every launch (not part of the timing)
+            P.sdr_profile(solver.h, True)
+            solver.recycle(mats[0], 0)
+            x.zero_()
+            P.sdr_solve(solver.h, mats[0], bs[0], x)
+            torch.cuda.synchronize()
+            prof = P.sdr_profile_get(solver.h)
+            P.sdr_profile(solver.h, False)
+            tot = sum(v[1] for v in prof.values())
+            print(f"{name}:", file=sys.stderr)
+            for k_, (n_, t_) in sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]:
+                print(f"  {k_:16s} launches {n_:7d}  {t_:10.2f} ms  {100 * t_ / max(tot, 1e-9):5.1f}%  "
+                      f"{1e3 * t_ / max(n_, 1):9.2f} us/launch", file=sys.stderr)
         out[name] = dict(ms_per_system=sum(out[name + "_ms"]) / len(out[name + "_ms"]), clocks=ck,
                          cycles=sum(s_["cycles"] for s_ in stats_list) / len(stats_list),
                          refinements=sum(s_["refinements"] for s_ in stats_list) / len(stats_list),

@@ -302,7 +302,13 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   ws.tctr = (int*)(ws.accV + (size_t)(M_MAX + 2) * 2 * S_MAX);
   chk(halloc(h, &ws.part3, (size_t)ws.grid_max * 2 * NPART));
   chk(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
-  chk(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking));
+  {
+    // the control stream's one-CTA kernels sit on the critical path of a cycle:
+    // give them the scheduler's precedence over the streaming kernels
+    int lo_pri = 0, hi_pri = 0;
+    chk(cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri));
+    chk(cudaStreamCreateWithPriority(&h->st2, cudaStreamNonBlocking, hi_pri));
+  }
   chk(cudaEventCreateWithFlags(&h->evIn, cudaEventDisableTiming));
   chk(cudaEventCreateWithFlags(&h->evOut, cudaEventDisableTiming));
   chk(cudaEventCreateWithFlags(&h->evFork, cudaEventDisableTiming));
