@@ -747,14 +747,26 @@ size_t ce_eig_smem() { return ((size_t)(D_MAX + 1) * D_MAX + 2 * D_MAX + 64) * s
 struct cplx { double re, im; };
 __device__ inline cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 __device__ inline cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
-__device__ inline cplx cdiv(cplx a, cplx b) {  // Smith's algorithm
-  if (fabs(b.re) >= fabs(b.im)) {
-    const double r = b.im / b.re, den = b.re + b.im * r;
-    return {(a.re + a.im * r) / den, (a.im - a.re * r) / den};
-  }
-  const double r = b.re / b.im, den = b.re * r + b.im;
-  return {(a.re * r + a.im) / den, (a.im * r - a.re) / den};
+// 1 / d for a complex d: conj(d) / |d|^2 with |d|^2 scaled into range by a
+// power of two and its reciprocal from an FP32 estimate refined by two Newton
+// steps r <- r (2 - q r) (an FP64 division is a long instruction sequence on
+// this GPU; these are a few dependent FMAs).
+__device__ inline cplx crecip(cplx d) {
+  const double m = fmax(fabs(d.re), fabs(d.im));
+  if (!(m > 0.0) || !isfinite(m)) return cplx{0.0, 0.0};
+  const int e = (int)(((unsigned long long)__double_as_longlong(m) >> 52) & 0x7FF) - 1023;
+  const int ec = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+  const double sc = __longlong_as_double((long long)((unsigned long long)(1023 - ec) << 52));  // 2^-ec
+  const double ar = d.re * sc, ai = d.im * sc;          // |scaled| in [1, 2)
+  const double q = fma(ar, ar, ai * ai);                 // in [1, 8)
+  double r = (double)__frcp_rn((float)q);
+  r = r * fma(-q, r, 2.0);
+  r = r * fma(-q, r, 2.0);
+  r = r * fma(-q, r, 2.0);
+  // 1/d = conj(d_s) / q * sc
+  return cplx{ar * r * sc, -ai * r * sc};
 }
+
 
 __global__ void __launch_bounds__(256) k_ce_invit(WS ws) {
   Ctl* c = ws.ctl;
@@ -820,7 +832,7 @@ __global__ void __launch_bounds__(256) k_ce_invit(WS ws) {
         d.re = tiny;
         Ar[k + (int64_t)k * LDD] = tiny;
       }
-      const cplx inv = cdiv(cplx{1.0, 0.0}, d);
+      const cplx inv = crecip(d);
       bc[0] = inv.re;
       bc[1] = inv.im;
     }
@@ -851,7 +863,14 @@ __global__ void __launch_bounds__(256) k_ce_invit(WS ws) {
     }
     __syncthreads();
   }
-  // inverse iteration from x = (1, ..., 1)
+  // inverse iteration from x = (1, ..., 1); the reciprocals of U's diagonal
+  // are formed once, in parallel, so the back substitution only multiplies
+  __shared__ double udr[D_MAX], udi[D_MAX];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const cplx inv = crecip(cplx{Ar[k + (int64_t)k * LDD], cx ? Ai[k + (int64_t)k * LDD] : 0.0});
+    udr[k] = inv.re;
+    udi[k] = inv.im;
+  }
   for (int i = threadIdx.x; i < n; i += blockDim.x) { xr[i] = 1.0; xi[i] = 0.0; }
   __syncthreads();
   for (int it = 0; it < 3; ++it) {
@@ -877,8 +896,7 @@ __global__ void __launch_bounds__(256) k_ce_invit(WS ws) {
     }
     for (int k = n - 1; k >= 0; --k) {  // upper triangular solve
       if (threadIdx.x == 0) {
-        const cplx d{Ar[k + (int64_t)k * LDD], cx ? Ai[k + (int64_t)k * LDD] : 0.0};
-        const cplx v = cdiv(cplx{xr[k], xi[k]}, d);
+        const cplx v = cmul(cplx{xr[k], xi[k]}, cplx{udr[k], udi[k]});
         xr[k] = v.re;
         xi[k] = v.im;
       }
@@ -904,7 +922,7 @@ __global__ void __launch_bounds__(256) k_ce_invit(WS ws) {
     }
     __syncthreads();
     const cplx piv{bc[0], bc[1]};
-    const cplx inv = (piv.re == 0.0 && piv.im == 0.0) ? cplx{1.0, 0.0} : cdiv(cplx{1.0, 0.0}, piv);
+    const cplx inv = (piv.re == 0.0 && piv.im == 0.0) ? cplx{1.0, 0.0} : crecip(piv);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const cplx v = cmul(cplx{xr[i], xi[i]}, inv);
