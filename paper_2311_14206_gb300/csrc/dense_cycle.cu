@@ -184,9 +184,11 @@ __global__ void k_ce_M(WS ws, int kh) {
 // M_l = S_l^{-1} U_l^T C V_l and V_l kept for P = V_l Z.
 //
 // The rotations run on a cluster of SVD_CTAS CTAs (one per SM, so the FP64
-// pipes of all of them work); a half-warp rotates one column pair, so the
-// warp-uniform scalar work of a rotation (divisions, square roots) is shared
-// by two pairs.  Column c of the working matrix and of V lives
+// pipes of all of them work).  The pairs of a round are dealt out to the
+// CTAs, and each pair gets all the warps of its CTA that the round leaves
+// free: each warp handles a slice of the two columns, the warps' partial dot
+// products are combined in shared memory, one thread forms the rotation, and
+// the slices are rotated in parallel.  Column c of the working matrix and of V lives
 // in the shared memory of CTA c mod SVD_CTAS and is reached by every CTA of
 // the cluster through distributed shared memory.  In each round of the
 // round-robin ordering the d/2 disjoint column pairs are spread over all
@@ -219,6 +221,8 @@ __global__ void __launch_bounds__(512) k_ce_svd(WS ws, int kh) {
   __shared__ int sweep_flag[2];                // rank 0's copy: a rotation happened in that sweep
   __shared__ double cnorm[D_MAX];              // rank 0's copy: squared column norms at a sweep's start
   __shared__ int perm[D_MAX];                  // visiting order of the sweep (rank 0's copy, then local)
+  __shared__ double wpart[16 * 3];             // per-warp partial dots of a round
+  __shared__ double rotp[16 * 3];              // per-pair rotation (cs, sn, rotate?) of a round
   const int ld = ws.dmax;
   for (int idx = threadIdx.x; idx < SVD_COLS * d; idx += blockDim.x) {
     const int q = idx / d, i = idx % d;
@@ -246,9 +250,6 @@ __global__ void __launch_bounds__(512) k_ce_svd(WS ws, int kh) {
   auto colV = [&](int col) { return cluster.map_shared_rank(Vloc, col % SVD_CTAS) + (col / SVD_CTAS) * LDD; };
   const int dd = d + (d & 1);  // even number of players; index d (if odd) is a dummy
   const int lane = threadIdx.x & 31;
-  const int hl = lane & 15;                            // lane within the half-warp
-  const int gw = rank * (blockDim.x >> 4) + (threadIdx.x >> 4), nw = SVD_CTAS * (blockDim.x >> 4);  // half-warps
-  const int nit = (d + 15) >> 4;                       // elements per lane (uniform)
   int sweeps = 0;
   double* cnorm0 = cluster.map_shared_rank(cnorm, 0);
   int* perm0 = cluster.map_shared_rank(perm, 0);
@@ -282,103 +283,126 @@ __global__ void __launch_bounds__(512) k_ce_svd(WS ws, int kh) {
       for (int i = threadIdx.x; i < d; i += blockDim.x) perm[i] = perm0[i];
     __syncthreads();
     for (int round = 0; round < dd - 1; ++round) {
-      // both half-warps of a warp run the loop the same number of times
-      const int kbase = gw - (gw & 1);
-      for (int k0 = kbase; k0 < dd / 2; k0 += nw) {
-        const int k = k0 + (gw & 1);
-        int a = 0, b = d;
-        if (k < dd / 2) {
-          if (k == 0) {
-            a = 0;
-            b = 1 + (round % (dd - 1));
-          } else {
-            a = 1 + ((k + round) % (dd - 1));
-            b = 1 + ((dd - 1 - k + round) % (dd - 1));
-          }
-          if (a > b) { int tmp = a; a = b; b = tmp; }
-        }
-        const bool live = b < d;  // a real pair (b == d is the dummy player, or no pair)
-        if (live) {
-          a = perm[a];
-          b = perm[b];
-        } else {
+      // pairs k = rank, rank + SVD_CTAS, ... of this round belong to this CTA;
+      // each gets wpp warps, warp `part` of a pair takes elements
+      // part*32 + lane + 32*wpp*it
+      const int npc = (dd / 2 - rank + SVD_CTAS - 1) / SVD_CTAS;  // pairs of this CTA (>= 0)
+      const int nwarp = blockDim.x >> 5;
+      const int wpp = npc > 0 ? (nwarp / npc > 0 ? nwarp / npc : 1) : 1;
+      const int w = threadIdx.x >> 5;
+      const int q = w / wpp, part = w % wpp;
+      int a = 0, b = d;
+      const int k = rank + q * SVD_CTAS;
+      if (q < npc && k < dd / 2) {
+        if (k == 0) {
           a = 0;
-          b = 0;
+          b = 1 + (round % (dd - 1));
+        } else {
+          a = 1 + ((k + round) % (dd - 1));
+          b = 1 + ((dd - 1 - k + round) % (dd - 1));
         }
-        double* ap = colA(a);
-        double* aq = colA(b);
-        double* vp = colV(a);
-        double* vq = colV(b);
-        // every load of the pair (both columns of A and of V, remote shared
-        // memory of up to four CTAs) is issued before any store, so they
-        // overlap instead of waiting for one another
-        double xa[D_MAX / 16], xb[D_MAX / 16], ya[D_MAX / 16], yb[D_MAX / 16];
+        if (a > b) { int tmp = a; a = b; b = tmp; }
+      }
+      const bool live = b < d && q < npc;
+      if (live) {
+        a = perm[a];
+        b = perm[b];
+      } else {
+        a = 0;
+        b = 0;
+      }
+      double* ap = colA(a);
+      double* aq = colA(b);
+      double* vp = colV(a);
+      double* vq = colV(b);
+      constexpr int NE = (D_MAX + 31) / 32;  // elements per lane when one warp holds a pair
+      double xa[NE], xb[NE], ya[NE], yb[NE];
 #pragma unroll
-        for (int u = 0; u < D_MAX / 16; ++u) {
-          const int i = hl + 16 * u;
-          const bool in = live && u < nit && i < d;
-          xa[u] = in ? ap[i] : 0.0;
-          xb[u] = in ? aq[i] : 0.0;
-          ya[u] = in ? vp[i] : 0.0;
-          yb[u] = in ? vq[i] : 0.0;
+      for (int u = 0; u < NE; ++u) {
+        const int i = part * 32 + lane + 32 * wpp * u;
+        const bool in = live && i < d;
+        xa[u] = in ? ap[i] : 0.0;
+        xb[u] = in ? aq[i] : 0.0;
+        ya[u] = in ? vp[i] : 0.0;
+        yb[u] = in ? vq[i] : 0.0;
+      }
+      double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        if (part * 32 + 32 * wpp * u < d) {  // warp-uniform
+          al = fma(xa[u], xa[u], al);
+          be = fma(xb[u], xb[u], be);
+          ga = fma(xa[u], xb[u], ga);
         }
-        double al = 0.0, be = 0.0, ga = 0.0;
+      }
 #pragma unroll
-        for (int u = 0; u < D_MAX / 16; ++u) {
-          if (u < nit) {
-            al = fma(xa[u], xa[u], al);
-            be = fma(xb[u], xb[u], be);
-            ga = fma(xa[u], xb[u], ga);
-          }
+      for (int o = 16; o > 0; o >>= 1) {  // three sums interleaved (FP64 adds have a long latency here)
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+      }
+      if (lane == 0) {
+        wpart[w * 3 + 0] = al;
+        wpart[w * 3 + 1] = be;
+        wpart[w * 3 + 2] = ga;
+      }
+      __syncthreads();
+      // the pair's first warp combines the parts and forms the rotation
+      if (live && part == 0 && lane == 0) {
+        double sa = 0.0, sb = 0.0, sg = 0.0;
+        for (int t2 = 0; t2 < wpp; ++t2) {
+          sa += wpart[(w + t2) * 3 + 0];
+          sb += wpart[(w + t2) * 3 + 1];
+          sg += wpart[(w + t2) * 3 + 2];
         }
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {  // sums within each half-warp
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        }
-        const bool rot = live && (ga * ga > tol * tol * al * be) && al > negl && be > negl;
-        if (!__any_sync(0xffffffffu, rot)) continue;
-        // The rotation angle needs only single precision (an inexact angle
-        // still gives an exactly orthogonal rotation, and the next sweep
-        // removes what it leaves); the cosine is refined to double precision
-        // so that cs^2 + sn^2 = 1 to rounding.  FP64 division and square root
-        // are long instruction sequences on this GPU, the FP32 ones are not.
-        const double num = be - al, den = 2.0 * (rot ? ga : 1.0);
-        // scale both by a power of two so the FP32 casts stay in range
-        const int en = (int)(((unsigned long long)__double_as_longlong(num) >> 52) & 0x7FF);
-        const int ed = (int)(((unsigned long long)__double_as_longlong(den) >> 52) & 0x7FF);
-        int e = (en > ed ? en : ed) - 1023;
-        e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
-        const double sc = __longlong_as_double((long long)((unsigned long long)(1023 - e) << 52));
-        const float zf = __fdividef((float)(num * sc), (float)(den * sc));
-        const float az = fabsf(zf);
-        const float tf = az > 1e18f ? copysignf(0.5f / az, zf)
-                                    : copysignf(1.0f, zf) / (az + sqrtf(fmaf(zf, zf, 1.0f)));
-        const double t = (double)tf;
-        // cs = 1 / sqrt(1 + t^2): FP32 estimate, three Newton steps y <- y (3 - x y^2) / 2
-        const double xq = fma(t, t, 1.0);
-        double cs = (double)rsqrtf((float)xq);
-#pragma unroll
-        for (int it = 0; it < 3; ++it) cs = cs * fma(-0.5 * xq, cs * cs, 1.5);
-        const double sn = cs * t;
+        const bool rot = (sg * sg > tol * tol * sa * sb) && sa > negl && sb > negl;
+        double cs = 1.0, sn = 0.0;
         if (rot) {
+          // The rotation angle needs only single precision (an inexact angle
+          // still gives an exactly orthogonal rotation, and the next sweep
+          // removes what it leaves); the cosine is refined to double
+          // precision so that cs^2 + sn^2 = 1 to rounding.  FP64 division and
+          // square root are long instruction sequences on this GPU.
+          const double num = sb - sa, den = 2.0 * sg;
+          const int en = (int)(((unsigned long long)__double_as_longlong(num) >> 52) & 0x7FF);
+          const int ed = (int)(((unsigned long long)__double_as_longlong(den) >> 52) & 0x7FF);
+          int e = (en > ed ? en : ed) - 1023;
+          e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+          const double sc = __longlong_as_double((long long)((unsigned long long)(1023 - e) << 52));
+          const float zf = __fdividef((float)(num * sc), (float)(den * sc));
+          const float az = fabsf(zf);
+          const float tf = az > 1e18f ? copysignf(0.5f / az, zf)
+                                      : copysignf(1.0f, zf) / (az + sqrtf(fmaf(zf, zf, 1.0f)));
+          const double t = (double)tf;
+          // cs = 1 / sqrt(1 + t^2): FP32 estimate, three Newton steps y <- y (3 - x y^2) / 2
+          const double xq = fma(t, t, 1.0);
+          cs = (double)rsqrtf((float)xq);
 #pragma unroll
-          for (int u = 0; u < D_MAX / 16; ++u) {
-            const int i = hl + 16 * u;
-            if (u < nit && i < d) {
-              ap[i] = cs * xa[u] - sn * xb[u];
-              aq[i] = sn * xa[u] + cs * xb[u];
-              vp[i] = cs * ya[u] - sn * yb[u];
-              vq[i] = sn * ya[u] + cs * yb[u];
-            }
-          }
-          rotated = 1;
+          for (int it = 0; it < 3; ++it) cs = cs * fma(-0.5 * xq, cs * cs, 1.5);
+          sn = cs * t;
         }
+        rotp[q * 3 + 0] = cs;
+        rotp[q * 3 + 1] = sn;
+        rotp[q * 3 + 2] = rot ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      if (live && rotp[q * 3 + 2] != 0.0) {
+        const double cs = rotp[q * 3 + 0], sn = rotp[q * 3 + 1];
+#pragma unroll
+        for (int u = 0; u < NE; ++u) {
+          const int i = part * 32 + lane + 32 * wpp * u;
+          if (i < d) {
+            ap[i] = cs * xa[u] - sn * xb[u];
+            aq[i] = sn * xa[u] + cs * xb[u];
+            vp[i] = cs * ya[u] - sn * yb[u];
+            vq[i] = sn * ya[u] + cs * yb[u];
+          }
+        }
+        rotated = 1;
       }
       cluster.sync();
     }
-    if (rotated && hl == 0) atomicOr(flag0 + par, 1);
+    if (rotated && lane == 0) atomicOr(flag0 + par, 1);
     if (rank == 0 && threadIdx.x == 0) sweep_flag[1 - par] = 0;  // the next sweep's flag (nobody reads it yet)
     cluster.sync();
     const int any = *(volatile int*)(flag0 + par);
