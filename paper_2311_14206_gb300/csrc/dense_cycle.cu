@@ -514,6 +514,56 @@ __device__ inline float block_sum_f(float v, float* red) {
 
 __device__ inline float& HF(float* H, int ldh, int i, int j) { return H[i + j * ldh]; }
 
+// Row and column parts of one 3x3 (or 2x2) reflector of the bulge chase, with
+// every load of a lane (at most NS entries per row or column) issued first.
+template <int NS>
+__device__ __forceinline__ void row_update(float* H, int ldh, int k, int nn, int lane, bool three, float qq,
+                                           float rq, float xx, float yy, float zz) {
+  float a0[NS], a1[NS], a2[NS];
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int jj = k + lane + 32 * t;
+    const bool in = jj <= nn;
+    a0[t] = in ? HF(H, ldh, k, jj) : 0.f;
+    a1[t] = in ? HF(H, ldh, k + 1, jj) : 0.f;
+    a2[t] = (in && three) ? HF(H, ldh, k + 2, jj) : 0.f;
+  }
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int jj = k + lane + 32 * t;
+    if (jj <= nn) {
+      const float pp = a0[t] + qq * a1[t] + rq * a2[t];
+      if (three) HF(H, ldh, k + 2, jj) = a2[t] - pp * zz;
+      HF(H, ldh, k + 1, jj) = a1[t] - pp * yy;
+      HF(H, ldh, k, jj) = a0[t] - pp * xx;
+    }
+  }
+}
+
+template <int NS>
+__device__ __forceinline__ void col_update(float* H, int ldh, int k, int l, int imax, int lane, bool three,
+                                           float qq, float rq, float xx, float yy, float zz) {
+  float b0[NS], b1[NS], b2[NS];
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int i = l + lane + 32 * t;
+    const bool in = i <= imax;
+    b0[t] = in ? HF(H, ldh, i, k) : 0.f;
+    b1[t] = in ? HF(H, ldh, i, k + 1) : 0.f;
+    b2[t] = (in && three) ? HF(H, ldh, i, k + 2) : 0.f;
+  }
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int i = l + lane + 32 * t;
+    if (i <= imax) {
+      const float pp = xx * b0[t] + yy * b1[t] + zz * b2[t];
+      if (three) HF(H, ldh, i, k + 2) = b2[t] - pp * rq;
+      HF(H, ldh, i, k + 1) = b1[t] - pp * qq;
+      HF(H, ldh, i, k) = b0[t] - pp;
+    }
+  }
+}
+
 // Francis double-shift QR on the upper-Hessenberg H (n x n, ld ldh), one warp;
 // eigenvalues into wr, wi.  Returns false when the iteration limit is reached.
 __device__ bool hqr_f32_warp(float* H, int ldh, int n, float* wr, float* wi) {
@@ -629,25 +679,22 @@ __device__ bool hqr_f32_warp(float* H, int ldh, int n, float* wr, float* wi) {
           const float is = __fdividef(1.f, s), ip = __fdividef(1.f, p);
           const float xx = p * is, yy = q * is, zz = r * is, qq = q * ip, rq = r * ip;
           __syncwarp();
-          for (int jj = k + lane; jj <= nn; jj += 32) {
-            float pp = HF(H, ldh, k, jj) + qq * HF(H, ldh, k + 1, jj);
-            if (k != nn - 1) {
-              pp += rq * HF(H, ldh, k + 2, jj);
-              HF(H, ldh, k + 2, jj) -= pp * zz;
-            }
-            HF(H, ldh, k + 1, jj) -= pp * yy;
-            HF(H, ldh, k, jj) -= pp * xx;
+          // The reflector touches rows k..k+2 of columns k..nn, then columns
+          // k..k+2 of rows l..min(nn, k+3).  A lane's columns (rows) are
+          // disjoint, so all its loads are issued before any store: in
+          // chunks of two per lane while the range is short, else four.
+          const bool three = k != nn - 1;
+          if (nn - k < 64) {
+            row_update<2>(H, ldh, k, nn, lane, three, qq, rq, xx, yy, zz);
+          } else {
+            row_update<5>(H, ldh, k, nn, lane, three, qq, rq, xx, yy, zz);
           }
           __syncwarp();
           const int imax = nn < k + 3 ? nn : k + 3;
-          for (int i = l + lane; i <= imax; i += 32) {
-            float pp = xx * HF(H, ldh, i, k) + yy * HF(H, ldh, i, k + 1);
-            if (k != nn - 1) {
-              pp += zz * HF(H, ldh, i, k + 2);
-              HF(H, ldh, i, k + 2) -= pp * rq;
-            }
-            HF(H, ldh, i, k + 1) -= pp * qq;
-            HF(H, ldh, i, k) -= pp;
+          if (imax - l < 64) {
+            col_update<2>(H, ldh, k, l, imax, lane, three, qq, rq, xx, yy, zz);
+          } else {
+            col_update<5>(H, ldh, k, l, imax, lane, three, qq, rq, xx, yy, zz);
           }
           __syncwarp();
         }
