@@ -42,7 +42,7 @@ __device__ inline T csr_row_dot(const CsrDev& A, const T* __restrict__ x, int64_
 }
 
 // Two CSR rows at once (either may be absent): the column indices and values
-// of both rows are loaded in chunks of eight before the gathers and the
+// of both rows are loaded in chunks of seven before the gathers and the
 // products, so a thread keeps two rows' worth of loads in flight.  Each row's
 // sum is formed in column order exactly as in csr_row_dot.
 template <typename T>
@@ -53,7 +53,9 @@ __device__ __forceinline__ void csr_row_pair(const CsrDev& A, const T* __restric
   const T* __restrict__ av = csr_val<T>(A);
   int a0 = va_ ? rp[ra] : 0, a1 = va_ ? rp[ra + 1] : 0;
   int b0 = vb_ ? rp[rb] : 0, b1 = vb_ ? rp[rb + 1] : 0;
-  constexpr int U = 8;
+  // a chunk of seven covers a 7-point stencil row in one pass (a masked FP64
+  // instruction costs as much as a full one on this GPU)
+  constexpr int U = 7;
   T sa = 0, sb = 0;
   while (a0 < a1 || b0 < b1) {
     int ca[U], cb[U];
@@ -833,10 +835,16 @@ __global__ void __launch_bounds__(RB_THREADS, 2) k_recycle_rb(WS ws, const T* __
   }
   extern __shared__ __align__(16) unsigned char smraw[];
   YK* ytab = (YK*)smraw;                                      // [dcap][NCOL]
-  Q52* xq = (Q52*)(smraw + (size_t)dcap * NCOL * sizeof(YK));  // [dcap][RB_ROWS]
+  // [dcap][RB_ROWS]: row r of column l at l*RB_ROWS + 2*(r % 32) + r / 32, so a
+  // lane's two rows (r and r + 32) are one 16-byte load
+  Q52* xq = (Q52*)(smraw + (size_t)dcap * NCOL * sizeof(YK));
   __shared__ int dl[D_MAX];
   __shared__ int fx[NCOL];
-  for (int l = threadIdx.x; l < d; l += blockDim.x) dl[l] = col_delta(c, ucur, kh, l);
+  __shared__ const T* colp[D_MAX];
+  for (int l = threadIdx.x; l < d; l += blockDim.x) {
+    dl[l] = col_delta(c, ucur, kh, l);
+    colp[l] = wcol(U, V, ws.ldv, kh, l);
+  }
   for (int q = threadIdx.x; q < NCOL; q += blockDim.x) fx[q] = q < kp ? ws.Pexp[q] : 0;
   for (int idx = threadIdx.x; idx < d * NCOL; idx += blockDim.x) {
     const int l = idx / NCOL, q = idx % NCOL;
@@ -867,12 +875,13 @@ __global__ void __launch_bounds__(RB_THREADS, 2) k_recycle_rb(WS ws, const T* __
       for (int u = 0; u < 8; ++u) {
         const int idx = base + u * RB_THREADS;
         const int l = idx / RB_ROWS, r = idx % RB_ROWS;
-        wv[u] = (idx < d * RB_ROWS && r < nr) ? (double)wcol(U, V, ld, kh, l)[r0 + r] : 0.0;
+        wv[u] = (idx < d * RB_ROWS && r < nr) ? (double)colp[l][r0 + r] : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int idx = base + u * RB_THREADS;
-        if (idx < d * RB_ROWS) xq[idx] = q52(wv[u], 1022, dl[idx / RB_ROWS]);
+        const int l = idx / RB_ROWS, r = idx % RB_ROWS;
+        if (idx < d * RB_ROWS) xq[l * RB_ROWS + 2 * (r & 31) + (r >> 5)] = q52(wv[u], 1022, dl[l]);
       }
     }
     __syncthreads();
@@ -884,16 +893,19 @@ __global__ void __launch_bounds__(RB_THREADS, 2) k_recycle_rb(WS ws, const T* __
 #pragma unroll
         for (int q = 0; q < CPT; ++q) hh[i][q] = mm[i][q] = 0, ll[i][q] = 0ull;
       const YK* yrow = ytab + w * CPT;
-      const Q52* xrow = xq + lane;
+      const int4* xrow = (const int4*)(xq + 2 * lane);
+      static_assert(RB_RPL == 2, "two rows per lane: one 16-byte load");
 #pragma unroll 2
       for (int l = 0; l < d; ++l) {
+        const int4 xx = xrow[l * (RB_ROWS / 2)];
         Q52 x[RB_RPL];
+        x[0].hi = xx.x;
+        x[0].lo = (unsigned)xx.y;
+        x[1].hi = xx.z;
+        x[1].lo = (unsigned)xx.w;
         int xs[RB_RPL];
 #pragma unroll
-        for (int i = 0; i < RB_RPL; ++i) {
-          x[i] = xrow[l * RB_ROWS + 32 * i];
-          xs[i] = x[i].hi + (int)x[i].lo;
-        }
+        for (int i = 0; i < RB_RPL; ++i) xs[i] = x[i].hi + (int)x[i].lo;
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
           const YK y = yrow[l * NCOL + q];

@@ -1092,21 +1092,31 @@ __global__ void __launch_bounds__(512) k_ce_finish(WS ws, int kh, int ucur) {
   const int kp = c->kprime;
   CeLayout L = ce_layout(ws.dscr);
   __shared__ double red[32];
+  __shared__ double dts[K_MAX];
   double* Z = L.Zr;
   for (int col = 0; col < kp; ++col) {
     double* zc = Z + (int64_t)col * LDD;
     double n0 = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) n0 = fma(zc[i], zc[i], n0);
     n0 = sqrt(block_sum(n0, red));
+    // classical Gram-Schmidt, twice (as stable as modified Gram-Schmidt twice);
+    // all projections of a pass at once, one warp per earlier column
     for (int pass = 0; pass < 2; ++pass) {
-      for (int q = 0; q < col; ++q) {
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int q = wid; q < col; q += nw) {
         const double* zq = Z + (int64_t)q * LDD;
         double dt = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) dt = fma(zq[i], zc[i], dt);
-        dt = block_sum(dt, red);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) zc[i] = fma(-dt, zq[i], zc[i]);
-        __syncthreads();
+        for (int i = lane; i < n; i += 32) dt = fma(zq[i], zc[i], dt);
+        dt = warp_sum(dt);
+        if (lane == 0) dts[q] = dt;
       }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double v = zc[i];
+        for (int q = 0; q < col; ++q) v = fma(-dts[q], Z[i + (int64_t)q * LDD], v);
+        zc[i] = v;
+      }
+      __syncthreads();
     }
     double nr = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) nr = fma(zc[i], zc[i], nr);
