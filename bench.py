@@ -204,11 +204,19 @@ def run_gpu(args, rank, world):
         s_["recycle_dim"] for s_ in stats_list[:-1]) + 4 * stats_list[0]["recycle_dim"]
     # ---- per-kernel-class times: a separate pass with CUDA events around every launch ----
     P.sdr_profile(solver.h, True)
+    if args.trace:
+        P.sdr_trace(solver.h, 1 << 20)
     prof_stats = []
     for _ in range(min(args.steps, 3)):
         step(prof_stats)
     torch.cuda.synchronize()
     prof = P.sdr_profile_get(solver.h)
+    if args.trace:
+        with open(args.trace, "w") as f:
+            f.write("class,stream,start_us,end_us\n")
+            for c_, s_, t0_, t1_ in P.sdr_trace_get(solver.h):
+                f.write(f"{c_},{s_},{t0_:.2f},{t1_:.2f}\n")
+        P.sdr_trace(solver.h, 0)
     P.sdr_profile(solver.h, False)
     # ---- e2e: the same steps through the C ABI from pinned host buffers ----
     host_vals = [v.cpu().pin_memory() for v in vals]
@@ -645,6 +653,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--breakdown", action="store_true", help="print the per-kernel-class times to stderr")
+    ap.add_argument("--trace", default="", help="write every launch of the per-kernel pass (class, stream, "
+                    "start and end in us) to this CSV file")
     ap.add_argument("--n", type=int, default=0, help="grid side of a smaller case of the default workload "
                     "(for profiler captures; the bench line names it)")
     ap.add_argument("--systems", type=int, default=0, help="systems of the sequence kept on the device")

@@ -314,6 +314,27 @@ sdr_status sdr_profile(sdr_handle* h, int32_t enable);
  * receives SDR_K_COUNT. */
 sdr_status sdr_profile_get(sdr_handle* h, sdr_kernel_time* out, int32_t cap, int32_t* n);
 
+/* One launch of a traced call.  start_us and end_us are the CUDA events
+ * recorded just before and just after the launch on its stream, in
+ * microseconds after the first launch traced since sdr_trace; the span thus
+ * includes the time the launch waited for its stream and for free SMs. */
+typedef struct {
+  int32_t cls;      /* sdr_kernel_class */
+  int32_t stream;   /* 0: the handle's main stream, 1: its control stream */
+  double start_us;
+  double end_us;
+} sdr_trace_entry;
+
+/* cap > 0: while profiling is enabled (sdr_profile), keep a trace entry for
+ * each of the next cap launches (clears the earlier trace and takes a new
+ * time origin); cap = 0: stop tracing.  Entries are taken when a call
+ * collects its event pairs, i.e. before the call returns. */
+sdr_status sdr_trace(sdr_handle* h, int32_t cap);
+
+/* Copy min(cap, *n) trace entries into out (host pointer); *n receives the
+ * number kept. */
+sdr_status sdr_trace_get(sdr_handle* h, sdr_trace_entry* out, int32_t cap, int32_t* n);
+
 /* Human-readable text of a status (static storage). */
 const char* sdr_status_string(sdr_status st);
 

@@ -18,6 +18,8 @@ from .sdr import (  # noqa: F401
     sdr_get_history,
     sdr_profile,
     sdr_profile_get,
+    sdr_trace,
+    sdr_trace_get,
     sdr_recycle,
     sdr_recycle_dim,
     sdr_recycle_export,

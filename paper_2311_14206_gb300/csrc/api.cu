@@ -26,9 +26,15 @@ struct Prof {
   bool on = false;
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
-  std::vector<int> cls;  // class of event pair i (events 2i, 2i+1)
+  std::vector<int> cls;   // class of event pair i (events 2i, 2i+1)
+  std::vector<int> strm;  // stream of event pair i: 0 main, 1 control, 2 other
   double total_ms[SDR_K_COUNT] = {};
   int launches[SDR_K_COUNT] = {};
+  // trace: every launch's start and end against one reference event
+  int trace_cap = 0;
+  cudaEvent_t ref = nullptr;
+  bool ref_set = false;
+  std::vector<sdr_trace_entry> trace;
 };
 
 struct sdr_handle {
@@ -136,6 +142,12 @@ cudaError_t prof_begin(sdr_handle* h, int cls, cudaStream_t st) {
     P.pool.push_back(e);
   }
   P.cls.push_back(cls);
+  P.strm.push_back(st == h->st ? 0 : (st == h->st2 ? 1 : 2));
+  if (P.trace_cap > 0 && !P.ref_set) {
+    cudaError_t r = cudaEventRecord(P.ref, st);
+    if (r != cudaSuccess) return r;
+    P.ref_set = true;
+  }
   return cudaEventRecord(P.pool[2 * (P.cls.size() - 1)], st);
 }
 
@@ -154,8 +166,21 @@ cudaError_t prof_collect(sdr_handle* h) {
     if (r != cudaSuccess) return r;
     P.total_ms[P.cls[i]] += ms;
     P.launches[P.cls[i]] += 1;
+    if (P.trace_cap > 0 && (int)P.trace.size() < P.trace_cap) {
+      float t0 = 0.f, t1 = 0.f;
+      r = cudaEventElapsedTime(&t0, P.ref, P.pool[2 * i]);
+      if (r == cudaSuccess) r = cudaEventElapsedTime(&t1, P.ref, P.pool[2 * i + 1]);
+      if (r != cudaSuccess) return r;
+      sdr_trace_entry te;
+      te.cls = P.cls[i];
+      te.stream = P.strm[i];
+      te.start_us = 1e3 * (double)t0;
+      te.end_us = 1e3 * (double)t1;
+      P.trace.push_back(te);
+    }
   }
   P.cls.clear();
+  P.strm.clear();
   return cudaSuccess;
 }
 
@@ -209,6 +234,7 @@ sdr_status sdr_destroy(sdr_handle* h) {
   if (!h) return SDR_OK;
   if (h->st2) cudaStreamSynchronize(h->st2);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+  if (h->prof.ref) cudaEventDestroy(h->prof.ref);
   for (cudaEvent_t e : h->evS) cudaEventDestroy(e);
   for (cudaEvent_t e : h->evD) cudaEventDestroy(e);
   if (h->evFork) cudaEventDestroy(h->evFork);
@@ -300,6 +326,7 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   chk(halloc(h, &ws.acc, (size_t)6 * S_MAX + 16));
   chk(halloc(h, &ws.accV, CYCLE_SCRATCH_WORDS));
   ws.tctr = (int*)(ws.accV + (size_t)(M_MAX + 2) * 2 * S_MAX);
+  ws.dacc = ws.accV + (size_t)(M_MAX + 2) * 2 * S_MAX + (M_MAX + 2);
   chk(halloc(h, &ws.part3, (size_t)ws.grid_max * 2 * NPART));
   chk(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
   {
@@ -944,6 +971,7 @@ sdr_status sdr_profile(sdr_handle* h, int32_t enable) {
   Prof& P = h->prof;
   P.on = enable != 0;
   P.cls.clear();
+  P.strm.clear();
   for (int i = 0; i < SDR_K_COUNT; ++i) {
     P.total_ms[i] = 0.0;
     P.launches[i] = 0;
@@ -959,6 +987,24 @@ sdr_status sdr_profile_get(sdr_handle* h, sdr_kernel_time* out, int32_t cap, int
     out[i].pad = 0;
     out[i].total_ms = h->prof.total_ms[i];
   }
+  return SDR_OK;
+}
+
+sdr_status sdr_trace(sdr_handle* h, int32_t cap) {
+  if (!h || cap < 0) return SDR_ERR_INVALID_ARG;
+  Prof& P = h->prof;
+  if (cap > 0 && !P.ref && cudaEventCreate(&P.ref) != cudaSuccess) return SDR_ERR_CUDA;
+  P.trace_cap = cap;
+  P.ref_set = false;
+  P.trace.clear();
+  return SDR_OK;
+}
+
+sdr_status sdr_trace_get(sdr_handle* h, sdr_trace_entry* out, int32_t cap, int32_t* n) {
+  if (!h || cap < 0 || (cap > 0 && !out)) return SDR_ERR_INVALID_ARG;
+  const int32_t nt = (int32_t)h->prof.trace.size();
+  if (n) *n = nt;
+  if (cap > 0) std::memcpy(out, h->prof.trace.data(), sizeof(sdr_trace_entry) * (size_t)(nt < cap ? nt : cap));
   return SDR_OK;
 }
 

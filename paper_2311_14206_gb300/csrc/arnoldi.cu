@@ -348,6 +348,82 @@ __device__ void finish_column(const WS& ws, int j, int grid2, double* buf, unsig
   __syncthreads();
 }
 
+// (lo, hi) += round(d / 2^u) in 128-bit two's complement, integer operations
+// only; zero and subnormal d add nothing (far below any unit used here), a
+// non-finite d or one beyond the 128-bit range sets bad.
+__device__ __forceinline__ void add_fixed128(unsigned long long& lo, unsigned long long& hi, double d, int u,
+                                             bool& bad) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return;
+  if (ex == 0x7FF) {
+    bad = true;
+    return;
+  }
+  const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  const int sh = (ex - 1075) - u;
+  if (sh > 72) {
+    bad = true;
+    return;
+  }
+  add_shifted128(lo, hi, (b >> 63) ? -m : m, sh);
+}
+
+// End of k_spmv_dots: in the last CTA, the column finish and, from the exact
+// fixed-point dot sums, the MGS coefficients H(i, j) (Algorithm 1, inner
+// loop).  buf: blockDim.x doubles.
+template <typename T, int NW, bool SK>
+__device__ __forceinline__ void spmv_dots_finish(const WS& ws, const Win<T>& win, int j, int grid2, const int* du,
+                                                 double* buf, unsigned long long* redu) {
+  Ctl* c = ws.ctl;
+  if (last_block(&c->counter)) {
+    if (j >= 1) finish_column(ws, j, grid2, buf, redu);
+    unsigned long long wmv = 0ull;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+      const unsigned long long u =
+          (unsigned long long)__double_as_longlong(__ldcg(ws.part + (int64_t)b * NPART + T_MAX));
+      wmv = u > wmv ? u : wmv;
+    }
+    const unsigned long long wmx = block_max_u64(wmv, redu);
+    const bool finite = bexp_of_bits(wmx) != 0x7FF;
+    double p[NW];
+#pragma unroll
+    for (int a = 0; a < NW; ++a) {
+      const unsigned long long* acc = ws.dacc + ((int64_t)j * T_MAX + a) * 2;
+      p[a] = finite ? i128_to_double(__ldcg(acc), __ldcg(acc + 1), du[a]) : __longlong_as_double(0x7FF8000000000000ll);
+    }
+    if (threadIdx.x == 0) {
+      // Truncated MGS (Algorithm 1, inner loop) from the dots: with
+      // v_i = alpha_i v_hat_i and w_true = alpha_j w,
+      // H(i,j) = v_i . (w_true - sum_{l<i} H(l,j) v_l).
+      const int t = ws.t;
+      const double aj = c->alpha[j];
+      double h[NW];
+      double bound = fabs(aj) * __longlong_as_double((long long)wmx);
+      c->coef[0] = aj;
+#pragma unroll
+      for (int a = 0; a < NW; ++a) {
+        const int i = win.lo + a;
+        const double ai = c->alpha[i];
+        double v = ai * aj * p[a];
+#pragma unroll
+        for (int b2 = 0; b2 < a; ++b2) {
+          const int l = win.lo + b2;
+          v -= h[b2] * ai * c->alpha[l] * c->gram[i][i - l - 1];
+        }
+        h[a] = v;
+        c->hband[j][i - j + t - 1] = v;
+        c->coef[1 + a] = v * ai;
+        bound += fabs(c->coef[1 + a]) * __longlong_as_double((long long)c->vmax[i]);
+      }
+      c->wmax = wmx;
+      c->vtop[j + 1] = window_top(bound * (1.0 + 1e-12), ws.win_bits);
+      atomicAdd(&c->matvecs, 1);
+      if (SK) atomicAdd(&c->sketches, 1);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Arnoldi step j, part 1: w = A v_hat_j (one thread per row) with the dots of
 // w against the truncation window, and, for j >= 1, the sketch S v_hat_j of
@@ -366,6 +442,8 @@ __global__ void __launch_bounds__(SK_THREADS, 3) k_spmv_dots(WS ws, CsrDev A, Wi
   uint16_t* ptr_s = ent_s + tileR * ws.zeta;
   __shared__ double buf[SK_THREADS];
   __shared__ unsigned long long redu[32];
+  // per-thread window-dot accumulators, fixed point (see add_fixed128)
+  __shared__ unsigned long long dlo[NW][SK_THREADS], dhi[NW][SK_THREADS];
   const T* __restrict__ x = win.v[NW - 1];
   T* __restrict__ w = (T*)ws.Wv;
   const int top = SK ? c->vtop[j] : 0;
@@ -378,6 +456,26 @@ __global__ void __launch_bounds__(SK_THREADS, 3) k_spmv_dots(WS ws, CsrDev A, Wi
   for (int k = 0; k < SK_RPT; ++k) lo[k] = hi[k] = 0ull;
   const int64_t n = A.n;
   const int ntiles = (int)((n + tileR - 1) / tileR);
+  // Fixed-point units of the window dots: |w_r| <= ||A||_inf max|v_hat_j| and
+  // |v_hat_i,r| <= max|v_hat_i|, so |dot_a| < 2^E with E from the exponents of
+  // n, ||A||_inf and the two maxima; the unit 2^(E - 120) keeps every sum
+  // within 128 bits and 2^-120 of the bound (max|v_hat_j| is bounded by the
+  // window top the previous step set; for j = 0 it is max|r0|).
+  int du[NW];
+  bool dbad = false;
+  {
+    const int ex = j == 0 ? bexp_of_bits(c->vmax[0]) - 1022 : c->vtop[j] - ws.win_bits - 2;
+    const int ea = bexp_of_bits((unsigned long long)__double_as_longlong(c->anorm_inf)) - 1022;
+    const int en = 64 - __clzll((long long)n);
+#pragma unroll
+    for (int a = 0; a < NW; ++a) {
+      const int i = win.lo + a;
+      const int ev = i == j ? ex : bexp_of_bits(c->vmax[i]) - 1022;
+      du[a] = en + ea + ex + ev - 120;
+      dlo[a][threadIdx.x] = 0ull;
+      dhi[a][threadIdx.x] = 0ull;
+    }
+  }
   // Tiles are handed out by a counter, so CTAs that start late (an SM shared
   // with the dense step on the other stream) take fewer tiles.
   __shared__ int next_tile;
@@ -386,7 +484,10 @@ __global__ void __launch_bounds__(SK_THREADS, 3) k_spmv_dots(WS ws, CsrDev A, Wi
   __syncthreads();
   for (int tile = next_tile; tile < ntiles; tile = next_tile) {
     __syncthreads();  // every thread holds this tile's index before it is replaced
-    if (threadIdx.x == 0) next_tile = atomicAdd(tctr, 1);
+    // the next tile's claim is published at the end of this one (its latency
+    // hides behind the tile's work)
+    int claimed = 0;
+    if (threadIdx.x == 0) claimed = atomicAdd(tctr, 1);
     const int64_t r0 = (int64_t)tile * tileR;
     const int ncols = (int)(n - r0 < (int64_t)tileR ? n - r0 : (int64_t)tileR);
     if (SK) tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
@@ -424,6 +525,15 @@ __global__ void __launch_bounds__(SK_THREADS, 3) k_spmv_dots(WS ws, CsrDev A, Wi
       }
     }
     if (SK) tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
+    // this thread's rows of the tile, summed in order, join its exact
+    // fixed-point accumulators: the dots then do not depend on which CTA took
+    // which tile
+#pragma unroll
+    for (int a = 0; a < NW; ++a) {
+      add_fixed128(dlo[a][threadIdx.x], dhi[a][threadIdx.x], (double)d[a], du[a], dbad);
+      d[a] = 0;
+    }
+    if (threadIdx.x == 0) next_tile = claimed;
     __syncthreads();  // next_tile is published
   }
   if (SK) {
@@ -433,56 +543,26 @@ __global__ void __launch_bounds__(SK_THREADS, 3) k_spmv_dots(WS ws, CsrDev A, Wi
       if (row < ws.s) atomic_add128(ws.accV + (int64_t)j * 2 * S_MAX + 2 * row, lo[k], hi[k]);
     }
   }
-  double dd[NW];
-#pragma unroll
-  for (int a = 0; a < NW; ++a) dd[a] = block_sum_lean((double)d[a], buf);
-  wm = block_max_u64(wm, redu);
-  if (threadIdx.x == 0) {
-    double* pp = ws.part + blockIdx.x * NPART;
-#pragma unroll
-    for (int a = 0; a < NW; ++a) pp[a] = dd[a];
-    pp[T_MAX] = __longlong_as_double((long long)wm);
-  }
-  if (last_block(&c->counter)) {
-    if (j >= 1) finish_column(ws, j, grid2, buf, redu);
-    double p[NW];
-#pragma unroll
-    for (int a = 0; a < NW; ++a) {
-      double v = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += ws.part[b * NPART + a];
-      p[a] = block_sum_lean(v, buf);
-    }
-    const unsigned long long wmx = reduce_parts_max(ws.part, gridDim.x, T_MAX, redu);
-    if (threadIdx.x == 0) {
-      // Truncated MGS (Algorithm 1, inner loop) from the dots: with
-      // v_i = alpha_i v_hat_i and w_true = alpha_j w,
-      // H(i,j) = v_i . (w_true - sum_{l<i} H(l,j) v_l).
-      const int t = ws.t;
-      const double aj = c->alpha[j];
-      double h[NW];
-      double bound = fabs(aj) * __longlong_as_double((long long)wmx);
-      c->coef[0] = aj;
+  // the CTA's dot sums (exact), its max |w| (non-finite when a partial was)
+  for (int st = SK_THREADS / 2; st > 0; st >>= 1) {
+    __syncthreads();
+    if ((int)threadIdx.x < st) {
 #pragma unroll
       for (int a = 0; a < NW; ++a) {
-        const int i = win.lo + a;
-        const double ai = c->alpha[i];
-        double v = ai * aj * p[a];
-#pragma unroll
-        for (int b2 = 0; b2 < a; ++b2) {
-          const int l = win.lo + b2;
-          v -= h[b2] * ai * c->alpha[l] * c->gram[i][i - l - 1];
-        }
-        h[a] = v;
-        c->hband[j][i - j + t - 1] = v;
-        c->coef[1 + a] = v * ai;
-        bound += fabs(c->coef[1 + a]) * __longlong_as_double((long long)c->vmax[i]);
+        const unsigned long long l0 = dlo[a][threadIdx.x], l1 = dlo[a][threadIdx.x + st];
+        const unsigned long long nl = l0 + l1;
+        dhi[a][threadIdx.x] += dhi[a][threadIdx.x + st] + (nl < l0 ? 1ull : 0ull);
+        dlo[a][threadIdx.x] = nl;
       }
-      c->wmax = wmx;
-      c->vtop[j + 1] = window_top(bound * (1.0 + 1e-12), ws.win_bits);
-      atomicAdd(&c->matvecs, 1);
-      if (SK) atomicAdd(&c->sketches, 1);
     }
   }
+  __syncthreads();
+  if ((int)threadIdx.x < NW) atomic_add128(ws.dacc + ((int64_t)j * T_MAX + threadIdx.x) * 2,
+                                           dlo[threadIdx.x][0], dhi[threadIdx.x][0]);
+  if (dbad) wm = 0x7FF8000000000000ull;
+  wm = block_max_u64(wm, redu);
+  if (threadIdx.x == 0) ws.part[blockIdx.x * NPART + T_MAX] = __longlong_as_double((long long)wm);
+  spmv_dots_finish<T, NW, SK>(ws, win, j, grid2, du, buf, redu);
 }
 
 int update_grid(const WS& ws) {

@@ -64,7 +64,9 @@ struct Ctl {
 // the same answer.  Steps past the stop compute columns that nothing reads.
 constexpr int SPEC_LAG = 3;
 // Words of the per-cycle block that holds the column accumulators and the tile counters.
-constexpr size_t CYCLE_SCRATCH_WORDS = (size_t)(M_MAX + 2) * 2 * S_MAX + (M_MAX + 2);
+// Layout: the column accumulators, the tile counters ((M_MAX + 2) ints), and
+// the window-dot accumulators of the Arnoldi SpMV (128 bits per step and dot).
+constexpr size_t CYCLE_SCRATCH_WORDS = (size_t)(M_MAX + 2) * 2 * S_MAX + (M_MAX + 2) + (size_t)(M_MAX + 2) * T_MAX * 2;
 __device__ __forceinline__ bool arnoldi_stopped(const Ctl* c, int j) { return c->jstop <= j - SPEC_LAG + 1; }
 
 // Per-cycle log entry kept on the device, mirrored by sdr_cycle_log.
@@ -99,6 +101,7 @@ struct WS {
   unsigned long long* accV; // one accumulator block (2 * S_MAX words) per basis column c = 0 .. M_MAX+1
   int* tctr;                // per-step tile counters of the SpMV (dynamic tile scheduling), M_MAX+2
   double* part3;            // [grid_max][NPART] partials of the control-stream reductions
+  unsigned long long* dacc; // [M_MAX + 2][T_MAX][2] window dots of step j, fixed point (in the cycle scratch)
   int grid_max;
   // small dense (column-major)
   double* SV;    // s x (m+1)

@@ -59,6 +59,11 @@ class sdr_kernel_time(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int32), ("pad", ctypes.c_int32), ("total_ms", ctypes.c_double)]
 
 
+class sdr_trace_entry(ctypes.Structure):
+    _fields_ = [("cls", ctypes.c_int32), ("stream", ctypes.c_int32), ("start_us", ctypes.c_double),
+                ("end_us", ctypes.c_double)]
+
+
 class sdr_cycle_log(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int32), ("checks", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("ell", ctypes.c_int32), ("kprime", ctypes.c_int32), ("kh", ctypes.c_int32),
@@ -92,6 +97,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sdr_recycle_import": ([vp, P(sdr_csr), i64, i32, vp, vp, vp], i32),
         "sdr_profile": ([vp, i32], i32),
         "sdr_profile_get": ([vp, P(sdr_kernel_time), i32, P(i32)], i32),
+        "sdr_trace": ([vp, i32], i32),
+        "sdr_trace_get": ([vp, P(sdr_trace_entry), i32, P(i32)], i32),
         "sdr_csr_transpose": ([P(sdr_csr), vp, vp, vp, vp, vp], i32),
         "sdr_solve_batch": ([i32, P(vp), P(sdr_csr), P(vp), P(vp), P(sdr_stats)], i32),
         "sdr_recycle_batch": ([i32, P(vp), P(sdr_csr), i32], i32),
@@ -289,6 +296,20 @@ def sdr_profile_get(h):
     n = ctypes.c_int32()
     _check(load_library().sdr_profile_get(h, arr, len(KERNEL_CLASSES), ctypes.byref(n)), "sdr_profile_get")
     return {KERNEL_CLASSES[i]: (arr[i].launches, arr[i].total_ms) for i in range(min(n.value, len(KERNEL_CLASSES)))}
+
+
+def sdr_trace(h, cap):
+    return _check(load_library().sdr_trace(h, int(cap)), "sdr_trace")
+
+
+def sdr_trace_get(h):
+    """[(class name, stream, start us, end us)] of the traced launches."""
+    n = ctypes.c_int32()
+    lib = load_library()
+    _check(lib.sdr_trace_get(h, None, 0, ctypes.byref(n)), "sdr_trace_get")
+    arr = (sdr_trace_entry * max(n.value, 1))()
+    _check(lib.sdr_trace_get(h, arr, n.value, ctypes.byref(n)), "sdr_trace_get")
+    return [(KERNEL_CLASSES[e.cls], e.stream, e.start_us, e.end_us) for e in arr[:n.value]]
 
 
 class Solver:

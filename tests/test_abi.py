@@ -55,4 +55,5 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(S.sdr_csr) == 48
     assert ctypes.sizeof(S.sdr_stats) == 72
     assert ctypes.sizeof(S.sdr_cycle_log) == 56
+    assert ctypes.sizeof(S.sdr_trace_entry) == 24
     assert len(S.KERNEL_CLASSES) == 21

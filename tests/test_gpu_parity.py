@@ -239,3 +239,64 @@ def test_already_converged_and_errors(P):
     solver.close()
     with pytest.raises(P.SdrError):
         P.Solver(100, 20, 4, 2, 20, 8, SEED, 1e-8)  # s < m + k + 2
+
+
+def irregular_matrix():
+    """cd2d 64 x 64 with extra weak couplings: row 100 gets 300 more entries
+    (longer than the integer SpMV's exact 64-bit row sums: summed in FP64),
+    and rows 600 .. 1099 six more each, so that the second 512-row block holds
+    more entries than one shared-memory stage (read from global memory
+    instead).  Entries of 1e-3 and a diagonal raised by their sum keep the
+    matrix as well conditioned as the stencil's."""
+    import scipy.sparse as sp
+    A0 = W.make_cd2d(64, (10.0, 10.0))
+    n = A0.n
+    M = sp.csr_matrix((A0.val, A0.col, A0.rowptr), shape=(n, n)).tolil()
+    rng = np.random.default_rng(5)
+    extra = [(100, c) for c in rng.choice(n, 300, replace=False)]
+    for r in range(600, 1100):
+        extra += [(r, c) for c in rng.choice(n, 6, replace=False)]
+    for r, c in extra:
+        if r != c:
+            M[r, c] = M[r, c] + 1e-3 * (1 if rng.random() < 0.5 else -1)
+            M[r, r] = M[r, r] + 1e-3
+    M = M.tocsr()
+    M.sort_indices()
+    return W.stencils.CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64))
+
+
+def test_irregular_rows_and_stage_overflow(P):
+    A = irregular_matrix()
+    lens = np.diff(A.rowptr)
+    assert lens.max() > 252 and A.rowptr[1024] - A.rowptr[512] > 4096
+    b = W.rhs(A.n, 4)
+    m, k, t, s, zeta, tol = 50, 10, 2, 120, 8, 1e-8
+    solver, Ad, x, st, stats, sres, log, ref = run_pair(P, A, b, m, k, t, s, zeta, tol)
+    bn = np.linalg.norm(b)
+    sres_close(sres[:len(ref.sres_per_cycle[0])], ref.sres_per_cycle[0], bn)
+    assert st == 0 and stats["converged"] == 1
+    assert abs(stats["cycles"] - ref.cycles) <= 1
+    assert np.linalg.norm(b - osdr.csr_matvec(A, x)) / bn <= tol * (1 + 1e-9)
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+    solver.close()
+
+
+def test_repeat_solves_bit_identical(P):
+    """Every reduction of the FP64 path has a fixed order (the staged SpMV sums
+    its dots per tile, whichever CTA took the tile), so repeated solves, with
+    captured graphs or direct launches, give the same bits."""
+    A = W.make_cd3d(24, (20.0, 10.0, 5.0))  # 13,824 rows: 14 tiles on up to 152 CTAs
+    b = dev(W.rhs(A.n, 9))
+    Ad = P.CSRDevice.from_numpy(A)
+    outs = []
+    for graphs in (True, True, False):
+        solver = P.Solver(A.n, 40, 8, 2, 120, 8, SEED, 1e-10, graphs=graphs)
+        x, st, stats = solver.solve(Ad, b)
+        sres, _ = solver.history()
+        outs.append((x.cpu().numpy(), stats["cycles"], np.asarray(sres)))
+        assert st == 0
+        solver.close()
+    for x, cyc, sres in outs[1:]:
+        assert cyc == outs[0][1]
+        assert np.array_equal(sres, outs[0][2])
+        assert np.array_equal(x, outs[0][0])
