@@ -498,8 +498,14 @@ sdr_status launch_cycle(CycleRun<T>& r) {
     if (graph) cudaGraphDestroy(graph);
     return s1 != SDR_OK ? s1 : cuda_status(e1);
   }
+  // the kernels keep the priority of the stream they were captured on (the
+  // control stream's dense steps ahead of the SpMV's CTAs), as in direct launches
   cudaGraphExec_t exec = nullptr;
-  const cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
+  cudaError_t e2 = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+  if (e2 != cudaSuccess) {
+    (void)cudaGetLastError();
+    e2 = cudaGraphInstantiate(&exec, graph, 0);
+  }
   cudaGraphDestroy(graph);
   SDR_CK(e2);
   sdr_handle::GraphEntry g{r.Ad.n, r.Ad.nnz, kh, cu, r.rb, xpar, h->launches - before, exec};
