@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(SK_THREADS, 3) k_spmv_dots(WS ws, CsrDev A, Wi
 }
 
 int update_grid(const WS& ws) {
-  const int g = (ws.grid_max / 8) * 2;  // two CTAs per SM, many rows per thread
+  const int g = (ws.grid_max / 8) * 3;  // three CTAs per SM, many rows per thread (two and four ran slower)
   return g < 1 ? 1 : g;
 }
 

@@ -62,7 +62,10 @@ struct Ctl {
 // stopped the cycle at jf <= j - SPEC_LAG + 1 is final when step j starts, and
 // any check still running can only set a larger jf: every CTA of a step sees
 // the same answer.  Steps past the stop compute columns that nothing reads.
-constexpr int SPEC_LAG = 3;
+// Five: the control stream's time per column varies (real checks), and a
+// shorter lag stalls the Arnoldi stream behind it; a longer one computes more
+// steps past a converged check.
+constexpr int SPEC_LAG = 5;
 // Words of the per-cycle block that holds the column accumulators and the tile counters.
 // Layout: the column accumulators, the tile counters ((M_MAX + 2) ints), and
 // the window-dot accumulators of the Arnoldi SpMV (128 bits per step and dot).
