@@ -839,7 +839,7 @@ __device__ inline cplx crecip(cplx d) {
 }
 
 
-__global__ void __launch_bounds__(256) k_ce_invit(WS ws) {
+__global__ void __launch_bounds__(512) k_ce_invit(WS ws) {
   Ctl* c = ws.ctl;
   if (c->jf <= 0) return;
   const int n = c->ell;
@@ -1251,7 +1251,7 @@ cudaError_t launch_cycle_end_part(int part, const WS& ws, int kh, int ucur, cons
       break;
     }
     case 4: k_ce_eig<<<1, 512, ce_eig_smem(), st>>>(ws); break;
-    case 5: k_ce_invit<<<KC, 256, 0, st>>>(ws); break;
+    case 5: k_ce_invit<<<KC, 512, 0, st>>>(ws); break;
     case 6: k_ce_select<<<1, 256, 0, st>>>(ws); break;
     case 7: k_ce_finish<<<1, 512, 0, st>>>(ws, kh, ucur); break;
     case 8: k_ce_sketch_update<<<K_MAX, 512, 0, st>>>(ws, kh, SU, SAU, SUn, SAUn); break;

@@ -13,7 +13,7 @@
 
 namespace sdr {
 
-constexpr int DT = 512;  // threads of the dense-step CTA
+constexpr int DT = 768;  // threads of the dense-step CTA (512 and 1024 ran slower)
 
 // ---- fixed-point helpers (see eidot.cuh) ----------------------------------
 __device__ __forceinline__ Q52 unpack(unsigned long long b) {
