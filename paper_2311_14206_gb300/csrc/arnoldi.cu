@@ -975,7 +975,7 @@ __global__ void __launch_bounds__(RB_THREADS, 2) k_recycle_rb(WS ws, const T* __
       const YK* yrow = ytab + w * CPT;
       const int4* xrow = (const int4*)(xq + 2 * lane);
       static_assert(RB_RPL == 2, "two rows per lane: one 16-byte load");
-#pragma unroll 2
+#pragma unroll 4
       for (int l = 0; l < d; ++l) {
         const int4 xx = xrow[l * (RB_ROWS / 2)];
         Q52 x[RB_RPL];
