@@ -300,3 +300,35 @@ def test_repeat_solves_bit_identical(P):
         assert cyc == outs[0][1]
         assert np.array_equal(sres, outs[0][2])
         assert np.array_equal(x, outs[0][0])
+
+
+def test_trace_entries(P):
+    """sdr_trace keeps one entry per profiled launch: on the stream it was
+    issued to, ordered within each stream, end after start, and as many per
+    class as sdr_profile_get counts; a cap bounds the list."""
+    A = W.make_cd2d(40, (20.0, 5.0))
+    b = dev(W.rhs(A.n, 2))
+    Ad = P.CSRDevice.from_numpy(A)
+    solver = P.Solver(A.n, 40, 8, 2, 120, 8, SEED, 1e-8)
+    P.sdr_profile(solver.h, True)
+    P.sdr_trace(solver.h, 1 << 16)
+    x, st, stats = solver.solve(Ad, b)
+    assert st == 0
+    tr = P.sdr_trace_get(solver.h)
+    prof = P.sdr_profile_get(solver.h)
+    assert len(tr) == sum(n for n, _ in prof.values()) > 0
+    for cls, (n, _) in prof.items():
+        assert sum(1 for e in tr if e[0] == cls) == n
+    assert all(e[1] in (0, 1) and 0.0 <= e[2] <= e[3] for e in tr)
+    assert {e[1] for e in tr if e[0] == "spmv_dots"} == {0}
+    assert {e[1] for e in tr if e[0] == "step_dense"} == {1}
+    for s_ in (0, 1):
+        starts = [e[2] for e in tr if e[1] == s_]
+        assert starts == sorted(starts)
+    P.sdr_trace(solver.h, 5)
+    solver.solve(Ad, b)
+    assert len(P.sdr_trace_get(solver.h)) == 5
+    P.sdr_trace(solver.h, 0)
+    assert P.sdr_trace_get(solver.h) == []
+    P.sdr_profile(solver.h, False)
+    solver.close()
