@@ -56,7 +56,7 @@ STEP_EQUIV_PER_SYSTEM = 400
 # DRAM bytes (read + write) per row of one k_spmv_dots launch, from the ncu capture in
 # profiles/spmv_dots_cd3d_96.md (107.0 MB per launch at 884,736 rows); set to None when the
 # kernel changes until it is captured again.
-SPMV_DRAM_BYTES_PER_ROW = 107.0e6 / 884736
+SPMV_DRAM_BYTES_PER_ROW = (106.546e6 + 4.053e6) / 884736
 
 
 def peaks():
