@@ -514,39 +514,15 @@ __device__ inline float block_sum_f(float v, float* red) {
 
 __device__ inline float& HF(float* H, int ldh, int i, int j) { return H[i + j * ldh]; }
 
-// Row and column parts of one 3x3 (or 2x2) reflector of the bulge chase, with
-// every load of a lane (at most NS entries per row or column) issued first.
+// Column part of one 3x3 (or 2x2) reflector of the bulge chase on rows
+// l + off + stride t <= imax, with every load (at most NS rows) issued first.
 template <int NS>
-__device__ __forceinline__ void row_update(float* H, int ldh, int k, int nn, int lane, bool three, float qq,
-                                           float rq, float xx, float yy, float zz) {
-  float a0[NS], a1[NS], a2[NS];
-#pragma unroll
-  for (int t = 0; t < NS; ++t) {
-    const int jj = k + lane + 32 * t;
-    const bool in = jj <= nn;
-    a0[t] = in ? HF(H, ldh, k, jj) : 0.f;
-    a1[t] = in ? HF(H, ldh, k + 1, jj) : 0.f;
-    a2[t] = (in && three) ? HF(H, ldh, k + 2, jj) : 0.f;
-  }
-#pragma unroll
-  for (int t = 0; t < NS; ++t) {
-    const int jj = k + lane + 32 * t;
-    if (jj <= nn) {
-      const float pp = a0[t] + qq * a1[t] + rq * a2[t];
-      if (three) HF(H, ldh, k + 2, jj) = a2[t] - pp * zz;
-      HF(H, ldh, k + 1, jj) = a1[t] - pp * yy;
-      HF(H, ldh, k, jj) = a0[t] - pp * xx;
-    }
-  }
-}
-
-template <int NS>
-__device__ __forceinline__ void col_update(float* H, int ldh, int k, int l, int imax, int lane, bool three,
+__device__ __forceinline__ void col_update(float* H, int ldh, int k, int l, int imax, int off, int stride, bool three,
                                            float qq, float rq, float xx, float yy, float zz) {
   float b0[NS], b1[NS], b2[NS];
 #pragma unroll
   for (int t = 0; t < NS; ++t) {
-    const int i = l + lane + 32 * t;
+    const int i = l + off + stride * t;
     const bool in = i <= imax;
     b0[t] = in ? HF(H, ldh, i, k) : 0.f;
     b1[t] = in ? HF(H, ldh, i, k + 1) : 0.f;
@@ -554,7 +530,7 @@ __device__ __forceinline__ void col_update(float* H, int ldh, int k, int l, int 
   }
 #pragma unroll
   for (int t = 0; t < NS; ++t) {
-    const int i = l + lane + 32 * t;
+    const int i = l + off + stride * t;
     if (i <= imax) {
       const float pp = xx * b0[t] + yy * b1[t] + zz * b2[t];
       if (three) HF(H, ldh, i, k + 2) = b2[t] - pp * rq;
@@ -564,10 +540,56 @@ __device__ __forceinline__ void col_update(float* H, int ldh, int k, int l, int 
   }
 }
 
-// Francis double-shift QR on the upper-Hessenberg H (n x n, ld ldh), one warp;
-// eigenvalues into wr, wi.  Returns false when the iteration limit is reached.
-__device__ bool hqr_f32_warp(float* H, int ldh, int n, float* wr, float* wi) {
-  const int lane = threadIdx.x & 31;
+// Row part of a reflector on columns c0 + off + stride t <= c1 (rows k..k+2,
+// or k..k+1 when !three), with every load (at most NS columns) issued first.
+template <int NS>
+__device__ __forceinline__ void row_update_range(float* H, int ldh, int k, int c0, int c1, int off, int stride,
+                                                 bool three, float qq, float rq, float xx, float yy, float zz) {
+  float a0[NS], a1[NS], a2[NS];
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int jj = c0 + off + stride * t;
+    const bool in = jj <= c1;
+    a0[t] = in ? HF(H, ldh, k, jj) : 0.f;
+    a1[t] = in ? HF(H, ldh, k + 1, jj) : 0.f;
+    a2[t] = (in && three) ? HF(H, ldh, k + 2, jj) : 0.f;
+  }
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int jj = c0 + off + stride * t;
+    if (jj <= c1) {
+      const float pp = a0[t] + qq * a1[t] + rq * a2[t];
+      if (three) HF(H, ldh, k + 2, jj) = a2[t] - pp * zz;
+      HF(H, ldh, k + 1, jj) = a1[t] - pp * yy;
+      HF(H, ldh, k, jj) = a0[t] - pp * xx;
+    }
+  }
+}
+
+// Warps of the QR iteration: warp 0 on the region around the bulge, QR_RW on
+// the row part and QR_CW on the column part of the rest.
+constexpr int QR_RW = 2, QR_CW = 2, QR_WARPS = 1 + QR_RW + QR_CW;
+__device__ __forceinline__ void qr_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * QR_WARPS) : "memory"); }
+
+// Francis double-shift QR on the upper-Hessenberg H (n x n, ld ldh), the
+// first QR_WARPS warps of the block; eigenvalues into wr, wi.  Returns false
+// when the iteration limit is reached.  All these warps follow the same
+// control flow (their decisions are read from the same shared values); shared
+// writes outside the bulge chase are made by warp 0 between barriers.
+//
+// Each step k of the bulge chase applies one reflector to rows k..k+2 (columns
+// k..nn) and to columns k..k+2 (rows l..min(k+3, nn)).  Warp 0 takes the 4 x 4
+// region rows and columns k..k+3 (in registers, every lane the same
+// arithmetic; lane 0 stores) and forms the next reflector from its column k;
+// the other warps take the rest: QR_RW warps the row part on columns k+4..nn,
+// QR_CW warps the column part on rows l..k-1.  The parts touch disjoint
+// elements, each element gets the operations of the one-warp order, and the
+// next step's inputs from other warps (column k+4 of rows k+1..k+2, row k of
+// columns k+1..k+3) are complete after the one barrier between steps.
+// rs: 8 floats of shared memory.
+__device__ bool hqr_f32_2w(float* H, int ldh, int n, float* wr, float* wi, float* rs) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, wrp = tid >> 5;
   const float eps = 1.1920929e-7f;
   float an = 0.f;
   for (int idx = lane; idx < n * n; idx += 32) {
@@ -587,12 +609,12 @@ __device__ bool hqr_f32_warp(float* H, int ldh, int n, float* wr, float* wi) {
         if (fabsf(HF(H, ldh, l, l - 1)) <= eps * s) break;
         --l;
       }
-      __syncwarp();
-      if (l > 0 && lane == 0) HF(H, ldh, l, l - 1) = 0.f;
-      __syncwarp();
+      qr_bar();
+      if (l > 0 && tid == 0) HF(H, ldh, l, l - 1) = 0.f;
+      qr_bar();
       float x = HF(H, ldh, nn, nn);
       if (l == nn) {
-        if (lane == 0) { wr[nn] = x + tsh; wi[nn] = 0.f; }
+        if (tid == 0) { wr[nn] = x + tsh; wi[nn] = 0.f; }
         nn -= 1;
         break;
       }
@@ -602,7 +624,7 @@ __device__ bool hqr_f32_warp(float* H, int ldh, int n, float* wr, float* wi) {
         const float p = 0.5f * (y - x), q = p * p + w;
         float z = sqrtf(fabsf(q));
         x += tsh;
-        if (lane == 0) {
+        if (tid == 0) {
           if (q >= 0.f) {
             z = p + copysignf(z, p);
             wr[nn - 1] = wr[nn] = x + z;
@@ -618,15 +640,16 @@ __device__ bool hqr_f32_warp(float* H, int ldh, int n, float* wr, float* wi) {
         break;
       }
       if (its >= 60 || total >= 60 * n) {
-        for (int i = lane; i <= nn; i += 32) { wr[i] = NAN; wi[i] = 0.f; }
-        __syncwarp();
+        for (int i = tid; i <= nn; i += 32 * QR_WARPS) { wr[i] = NAN; wi[i] = 0.f; }
+        qr_bar();
         return false;
       }
       if (its == 10 || its == 20) {  // exceptional shift
         tsh += x;
-        __syncwarp();
-        for (int i = lane; i <= nn; i += 32) HF(H, ldh, i, i) -= x;
-        __syncwarp();
+        qr_bar();
+        if (wrp == 0)
+          for (int i = lane; i <= nn; i += 32) HF(H, ldh, i, i) -= x;
+        qr_bar();
         const float s = fabsf(HF(H, ldh, nn, nn - 1)) + fabsf(HF(H, ldh, nn - 1, nn - 2));
         x = y = 0.75f * s;
         w = -0.4375f * s * s;
@@ -649,54 +672,119 @@ __device__ bool hqr_f32_warp(float* H, int ldh, int n, float* wr, float* wi) {
         if (u <= eps * v) break;
         --m;
       }
-      __syncwarp();
-      for (int i = m + 2 + lane; i <= nn; i += 32) {
-        HF(H, ldh, i, i - 2) = 0.f;
-        if (i != m + 2) HF(H, ldh, i, i - 3) = 0.f;
-      }
-      __syncwarp();
-      for (int k = m; k <= nn - 1; ++k) {
-        if (k != m) {
-          p = HF(H, ldh, k, k - 1);
-          q = HF(H, ldh, k + 1, k - 1);
-          r = (k != nn - 1) ? HF(H, ldh, k + 2, k - 1) : 0.f;
-          x = fabsf(p) + fabsf(q) + fabsf(r);
-          if (x != 0.f) { const float inv = __fdividef(1.f, x); p *= inv; q *= inv; r *= inv; }
+      qr_bar();
+      if (wrp == 0)
+        for (int i = m + 2 + lane; i <= nn; i += 32) {
+          HF(H, ldh, i, i - 2) = 0.f;
+          if (i != m + 2) HF(H, ldh, i, i - 3) = 0.f;
         }
-        const float s = copysignf(sqrtf(p * p + q * q + r * r), p);
-        __syncwarp();
+      qr_bar();
+      float s = copysignf(sqrtf(p * p + q * q + r * r), p);
+      float xnorm = 0.f;
+      for (int k = m; k <= nn - 1; ++k) {
+        const bool three = k != nn - 1;
+        const bool has_next = k + 1 <= nn - 1;
+        float np = 0.f, nq = 0.f, nr = 0.f;
         if (s != 0.f) {
-          if (lane == 0) {
-            if (k == m) {
-              if (l != m) HF(H, ldh, k, k - 1) = -HF(H, ldh, k, k - 1);
-            } else {
-              HF(H, ldh, k, k - 1) = -s * x;
-            }
-          }
-          p += s;
+          const float ps = p + s;
           // the values only locate the eigenvalues (refined in FP64 later):
           // approximate reciprocals are enough
-          const float is = __fdividef(1.f, s), ip = __fdividef(1.f, p);
-          const float xx = p * is, yy = q * is, zz = r * is, qq = q * ip, rq = r * ip;
-          __syncwarp();
-          // The reflector touches rows k..k+2 of columns k..nn, then columns
-          // k..k+2 of rows l..min(nn, k+3).  A lane's columns (rows) are
-          // disjoint, so all its loads are issued before any store: in
-          // chunks of two per lane while the range is short, else four.
-          const bool three = k != nn - 1;
-          if (nn - k < 64) {
-            row_update<2>(H, ldh, k, nn, lane, three, qq, rq, xx, yy, zz);
+          const float is = __fdividef(1.f, s), ip = __fdividef(1.f, ps);
+          const float xx = ps * is, yy = q * is, zz = r * is, qq = q * ip, rq = r * ip;
+          if (wrp == 0) {
+            if (lane == 0) {
+              if (k == m) {
+                if (l != m) HF(H, ldh, k, k - 1) = -HF(H, ldh, k, k - 1);
+              } else {
+                HF(H, ldh, k, k - 1) = -s * xnorm;
+              }
+            }
+            // the 4 x 4 region: row part on columns k..hc, column part on rows k..rb
+            const int hc = nn < k + 3 ? nn : k + 3;
+            const int rb = hc;
+            float bl[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int c2 = 0; c2 < 4; ++c2)
+                bl[i][c2] = (k + i <= nn && k + c2 <= hc) ? HF(H, ldh, k + i, k + c2) : 0.f;
+#pragma unroll
+            for (int c2 = 0; c2 < 4; ++c2) {
+              if (k + c2 <= hc) {
+                const float a2 = three ? bl[2][c2] : 0.f;
+                const float pp = bl[0][c2] + qq * bl[1][c2] + rq * a2;
+                if (three) bl[2][c2] = a2 - pp * zz;
+                bl[1][c2] = bl[1][c2] - pp * yy;
+                bl[0][c2] = bl[0][c2] - pp * xx;
+              }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              if (k + i <= rb) {
+                const float b2 = three ? bl[i][2] : 0.f;
+                const float pp = xx * bl[i][0] + yy * bl[i][1] + zz * b2;
+                if (three) bl[i][2] = b2 - pp * rq;
+                bl[i][1] = bl[i][1] - pp * qq;
+                bl[i][0] = bl[i][0] - pp;
+              }
+            }
+            __syncwarp();
+            if (lane == 0) {
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int c2 = 0; c2 < 4; ++c2)
+                  if (k + i <= nn && k + c2 <= hc) HF(H, ldh, k + i, k + c2) = bl[i][c2];
+            }
+            if (has_next) {
+              np = bl[1][0];
+              nq = bl[2][0];
+              nr = (k + 1 != nn - 1) ? bl[3][0] : 0.f;
+            }
+          } else if (wrp <= QR_RW) {
+            // row part on columns k+4..nn
+            const int off = 32 * (wrp - 1) + lane, stride = 32 * QR_RW;
+            if (nn - k - 4 < 64) {
+              row_update_range<1>(H, ldh, k, k + 4, nn, off, stride, three, qq, rq, xx, yy, zz);
+            } else {
+              row_update_range<(D_MAX + 32 * QR_RW - 1) / (32 * QR_RW)>(H, ldh, k, k + 4, nn, off, stride, three, qq,
+                                                                         rq, xx, yy, zz);
+            }
           } else {
-            row_update<5>(H, ldh, k, nn, lane, three, qq, rq, xx, yy, zz);
+            // column part on rows l..k-1
+            const int off = 32 * (wrp - 1 - QR_RW) + lane, stride = 32 * QR_CW;
+            if (k - 1 - l < 64) {
+              col_update<1>(H, ldh, k, l, k - 1, off, stride, three, qq, rq, xx, yy, zz);
+            } else {
+              col_update<(D_MAX + 32 * QR_CW - 1) / (32 * QR_CW)>(H, ldh, k, l, k - 1, off, stride, three, qq, rq,
+                                                                  xx, yy, zz);
+            }
           }
-          __syncwarp();
-          const int imax = nn < k + 3 ? nn : k + 3;
-          if (imax - l < 64) {
-            col_update<2>(H, ldh, k, l, imax, lane, three, qq, rq, xx, yy, zz);
-          } else {
-            col_update<5>(H, ldh, k, l, imax, lane, three, qq, rq, xx, yy, zz);
+        } else if (wrp == 0 && has_next) {
+          np = HF(H, ldh, k + 1, k);
+          nq = HF(H, ldh, k + 2, k);
+          nr = (k + 1 != nn - 1) ? HF(H, ldh, k + 3, k) : 0.f;
+        }
+        float* slot = rs + 4 * (k & 1);
+        if (tid == 0) {
+          slot[0] = np;
+          slot[1] = nq;
+          slot[2] = nr;
+        }
+        qr_bar();
+        if (has_next) {
+          p = slot[0];
+          q = slot[1];
+          r = slot[2];
+          xnorm = fabsf(p) + fabsf(q) + fabsf(r);
+          if (xnorm != 0.f) {
+            const float inv = __fdividef(1.f, xnorm);
+            p *= inv;
+            q *= inv;
+            r *= inv;
           }
-          __syncwarp();
+          const float ss = p * p + q * q + r * r;  // an approximate root is enough here
+          s = copysignf(ss > 0.f ? ss * rsqrtf(ss) : 0.f, p);
         }
       }
     }
@@ -704,7 +792,7 @@ __device__ bool hqr_f32_warp(float* H, int ldh, int n, float* wr, float* wi) {
   return true;
 }
 
-__global__ void __launch_bounds__(512) k_ce_eig(WS ws) {
+__global__ void __launch_bounds__(512, 1) k_ce_eig(WS ws) {
   Ctl* c = ws.ctl;
   if (c->jf <= 0) return;
   const int n = c->ell;
@@ -763,8 +851,9 @@ __global__ void __launch_bounds__(512) k_ce_eig(WS ws) {
     if (i > jj + 1) HF(H, ldh, i, jj) = 0.f;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const bool good = hqr_f32_warp(H, ldh, n, wr, wi);
+  __shared__ float rsl[8];
+  if (threadIdx.x < 32 * QR_WARPS) {
+    const bool good = hqr_f32_2w(H, ldh, n, wr, wi, rsl);
     if (threadIdx.x == 0) ok = good ? 1 : 0;
   }
   __syncthreads();
