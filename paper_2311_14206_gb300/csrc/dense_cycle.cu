@@ -602,12 +602,22 @@ __device__ bool hqr_f32_2w(float* H, int ldh, int n, float* wr, float* wi, float
   while (nn >= 0) {
     int its = 0;
     while (true) {
-      int l = nn;
-      while (l > 0) {
-        float s = fabsf(HF(H, ldh, l - 1, l - 1)) + fabsf(HF(H, ldh, l, l));
-        if (s == 0.f) s = an;
-        if (fabsf(HF(H, ldh, l, l - 1)) <= eps * s) break;
-        --l;
+      // the largest l <= nn with a negligible H(l, l-1) (0 if none): 32
+      // candidates per round, one per lane, the largest found by a ballot
+      int l = 0;
+      for (int base = nn; base > 0; base -= 32) {
+        const int cand = base - lane;
+        bool hit = false;
+        if (cand > 0) {
+          float s = fabsf(HF(H, ldh, cand - 1, cand - 1)) + fabsf(HF(H, ldh, cand, cand));
+          if (s == 0.f) s = an;
+          hit = fabsf(HF(H, ldh, cand, cand - 1)) <= eps * s;
+        }
+        const unsigned msk = __ballot_sync(0xffffffffu, hit);
+        if (msk) {
+          l = base - (__ffs(msk) - 1);
+          break;
+        }
       }
       qr_bar();
       if (l > 0 && tid == 0) HF(H, ldh, l, l - 1) = 0.f;
@@ -656,21 +666,41 @@ __device__ bool hqr_f32_2w(float* H, int ldh, int n, float* wr, float* wi, float
       }
       ++its;
       ++total;
-      int m = nn - 2;
-      float p = 0.f, q = 0.f, r = 0.f, z = 0.f;
-      while (true) {
-        z = HF(H, ldh, m, m);
-        const float rr = x - z, ss = y - z;
-        p = (rr * ss - w) / HF(H, ldh, m + 1, m) + HF(H, ldh, m, m + 1);
-        q = HF(H, ldh, m + 1, m + 1) - z - rr - ss;
-        r = HF(H, ldh, m + 2, m + 1);
-        const float inv = 1.f / (fabsf(p) + fabsf(q) + fabsf(r));
-        p *= inv; q *= inv; r *= inv;
-        if (m == l) break;
-        const float u = fabsf(HF(H, ldh, m, m - 1)) * (fabsf(q) + fabsf(r));
-        const float v = fabsf(p) * (fabsf(HF(H, ldh, m - 1, m - 1)) + fabsf(z) + fabsf(HF(H, ldh, m + 1, m + 1)));
-        if (u <= eps * v) break;
-        --m;
+      // where the double shift starts: the largest m in [l, nn-2] whose
+      // first column (p, q, r) of (H - sigma1)(H - sigma2) decouples from row
+      // m-1 (or m = l), 32 candidates per round as above
+      int m = l;
+      float p = 0.f, q = 0.f, r = 0.f;
+      for (int base = nn - 2; base >= l; base -= 32) {
+        const int cand = base - lane;
+        bool stop = false;
+        float pc = 0.f, qc = 0.f, rc = 0.f;
+        if (cand >= l) {
+          const float z = HF(H, ldh, cand, cand);
+          const float rr = x - z, ss = y - z;
+          pc = (rr * ss - w) / HF(H, ldh, cand + 1, cand) + HF(H, ldh, cand, cand + 1);
+          qc = HF(H, ldh, cand + 1, cand + 1) - z - rr - ss;
+          rc = HF(H, ldh, cand + 2, cand + 1);
+          const float inv = 1.f / (fabsf(pc) + fabsf(qc) + fabsf(rc));
+          pc *= inv; qc *= inv; rc *= inv;
+          if (cand == l) {
+            stop = true;
+          } else {
+            const float u = fabsf(HF(H, ldh, cand, cand - 1)) * (fabsf(qc) + fabsf(rc));
+            const float v = fabsf(pc) * (fabsf(HF(H, ldh, cand - 1, cand - 1)) + fabsf(z) +
+                                         fabsf(HF(H, ldh, cand + 1, cand + 1)));
+            stop = u <= eps * v;
+          }
+        }
+        const unsigned msk = __ballot_sync(0xffffffffu, stop);
+        if (msk) {
+          const int src = __ffs(msk) - 1;
+          m = base - src;
+          p = __shfl_sync(0xffffffffu, pc, src);
+          q = __shfl_sync(0xffffffffu, qc, src);
+          r = __shfl_sync(0xffffffffu, rc, src);
+          break;
+        }
       }
       qr_bar();
       if (wrp == 0)
