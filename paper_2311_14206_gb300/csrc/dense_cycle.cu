@@ -888,24 +888,29 @@ __global__ void __launch_bounds__(512, 1) k_ce_eig(WS ws) {
   }
   __syncthreads();
   // --- candidates: k + KC_MARGIN largest |mu| (FP32 order), pairs whole ---
+  // The order: larger |mu| first, then larger real part, then lower index (a
+  // strict total order); each thread ranks its eigenvalues against all others.
+  // (a value the iteration left as NaN sorts last, so the ranks stay a permutation)
+  __shared__ float mag[D_MAX], wrs[D_MAX];
+  __shared__ int ord[D_MAX];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float h = hypotf(wr[i], wi[i]);
+    mag[i] = isnan(h) ? -1.f : h;
+    wrs[i] = isnan(wr[i]) ? -INFINITY : wr[i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float mi = mag[i], ri = wrs[i];
+    int rank = 0;
+    for (int j2 = 0; j2 < n; ++j2) {
+      const float mj = mag[j2], rj = wrs[j2];
+      rank += (mj > mi) || (mj == mi && rj > ri) || (mj == mi && rj == ri && j2 < i);
+    }
+    ord[rank] = i;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     if (!ok) c->rankfail = 1;
-    int ord[D_MAX];
-    for (int i = 0; i < n; ++i) ord[i] = i;
-    for (int i = 1; i < n; ++i) {
-      const int v = ord[i];
-      const float mv = hypotf(wr[v], wi[v]);
-      int y = i - 1;
-      while (y >= 0) {
-        const int u = ord[y];
-        const float mu = hypotf(wr[u], wi[u]);
-        const bool after = (mu < mv) || (mu == mv && wr[u] < wr[v]) || (mu == mv && wr[u] == wr[v] && u > v);
-        if (!after) break;
-        ord[y + 1] = u;
-        --y;
-      }
-      ord[y + 1] = v;
-    }
     int kc = ws.k + KC_MARGIN < n ? ws.k + KC_MARGIN : n;
     if (kc > 0 && kc < n) {
       const int a = ord[kc - 1], b = ord[kc];
@@ -920,10 +925,10 @@ __global__ void __launch_bounds__(512, 1) k_ce_eig(WS ws) {
       ++nc;
     }
     L.cnt[0] = nc;
-    for (int i = 0; i < n; ++i) {
-      L.wr[i] = wr[i];
-      L.wi[i] = wi[i];
-    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    L.wr[i] = wr[i];
+    L.wi[i] = wi[i];
   }
 }
 
