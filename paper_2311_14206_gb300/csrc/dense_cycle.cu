@@ -1066,57 +1066,103 @@ __global__ void __launch_bounds__(512) k_ce_invit(WS ws) {
     udr[k] = inv.re;
     udi[k] = inv.im;
   }
+  // the row interchanges of the factorisation as one permutation: row k of
+  // P x is x[sig[k]]
+  __shared__ int sig[D_MAX];
+  __shared__ double yr[D_MAX], yi[D_MAX];
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < n; ++k) sig[k] = k;
+    for (int k = 0; k < n; ++k) {
+      const int p = perm[k];
+      const int t = sig[k];
+      sig[k] = sig[p];
+      sig[p] = t;
+    }
+  }
   for (int i = threadIdx.x; i < n; i += blockDim.x) { xr[i] = 1.0; xi[i] = 0.0; }
   __syncthreads();
+  // The triangular solves: thread t owns row t (n <= D_MAX <= blockDim.x)
+  // and keeps the next PF entries of its row of L (or U) in flight, so the
+  // L2 latency of the factors stays off the column-by-column chain; one
+  // barrier of the first nb threads per column.
+  constexpr int PF = 4;
+  const int t = threadIdx.x;
+  const bool own = t < n;
+  const int nb = (n + 31) / 32 * 32;
+  const bool inb = t < nb;
   for (int it = 0; it < 3; ++it) {
-    if (threadIdx.x == 0) {  // row interchanges of the factorisation
-      for (int k = 0; k < n; ++k) {
-        const int p = perm[k];
-        if (p != k) {
-          double t = xr[k]; xr[k] = xr[p]; xr[p] = t;
-          t = xi[k]; xi[k] = xi[p]; xi[p] = t;
+    if (own) {
+      yr[t] = xr[sig[t]];
+      yi[t] = xi[sig[t]];
+    }
+    __syncthreads();
+    if (inb) {
+      // L y = P x (unit lower): at column k, rows t > k take y_k
+      cplx lp[PF];
+#pragma unroll
+      for (int u = 0; u < PF; ++u)
+        lp[u] = (own && u < t) ? cplx{Ar[t + (int64_t)u * LDD], cx ? Ai[t + (int64_t)u * LDD] : 0.0} : cplx{0.0, 0.0};
+      for (int k0 = 0; k0 < n; k0 += PF) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+          const int k = k0 + u;
+          if (k < n) {
+            if (own && t > k) {
+              const cplx v = csub(cplx{yr[t], yi[t]}, cmul(lp[u], cplx{yr[k], yi[k]}));
+              yr[t] = v.re;
+              yi[t] = v.im;
+            }
+            const int kn = k + PF;
+            lp[u] = (own && kn < t) ? cplx{Ar[t + (int64_t)kn * LDD], cx ? Ai[t + (int64_t)kn * LDD] : 0.0}
+                                    : cplx{0.0, 0.0};
+            asm volatile("bar.sync 2, %0;" ::"r"(nb) : "memory");
+          }
+        }
+      }
+      // U x = y (upper), columns from the last: x_k = y_k / u_kk, then rows t < k
+      cplx up[PF];
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int kk = n - 1 - u;
+        up[u] = (own && kk > t) ? cplx{Ar[t + (int64_t)kk * LDD], cx ? Ai[t + (int64_t)kk * LDD] : 0.0}
+                                : cplx{0.0, 0.0};
+      }
+      for (int k0 = n - 1; k0 >= 0; k0 -= PF) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+          const int k = k0 - u;
+          if (k >= 0) {
+            const cplx xk = cmul(cplx{yr[k], yi[k]}, cplx{udr[k], udi[k]});
+            if (own && t < k) {
+              const cplx v = csub(cplx{yr[t], yi[t]}, cmul(up[u], xk));
+              yr[t] = v.re;
+              yi[t] = v.im;
+            }
+            if (t == k) {
+              xr[k] = xk.re;
+              xi[k] = xk.im;
+            }
+            const int kn = k - PF;
+            up[u] = (own && kn > t && kn >= 0)
+                        ? cplx{Ar[t + (int64_t)kn * LDD], cx ? Ai[t + (int64_t)kn * LDD] : 0.0}
+                        : cplx{0.0, 0.0};
+            asm volatile("bar.sync 2, %0;" ::"r"(nb) : "memory");
+          }
         }
       }
     }
     __syncthreads();
-    for (int k = 0; k < n; ++k) {  // unit lower triangular solve, column oriented
-      const cplx xk{xr[k], xi[k]};
-      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
-        const cplx l{Ar[i + (int64_t)k * LDD], cx ? Ai[i + (int64_t)k * LDD] : 0.0};
-        const cplx v = csub(cplx{xr[i], xi[i]}, cmul(l, xk));
-        xr[i] = v.re;
-        xi[i] = v.im;
-      }
-      __syncthreads();
+    // normalise by the entry of largest |re| + |im| (ties: lowest index)
+    unsigned long long key = 0ull;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double a = fabs(xr[i]) + fabs(xi[i]);
+      const unsigned long long kk =
+          ((unsigned long long)__double_as_longlong(a) & ~0x3FFull) | (unsigned long long)(0x3FF - i);
+      key = kk > key ? kk : key;
     }
-    for (int k = n - 1; k >= 0; --k) {  // upper triangular solve
-      if (threadIdx.x == 0) {
-        const cplx v = cmul(cplx{xr[k], xi[k]}, cplx{udr[k], udi[k]});
-        xr[k] = v.re;
-        xi[k] = v.im;
-      }
-      __syncthreads();
-      const cplx xk{xr[k], xi[k]};
-      for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        const cplx u{Ar[i + (int64_t)k * LDD], cx ? Ai[i + (int64_t)k * LDD] : 0.0};
-        const cplx v = csub(cplx{xr[i], xi[i]}, cmul(u, xk));
-        xr[i] = v.re;
-        xi[i] = v.im;
-      }
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {  // normalise by the entry of largest |re| + |im| (first such index)
-      double best = -1.0;
-      int bi = 0;
-      for (int i = 0; i < n; ++i) {
-        const double a = fabs(xr[i]) + fabs(xi[i]);
-        if (a > best) { best = a; bi = i; }
-      }
-      bc[0] = xr[bi];
-      bc[1] = xi[bi];
-    }
-    __syncthreads();
-    const cplx piv{bc[0], bc[1]};
+    key = block_max_u64(key, redu);
+    const int bi = 0x3FF - (int)(key & 0x3FF);
+    const cplx piv{xr[bi], xi[bi]};
     const cplx inv = (piv.re == 0.0 && piv.im == 0.0) ? cplx{1.0, 0.0} : crecip(piv);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
