@@ -153,7 +153,7 @@ def run_gpu(args, rank, world):
     col = torch.as_tensor(A0.col, device=dev)
     vals = [torch.as_tensor(system_values(A0, dvec, diag_pos, i + 1, cfg["eps"]), device=dev) for i in range(nsys)]
     # each replica solves its own right-hand sides (weak scaling)
-    bs = [torch.as_tensor(W.rhs(N, 1000 * rank + i), device=dev) for i in range(nsys)]
+    bs = [torch.as_tensor(W.rhs(N, replica_rhs_seed(rank, i)), device=dev) for i in range(nsys)]
     mats = [P.CSRDevice(N, rowptr, col, v) for v in vals]
     solver = P.Solver(N, cfg["m"], cfg["k"], cfg["t"], cfg["s"], cfg["zeta"], cfg["seed"], cfg["rel_tol"])
     xs = torch.zeros(N, dtype=torch.float64, device=dev)
@@ -620,6 +620,26 @@ def cpu_baseline(step_equiv):
                         f"scaled by {step_equiv:.0f} step-equivalents per system"))
 
 
+def replica_rhs_seed(rank, i):
+    """Seed of the right-hand side of system i on replica `rank`: every replica solves
+    its own right-hand sides (weak scaling), distinct for i < 1000."""
+    return 1000 * rank + i
+
+
+def reduce_over_ranks(ms, e2e_ms, systems, world, device):
+    """Whole-job times over `world` replicas.  ms: one replica's timed region (the
+    `systems` solves); e2e_ms: its end-to-end time per system.  Both are maxed over the
+    ranks (the slowest replica ends the job); every rank returns the same pair: ms per
+    system of the whole job (all ranks' systems / the slowest region) and the
+    end-to-end figure on the same footing."""
+    if world == 1:
+        return ms / systems, e2e_ms
+    import torch
+    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t[0]) / (systems * world), float(t[1]) / world
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -681,12 +701,7 @@ def main():
             print(json.dumps(fn(args)), flush=True)
         return
     res = run_gpu(args, rank, world)
-    ms_per_system = res["ms"] / res["systems"]
-    if world > 1:
-        t = torch.tensor([res["ms"]], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-        ms_per_system = ms_total / (res["systems"] * world)
+    ms_per_system, e2e_per_system = reduce_over_ranks(res["ms"], res["e2e_ms"], res["systems"], world, "cuda")
     if rank == 0:
         agg = res["agg"]
         step_equiv = (agg["steps"] + agg["checks"] + WORKLOAD["k"] * res["systems"]) / max(res["systems"], 1)
@@ -704,7 +719,7 @@ def main():
                           peak_source=f"{rf['peak_kind']} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
                           bytes_per_launch=rf["bytes_per_launch"], ms_per_launch=rf["ms_per_launch"]),
             clocks=res["clocks"],
-            e2e=dict(value=res["e2e_ms"], unit=UNIT, h2d_bytes_per_step=res["h2d"], d2h_bytes_per_step=res["d2h"]),
+            e2e=dict(value=e2e_per_system, unit=UNIT, h2d_bytes_per_step=res["h2d"], d2h_bytes_per_step=res["d2h"]),
             gpu_launches=res["launches"],
             cycle_hbm=res["cycle_hbm"],
             cpu_baseline=cpu,
