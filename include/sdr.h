@@ -178,7 +178,12 @@ sdr_status sdr_solve_batch(int32_t count, sdr_handle* const* hs, const sdr_csr* 
                            double* const* xs, sdr_stats* stats);
 
 /* sdr_recycle for count handles (mode as in sdr_recycle), the SAU
- * recomputations of all handles issued before any is waited for. */
+ * recomputations of all handles issued before any is waited for.
+ *   hs: host array of count handles.  As: host array of count CSR
+ *   descriptors (read only in mode 0; may be NULL otherwise).
+ * Returns when every handle's stream is idle.  Errors: INVALID_ARG (count
+ * < 0, a NULL handle, mode outside 0..2, or in mode 0 a descriptor that
+ * fails the sdr_solve checks for a handle with a recycle space), CUDA. */
 sdr_status sdr_recycle_batch(int32_t count, sdr_handle* const* hs, const sdr_csr* As, int32_t mode);
 
 /* Prepare the recycle space for the next system in a sequence (Section 3.6).
@@ -187,16 +192,24 @@ sdr_status sdr_recycle_batch(int32_t count, sdr_handle* const* hs, const sdr_csr
  *          descriptor of device arrays).
  *   mode 1 (inexact): keep SAU as it is (A_next unused, may be NULL).
  *   mode 2: drop the recycle space.
- * A system sequence with a fixed matrix needs no call at all. */
+ * A system sequence with a fixed matrix needs no call at all.
+ * Synchronous: returns when the new SAU is in place.  Errors: INVALID_ARG
+ * (h NULL, mode outside 0..2, or in mode 0 with a non-empty recycle space an
+ * A_next that is NULL, has a NULL array, n outside 1..n_max or nnz outside
+ * 0..2^31 - 1), CUDA. */
 sdr_status sdr_recycle(sdr_handle* h, const sdr_csr* A_next, int32_t mode);
 
-/* Release all device memory of the handle.  h may be NULL. */
+/* Release all device memory of the handle and the handle itself (h must not
+ * be used afterwards).  h may be NULL. */
 sdr_status sdr_destroy(sdr_handle* h);
 
 /* ---- inspection and state transfer ---------------------------------- */
 
-/* y = S x: apply the handle's sketch to a length-n vector.
- *   x: device pointer (n entries).  y: device pointer (s entries). */
+/* y = S x: apply the handle's subspace embedding S (Section 3, Eq. (sketch)) to
+ * a length-n vector.
+ *   x: device pointer (n entries, 1 <= n <= n_max).  y: device pointer
+ *   (s entries), overwritten.
+ * Synchronous.  Errors: INVALID_ARG (NULL pointer or n out of range), CUDA. */
 sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y);
 
 /* y = S x without allocating any device memory.  S is the same hash-defined
@@ -254,21 +267,31 @@ sdr_status sdr_value_gradient(const sdr_csr* A, const double* lambda, const doub
 /* Sketched residual norms of every Arnoldi step of the last sdr_solve, in
  * order, and the per-cycle log.  sres: host pointer with room for cap_steps
  * doubles (may be NULL).  log: host pointer with room for cap_cycles entries
- * (may be NULL).  n_steps / n_cycles: host pointers receiving the counts. */
+ * (may be NULL).  n_steps / n_cycles: host pointers receiving the counts
+ * (may be NULL).  The counts are those kept, not min(count, cap).  Reads host
+ * memory only.  Errors: INVALID_ARG (h NULL). */
 sdr_status sdr_get_history(sdr_handle* h, double* sres, int32_t cap_steps, int32_t* n_steps,
                            sdr_cycle_log* log, int32_t cap_cycles, int32_t* n_cycles);
 
-/* Current number of recycle columns (0 for a fresh handle). */
+/* Current number of recycle columns (0 for a fresh handle; at most k + 1).
+ * Errors: INVALID_ARG (h or kdim NULL). */
 sdr_status sdr_recycle_dim(sdr_handle* h, int32_t* kdim);
 
 /* Copy the recycle state out: U (device, n x kdim, ld n), SU and SAU
- * (device, s x kdim each, ld s).  Any pointer may be NULL to skip it. */
+ * (device, s x kdim each, ld s).  Any pointer may be NULL to skip it; n is
+ * the length of the system the space belongs to.  Synchronous; nothing is
+ * copied when kdim = 0.  Errors: INVALID_ARG (h NULL, n outside 1..n_max),
+ * NOT_IMPLEMENTED (a float32 handle), CUDA. */
 sdr_status sdr_recycle_export(sdr_handle* h, int64_t n, double* U, double* SU, double* SAU);
 
 /* Replace the recycle state: U (device, n x kdim, ld n); SU and SAU (device,
  * s x kdim) or NULL, in which case the missing sketches are computed from U
  * with A (host pointer to a CSR descriptor; needed only when SAU is NULL).
- * kdim <= k + 1. */
+ * kdim <= k + 1; kdim = 0 empties the space.  U's columns are taken as they
+ * are (the next cycle assumes nothing of their scaling).  Synchronous.
+ * Errors: INVALID_ARG (h NULL, n outside 1..n_max, kdim out of range, U NULL
+ * with kdim > 0, or A invalid when it is needed), NOT_IMPLEMENTED (a float32
+ * handle), CUDA. */
 sdr_status sdr_recycle_import(sdr_handle* h, const sdr_csr* A, int64_t n, int32_t kdim,
                               const double* U, const double* SU, const double* SAU);
 
@@ -306,12 +329,14 @@ typedef struct {
   double total_ms;   /* summed CUDA-event time between each launch's start and end */
 } sdr_kernel_time;
 
-/* enable != 0: bracket every kernel launch with CUDA events on the handle's
- * stream and accumulate per-class times (resets the totals); 0: stop. */
+/* enable != 0: bracket every kernel launch with CUDA events on the stream it
+ * is launched on and accumulate per-class times (resets the totals); 0: stop.
+ * Events serialise nothing but add a record per launch; a profiled call is
+ * slower than an unprofiled one.  Errors: INVALID_ARG (h NULL). */
 sdr_status sdr_profile(sdr_handle* h, int32_t enable);
 
-/* Copy min(cap, SDR_K_COUNT) per-class totals into out (host pointer); *n
- * receives SDR_K_COUNT. */
+/* Copy min(cap, SDR_K_COUNT) per-class totals into out (host pointer, may be
+ * NULL); *n receives SDR_K_COUNT.  Errors: INVALID_ARG (h NULL). */
 sdr_status sdr_profile_get(sdr_handle* h, sdr_kernel_time* out, int32_t cap, int32_t* n);
 
 /* One launch of a traced call.  start_us and end_us are the CUDA events
@@ -320,7 +345,7 @@ sdr_status sdr_profile_get(sdr_handle* h, sdr_kernel_time* out, int32_t cap, int
  * includes the time the launch waited for its stream and for free SMs. */
 typedef struct {
   int32_t cls;      /* sdr_kernel_class */
-  int32_t stream;   /* 0: the handle's main stream, 1: its control stream */
+  int32_t stream;   /* 0: the handle's main stream, 1: its control stream, 2: another stream */
   double start_us;
   double end_us;
 } sdr_trace_entry;
@@ -328,11 +353,12 @@ typedef struct {
 /* cap > 0: while profiling is enabled (sdr_profile), keep a trace entry for
  * each of the next cap launches (clears the earlier trace and takes a new
  * time origin); cap = 0: stop tracing.  Entries are taken when a call
- * collects its event pairs, i.e. before the call returns. */
+ * collects its event pairs, i.e. before the call returns.
+ * Errors: INVALID_ARG (h NULL, cap < 0), CUDA (event creation). */
 sdr_status sdr_trace(sdr_handle* h, int32_t cap);
 
 /* Copy min(cap, *n) trace entries into out (host pointer); *n receives the
- * number kept. */
+ * number kept.  Errors: INVALID_ARG (h NULL, cap < 0, out NULL with cap > 0). */
 sdr_status sdr_trace_get(sdr_handle* h, sdr_trace_entry* out, int32_t cap, int32_t* n);
 
 /* Human-readable text of a status (static storage). */
