@@ -57,3 +57,46 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(S.sdr_cycle_log) == 56
     assert ctypes.sizeof(S.sdr_trace_entry) == 24
     assert len(S.KERNEL_CLASSES) == 21
+
+
+def test_every_entry_point_rejects_invalid_arguments_before_cuda():
+    """Each call rejects a NULL handle or an out-of-range size with INVALID_ARG
+    before it touches CUDA (so this runs without a GPU)."""
+    import paper_2311_14206_gb300.sdr as S
+    lib = S.load_library()
+    INV = 1
+    i32 = ctypes.c_int32()
+    dummy = ctypes.c_void_p(16)  # never dereferenced: every call below returns first
+    assert lib.sdr_recycle(None, None, 0) == INV
+    assert lib.sdr_sketch(None, dummy, 10, dummy) == INV
+    assert lib.sdr_get_history(None, None, 0, None, None, 0, None) == INV
+    assert lib.sdr_recycle_dim(None, ctypes.byref(i32)) == INV
+    assert lib.sdr_recycle_export(None, 10, None, None, None) == INV
+    assert lib.sdr_recycle_import(None, None, 10, 0, None, None, None) == INV
+    assert lib.sdr_profile(None, 1) == INV
+    assert lib.sdr_profile_get(None, None, 0, None) == INV
+    assert lib.sdr_trace(None, 4) == INV
+    assert lib.sdr_trace_get(None, None, 0, None) == INV
+    assert lib.sdr_solve_batch(-1, None, None, None, None, None) == INV
+    assert lib.sdr_solve_batch(1, None, None, None, None, None) == INV
+    assert lib.sdr_recycle_batch(-1, None, None, 0) == INV
+    assert lib.sdr_recycle_batch(1, None, None, 0) == INV
+    # sketch without allocation: sizes outside 1 <= n < 2^31, 1 <= s <= 512,
+    # 1 <= zeta <= min(s, 32), and NULL vectors
+    for n, s, z, x, y in [(0, 8, 2, dummy, dummy), (1 << 31, 8, 2, dummy, dummy), (10, 0, 1, dummy, dummy),
+                          (10, 513, 2, dummy, dummy), (10, 8, 0, dummy, dummy), (10, 8, 9, dummy, dummy),
+                          (10, 64, 33, dummy, dummy), (10, 8, 2, None, dummy), (10, 8, 2, dummy, None)]:
+        assert lib.sdr_sketch_noalloc(x, n, s, z, 1, y, None) == INV, (n, s, z)
+    # adjoint helpers
+    bad_csr = S.sdr_csr()
+    bad_csr.n = 0
+    assert lib.sdr_csr_transpose(None, dummy, dummy, dummy, dummy, None) == INV
+    assert lib.sdr_csr_transpose(ctypes.byref(bad_csr), dummy, dummy, dummy, dummy, None) == INV
+    assert lib.sdr_gather_values(None, dummy, 4, dummy, None) == INV
+    assert lib.sdr_gather_values(dummy, dummy, -1, dummy, None) == INV
+    assert lib.sdr_value_gradient(None, dummy, dummy, dummy, None) == INV
+    assert lib.sdr_value_gradient(ctypes.byref(bad_csr), dummy, dummy, dummy, None) == INV
+    # every status has its own text
+    texts = [lib.sdr_status_string(c).decode() for c in range(8)]
+    assert len(set(texts)) == 8 and "unknown status" not in texts
+    assert lib.sdr_status_string(99).decode() == "unknown status"
