@@ -14,8 +14,9 @@ design notes of the repository):
   * QZ of (M_ell, Sigma_ell) is taken through the eigenpairs of
     Sigma_ell^{-1} M_ell: the span of Z(:, 1:k) is the span of the real and
     imaginary parts of the selected eigenvectors;
-  * k largest |mu| are kept (ties: larger real part, then lower index); when the
-    k-th and (k+1)-th form a complex-conjugate pair both are kept (k+1 columns);
+  * k largest |mu| are kept (ties: larger real part, then lower index); a
+    complex-conjugate pair is kept whole, so a pair at the k-th place gives
+    k+1 columns;
   * `safety` starts from its default at every cycle;
   * an exactly zero H(j+1, j) forces the true-residual check at that j;
   * tol is absolute: tol = rel_tol * ||b||.
@@ -77,16 +78,28 @@ def numerical_rank(sig: np.ndarray, d: int) -> int:
 
 def select_largest(mu: np.ndarray, k: int) -> np.ndarray:
     """Indices of the k eigenvalues of largest modulus (ties: larger real part,
-    then lower index), extended by one when the k-th and (k+1)-th are a
-    complex-conjugate pair (Section 3.5 targets the largest-modulus mu)."""
+    then lower index; Section 3.5 targets the largest-modulus mu).  A complex
+    eigenvalue is taken together with a conjugate partner, so a pair at the
+    k-th place gives k + 1 indices (the real basis of Section 3.5 needs whole
+    pairs; this also holds when a pair is repeated exactly)."""
     idx = np.arange(mu.size)
     order = np.lexsort((idx, -mu.real, -np.abs(mu)))
     kk = min(k, mu.size)
-    if 0 < kk < mu.size:
-        a, b = mu[order[kk - 1]], mu[order[kk]]
-        if a.imag != 0.0 and b == np.conj(a):
-            kk += 1
-    return order[:kk]
+    sel, used = [], np.zeros(mu.size, dtype=bool)
+    for i in order:
+        if len(sel) >= kk:
+            break
+        if used[i]:
+            continue
+        sel.append(i)
+        used[i] = True
+        if mu[i].imag != 0.0:
+            for j in order:  # the partner: same modulus and real part, later in the order
+                if not used[j] and mu[j] == np.conj(mu[i]):
+                    sel.append(j)
+                    used[j] = True
+                    break
+    return np.array(sel, dtype=np.int64)
 
 
 def invariant_basis(mu: np.ndarray, Y: np.ndarray, sel: np.ndarray) -> np.ndarray:

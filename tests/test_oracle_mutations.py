@@ -66,6 +66,26 @@ def test_sdr_mutation_is_caught(name, old, new):
     assert pins_catch(mod, P.ALL_PINS), f"no pin caught: {name}"
 
 
+PART_MUTATIONS = [
+    ("a conjugate pair split at the k-th eigenvalue", "        if mu[i].imag != 0.0:\n            for j in order:",
+     "        if False:\n            for j in order:"),
+    ("ties broken by the smaller real part", "np.lexsort((idx, -mu.real, -np.abs(mu)))",
+     "np.lexsort((idx, mu.real, -np.abs(mu)))"),
+    ("a complex pair contributes its real part only", "            cols.append(Y[:, i].imag)\n", ""),
+    ("rank threshold from the smallest singular value", "sig > sig[0] * d * EPS", "sig > sig[-1] * d * EPS"),
+    ("back substitution skips the last unknown", "R[i, i + 1:] @ y[i + 1:]", "R[i, i + 1:-1] @ y[i + 1:-1]"),
+    ("least squares with R^T R in place of R", "y = back_substitute(R, Q.T @ Sr0)",
+     "y = back_substitute(np.triu(R.T @ R), Q.T @ Sr0)"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", PART_MUTATIONS, ids=[m[0] for m in PART_MUTATIONS])
+def test_part_mutation_is_caught(name, old, new):
+    import test_oracle_parts as T
+    mod = load_mutant(sdr, old, new)
+    assert pins_catch(mod, T.PART_PINS), f"no pin caught: {name}"
+
+
 SKETCH_MUTATIONS = [
     ("sign from bit 1", "(w & np.uint64(1)) == 0", "(w & np.uint64(2)) == 0"),
     ("Floyd range off by one", "j = s - zeta + q", "j = s - zeta + q - 1"),
