@@ -286,7 +286,7 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   ws.win_bits = ceil_log2(n_max) + 1;
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
-  ws.grid_max = (nsm > 0 ? nsm : 148) * 8;
+  ws.grid_max = (nsm > 0 ? nsm : 152) * 8;  // 152 SMs on GB300, if the query fails
   const int64_t N = n_max;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };

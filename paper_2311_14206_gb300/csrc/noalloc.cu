@@ -143,7 +143,7 @@ extern "C" sdr_status sdr_sketch_noalloc(const double* x, int64_t n, int32_t s, 
   int win_bits = 0;
   while (((int64_t)1 << win_bits) < n) ++win_bits;
   win_bits += 1;
-  int nsm = 148;
+  int nsm = 152;  // GB300, kept if the query below fails
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ntiles = (n + NA_TILE - 1) / NA_TILE;
