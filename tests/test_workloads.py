@@ -138,3 +138,26 @@ def test_random_inputs_are_seeded_and_distributed_as_stated():
     assert sides_conv == W.batch_systems() and len(sides_conv) == 64
     for side, (cx, cy) in sides_conv:
         assert 32 <= side <= 512 and 1.0 <= cx <= 50.0 and 1.0 <= cy <= 50.0
+
+
+def test_vcdiff_torch_values_match_numpy_and_differentiate():
+    """The torch assembly (differentiable in theta) stores the numpy assembly's
+    values in CSR order; its vector-Jacobian product matches central finite
+    differences of the numpy assembly."""
+    torch = pytest.importorskip("torch")
+    from workloads.vcdiff_torch import vcdiff_pattern, vcdiff_values
+    n = 9
+    theta = np.random.default_rng(11).normal(0.0, 0.5, n * n)
+    A = W.make_vcdiff(n, theta)
+    rp, col = vcdiff_pattern(n)
+    assert np.array_equal(rp, A.rowptr) and np.array_equal(col, A.col)
+    th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    vals = vcdiff_values(n, th)
+    assert np.allclose(vals.detach().numpy(), A.val, rtol=1e-15, atol=0)
+    u = np.random.default_rng(12).standard_normal(A.nnz)
+    (g,) = torch.autograd.grad((vals * torch.as_tensor(u)).sum(), th)
+    for c in (0, n + 3, n * n // 2, n * n - 1):
+        e = np.zeros(n * n)
+        e[c] = 1e-6
+        fd = (W.make_vcdiff(n, theta + e).val - W.make_vcdiff(n, theta - e).val) @ u / 2e-6
+        assert g[c].item() == pytest.approx(fd, rel=1e-6)
