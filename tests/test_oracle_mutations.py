@@ -76,6 +76,10 @@ PART_MUTATIONS = [
     ("back substitution skips the last unknown", "R[i, i + 1:] @ y[i + 1:]", "R[i, i + 1:-1] @ y[i + 1:-1]"),
     ("least squares with R^T R in place of R", "y = back_substitute(R, Q.T @ Sr0)",
      "y = back_substitute(np.triu(R.T @ R), Q.T @ Sr0)"),
+    ("a lucky breakdown does not end the cycle", "            if breakdown:\n                jf = j + 1\n                break",
+     "            pass"),
+    ("a lucky breakdown does not force the check", "if sres < tol / safety or j == m - 1 or breakdown:",
+     "if sres < tol / safety or j == m - 1:"),
 ]
 
 

@@ -11,12 +11,17 @@ invariant of the definition (CPU only).
   harmonic_ritz_update  -- exact harmonic Ritz values mu = 1/lambda when W
                            spans an invariant subspace of A, with any sketch
                            (Section 3.5)
+  cycle                 -- a lucky breakdown (H(j+1, j) = 0) ends the cycle
+                           with the exact solution; finite termination after
+                           as many steps as the degree of the minimal
+                           polynomial (Algorithm 1)
 """
 import numpy as np
 import pytest
 import scipy.linalg
 
 import oracle.sdr as ORACLE
+import workloads as W
 from oracle.sketch import SparseSign
 
 
@@ -152,6 +157,45 @@ def pin_harmonic_ritz_exact_on_an_invariant_subspace(O, with_sketch=False):
     assert cosines.min() > 1 - 1e-8
 
 
+def diag_csr(d):
+    n = d.size
+    return W.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.asarray(d, dtype=np.float64))
+
+
+def pin_lucky_breakdown_stops_the_cycle(O):
+    """A = 2 I, b = e_3: A v_1 = 2 v_1 exactly, so H(2, 1) = 0 at the first step.
+    The forced check finds x = b / 2.  With tol = 0 no sres can trigger a check,
+    so only the breakdown rule ends the cycle after one column."""
+    n = 16
+    A = diag_csr(np.full(n, 2.0))
+    b = np.zeros(n)
+    b[3] = 1.0
+    S = SparseSign(5, n, 12, 3)
+    c = O.cycle(A, b, None, None, None, S, 1e-12, 8, 2, 2)
+    assert c.converged and c.j == 1 and len(c.sres) == 1
+    assert np.allclose(c.x_tilde, b / 2, rtol=0, atol=1e-15)
+    c0 = O.cycle(A, b, None, None, None, S, 0.0, 8, 2, 2)
+    assert not c0.converged and c0.j == 1 and len(c0.sres) == 1 and len(c0.checks) == 1
+
+
+def pin_finite_termination(O):
+    """A diagonal A with three distinct eigenvalues: the minimal polynomial of A
+    with respect to a generic b has degree 3, so GMRES with full orthogonalisation
+    over those steps (t = 3) reaches A^-1 b at the third step and not before."""
+    g = rng(9)
+    n = 30
+    d = g.choice([2.0, 5.0, -3.0], n)
+    d[:3] = [2.0, 5.0, -3.0]
+    A = diag_csr(d)
+    b = g.standard_normal(n)
+    S = SparseSign(6, n, 20, 4)
+    tol = 1e-10 * np.linalg.norm(b)
+    c = O.cycle(A, b, None, None, None, S, tol, 10, 3, 2)
+    assert c.converged and c.j == 3
+    assert min(c.sres[:2]) > 1e-3 * np.linalg.norm(b)
+    assert np.allclose(c.x_tilde, b / d, rtol=1e-9, atol=0)
+
+
 def pin_harmonic_ritz_exact_with_a_sketch(O):
     pin_harmonic_ritz_exact_on_an_invariant_subspace(O, with_sketch=True)
 
@@ -159,7 +203,8 @@ def pin_harmonic_ritz_exact_with_a_sketch(O):
 PART_PINS = [pin_back_substitute_matches_library_triangular_solve, pin_sketched_ls_matches_library_least_squares,
              pin_numerical_rank_known_spectra_and_matrices, pin_select_largest_invariants,
              pin_select_largest_real_distinct_matches_sort, pin_invariant_basis_spans_an_invariant_subspace,
-             pin_harmonic_ritz_exact_on_an_invariant_subspace, pin_harmonic_ritz_exact_with_a_sketch]
+             pin_harmonic_ritz_exact_on_an_invariant_subspace, pin_harmonic_ritz_exact_with_a_sketch,
+             pin_lucky_breakdown_stops_the_cycle, pin_finite_termination]
 
 
 @pytest.mark.parametrize("pin", PART_PINS, ids=[f.__name__[4:] for f in PART_PINS])
