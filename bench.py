@@ -579,7 +579,11 @@ def run_form_batch(args):
 
 
 # --------------------------------------------------------------------------- oracle arm
-ORACLE_SAMPLE_STEPS = 12
+# Arnoldi steps of the bounded oracle sample: about 10-15 s of one host core on the GPU machine.
+# The oracle's cost per step grows with the steps of its cycle (its basis is an N x (m+1)
+# row-major array, so every column access strides over more memory), so a longer sample is
+# also closer to the workload's m = 100 than a short one.
+ORACLE_SAMPLE_STEPS = 32
 
 
 def oracle_sample(steps=ORACLE_SAMPLE_STEPS, system=1):
@@ -645,10 +649,10 @@ def run_reference(args, rank, world):
         return None
     per = []
     for _ in range(args.warmup):
-        run_oracle_subprocess(4)
+        run_oracle_subprocess(4)  # warm-up: imports and caches only
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r = run_oracle_subprocess(4)
+        r = run_oracle_subprocess(ORACLE_SAMPLE_STEPS)
         per.append(r["per_step"])
     wall = time.perf_counter() - t0
     value = statistics.mean(per) * STEP_EQUIV_PER_SYSTEM * 1e3
@@ -658,9 +662,9 @@ def run_reference(args, rank, world):
                 config=dict(workload=WORKLOAD["workload"], N=2097152, m=100, k=20, t=2, s=480, zeta=8,
                             systems=20, rel_tol=1e-8),
                 cpu_baseline=dict(kind="oracle", cores=1, value=value, unit=UNIT,
-                                  sample=("each step: FP64 numpy oracle (1 thread) on 4 Arnoldi steps + one check "
-                                          f"of system 1, scaled by {STEP_EQUIV_PER_SYSTEM} step-equivalents per "
-                                          f"system; {wall:.0f} s for the timed steps")),
+                                  sample=(f"each step: FP64 numpy oracle (1 thread) on {ORACLE_SAMPLE_STEPS} Arnoldi "
+                                          f"steps + one check of system 1, scaled by {STEP_EQUIV_PER_SYSTEM} "
+                                          f"step-equivalents per system; {wall:.0f} s for the timed steps")),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     return line
 
