@@ -57,10 +57,11 @@ def abs_sketch(S, v):
 
 
 def assert_true_residual(A, b, x, tol_rel):
-    """||b - A x|| <= tol ||b|| + the rounding of the host's own product
-    (at most 8 eps (|A| |x|) per row for rows of at most 7 entries)."""
+    """||b - A x|| <= tol ||b|| + the rounding of the two residual products (the
+    GPU's, which decided convergence, and the host's: each at most 8 eps
+    (|A| |x|) per row for rows of at most 7 entries)."""
     r = b - osdr.csr_matvec(A, x)
-    slack = 8 * EPS * np.linalg.norm(osdr.csr_matvec(abs_csr(A), np.abs(x)))
+    slack = 16 * EPS * np.linalg.norm(osdr.csr_matvec(abs_csr(A), np.abs(x)))
     assert np.linalg.norm(r) <= tol_rel * np.linalg.norm(b) + slack
 
 
