@@ -11,5 +11,13 @@ Modules:
   sdr      -- one cycle of Algorithm 1, the restart driver and the sequence
               driver of Section 3.6 (exact and inexact recycling)
   adjoint  -- gradients of L = ||x(theta) - x_t||^2 through A(theta) x = b
+
+Parity unpinned (no closed form to pin them to; the GPU is compared with the
+oracle by span only, through principal angles):
+  * the harmonic-Ritz selection when |mu_k| and |mu_{k+1}| nearly tie, where
+    rounding decides which of the two is kept;
+  * the recycle basis U itself, which depends on the choice of basis of the
+    selected invariant subspace, while everything downstream depends only on
+    its span.
 """
 from . import adjoint, sketch, sdr  # noqa: F401

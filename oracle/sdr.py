@@ -20,6 +20,9 @@ design notes of the repository):
   * `safety` starts from its default at every cycle;
   * an exactly zero H(j+1, j) forces the true-residual check at that j;
   * tol is absolute: tol = rel_tol * ||b||.
+
+Parity unpinned: the selection when |mu_k| and |mu_{k+1}| nearly tie, and the
+basis of U (only its span is determined); see the package docstring.
 """
 from dataclasses import dataclass, field
 
