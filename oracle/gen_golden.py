@@ -1,5 +1,8 @@
 """Write the stored expected values under tests/golden/ from the oracle alone.
 
+TEST INFRASTRUCTURE ONLY (see the package docstring): never imported by the
+product path.
+
 Usage: python -m oracle.gen_golden
 """
 import json

@@ -1,5 +1,8 @@
 """GMRES-SDR in plain FP64, step by step as the paper states it.
 
+TEST INFRASTRUCTURE ONLY (see the package docstring): never imported by the
+product path.
+
 Algorithm 1 (one cycle), Section 3.4 (residual control with `safety`),
 Section 3.5 (sketched harmonic Ritz extraction with a truncated SVD and an
 ordered QZ), Section 3.6 (sequences: fixed A with varying b, and the exact and

@@ -1,5 +1,8 @@
 """Sparse-sign subspace embedding S, defined by a counter-based hash.
 
+TEST INFRASTRUCTURE ONLY (see the package docstring): never imported by the
+product path.
+
 Section 3 (eq. (sketch)) asks for an s x N operator S that is an
 epsilon-subspace embedding; the paper's experiments used a subsampled DCT.
 This build uses a sparse-sign embedding: column c of S has exactly zeta
