@@ -2,17 +2,19 @@
 counts its table prints (tests/golden/cd_paper_section_6_3.json).
 
 Three 2D convection-diffusion systems (n = 500, N = 250,000, convection
-alpha = 0, 5, 20, b = ones), solved in sequence with m = 80 of which k = 20
-recycled (60 Arnoldi steps per cycle, the experiments' meaning of m), t = 2,
-at most 10 restarts per system.  Readings: the target residual 1e-2 is taken
-relative to ||b||; the sketch is the sparse-sign one (the paper's is a
-subsampled DCT) with s = 8 m_max = 640 as Section 6 states.  Pinned:
-  * the exact variant (S A^(i+1) U recomputed) converges on all three
-    problems, with a matrix-vector count inside a loose band around the
-    paper's 1,971 (another sketch changes the counts);
+alpha = 0, 5, 20, b = ones), solved in sequence with m = 80 Arnoldi steps per
+cycle and k = 20 recycled columns (Algorithm 1's meaning of m), t = 2, at most
+10 restarts per system.  Readings: the target residual 1e-2 is taken relative
+to ||b||; the sketch is the sparse-sign one (the paper's is a subsampled DCT)
+with s = 8 m_max = 640 as Section 6 states.  Pinned:
   * the inexact variant (S A^(i) U kept) converges on the first two problems
     and fails on the third, where its true residual grows past ||b|| although
-    the sketched residuals keep falling.
+    the sketched residuals keep falling; its total count of matrix-vector
+    products is the printed 1,886 within 3 % (the third problem runs into the
+    restart cap, so the total is fixed mainly by the first two);
+  * the exact variant (S A^(i+1) U recomputed) converges on all three
+    problems, with a count inside a loose band around the printed 1,971 (it
+    comes out about 20 % lower, with either sketch family).
 About three and a half minutes on one core."""
 import json
 import os
@@ -35,7 +37,7 @@ def test_section_6_3_exact_and_inexact_recycling():
     As = [W.make_cd_paper(n, a) for a in fx["alpha"]]
     b = np.ones(N)
     k = fx["k_augmentation"]
-    m = fx["m_krylov_dimension"] - k
+    m = fx["m_krylov_dimension"]
     S = SparseSign(231114206, N, 8 * fx["m_krylov_dimension"], 8)
     kw = dict(m=m, k=k, t=2, rel_tol=fx["target_residual"], max_cycles=10)
 
@@ -61,6 +63,9 @@ def test_section_6_3_exact_and_inexact_recycling():
     fails = fx["inexact_fails_on_problem"] - 1
     assert [r.converged for r in inexact] == [i != fails for i in range(3)]
     assert inexact[fails].res > np.linalg.norm(b)
+    mv = sum(r.matvecs for r in inexact)
+    paper = fx["table"]["gmres_sdr_inexact"]["matvecs"]
+    assert 0.97 * paper <= mv <= 1.03 * paper, mv
     # within each cycle of the failing solve the sketched residual does not increase
     for cyc in inexact[fails].sres_per_cycle:
         assert all(b_ <= a_ * (1 + 1e-12) for a_, b_ in zip(cyc, cyc[1:]))
