@@ -93,6 +93,35 @@ class SparseSign:
         return D
 
 
+class SubsampledDCT:
+    """The sketch of the paper's experiments (Section 6, opening paragraph):
+    S = sqrt(N / s) P F E with E a diagonal of random signs, F the orthonormal
+    DCT (type II; scipy's transform serves as the library step) and P the
+    selection of s distinct rows drawn uniformly at random.  E ||S x||^2 =
+    ||x||^2.  Not part of the GPU path (whose sketch is the sparse sign above):
+    it lets the oracle run the paper's experiments with the paper's operator.
+    The random signs and rows come from numpy's PCG64 seeded [seed, n, s]."""
+
+    def __init__(self, seed: int, n: int, s: int):
+        g = np.random.default_rng([seed, n, s])
+        self.seed, self.n, self.s = seed, n, s
+        self.signs = g.choice(np.array([-1.0, 1.0]), n)
+        self.rows = np.sort(g.choice(n, s, replace=False))
+        self.scale = np.sqrt(n / s)
+
+    def apply(self, x: np.ndarray) -> np.ndarray:
+        import scipy.fft
+        return self.scale * scipy.fft.dct(self.signs * x, type=2, norm="ortho")[self.rows]
+
+    def apply_cols(self, X: np.ndarray) -> np.ndarray:
+        return np.stack([self.apply(X[:, i]) for i in range(X.shape[1])], axis=1) \
+            if X.shape[1] else np.zeros((self.s, 0))
+
+    def dense(self) -> np.ndarray:
+        """The s x N matrix (small n only; for tests)."""
+        return self.apply_cols(np.eye(self.n))
+
+
 class Identity:
     """S = I (s = N): reduces GMRES-SDR to unsketched augmented GMRES."""
 

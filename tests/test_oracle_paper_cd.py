@@ -5,8 +5,8 @@ Three 2D convection-diffusion systems (n = 500, N = 250,000, convection
 alpha = 0, 5, 20, b = ones), solved in sequence with m = 80 Arnoldi steps per
 cycle and k = 20 recycled columns (Algorithm 1's meaning of m), t = 2, at most
 10 restarts per system.  Readings: the target residual 1e-2 is taken relative
-to ||b||; the sketch is the sparse-sign one (the paper's is a subsampled DCT)
-with s = 8 m_max = 640 as Section 6 states.  Pinned:
+to ||b||.  The sketch is the paper's own, a subsampled randomised DCT with
+s = 8 m_max = 640 (Section 6).  Pinned:
   * the inexact variant (S A^(i) U kept) converges on the first two problems
     and fails on the third, where its true residual grows past ||b|| although
     the sketched residuals keep falling; its total count of matrix-vector
@@ -14,7 +14,7 @@ with s = 8 m_max = 640 as Section 6 states.  Pinned:
     restart cap, so the total is fixed mainly by the first two);
   * the exact variant (S A^(i+1) U recomputed) converges on all three
     problems, with a count inside a loose band around the printed 1,971 (it
-    comes out about 20 % lower, with either sketch family).
+    comes out about 20 % lower, with this sketch and with the sparse sign).
 About three and a half minutes on one core."""
 import json
 import os
@@ -24,7 +24,7 @@ import pytest
 
 import workloads as W
 from oracle import sdr as osdr
-from oracle.sketch import SparseSign
+from oracle.sketch import SubsampledDCT
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -38,7 +38,7 @@ def test_section_6_3_exact_and_inexact_recycling():
     b = np.ones(N)
     k = fx["k_augmentation"]
     m = fx["m_krylov_dimension"]
-    S = SparseSign(231114206, N, 8 * fx["m_krylov_dimension"], 8)
+    S = SubsampledDCT(231114206, N, 8 * fx["m_krylov_dimension"])
     kw = dict(m=m, k=k, t=2, rel_tol=fx["target_residual"], max_cycles=10)
 
     try:  # numpy's BLAS threads only spin on these memory-bound vector operations

@@ -93,6 +93,31 @@ def test_subspace_embedding_distortion():
     assert sv.min() > 0.55 and sv.max() < 1.45
 
 
+def test_subsampled_dct_definition_and_embedding():
+    """S = sqrt(N/s) P F E (Section 6): against the DCT-II written out as its
+    cosine sum, E ||S x||^2 = ||x||^2 over the draws, and the distortion band of
+    the sparse sign above."""
+    from oracle.sketch import SubsampledDCT
+    n, s = 64, 16
+    S = SubsampledDCT(7, n, s)
+    k = np.arange(n)[:, None]
+    j = np.arange(n)[None, :]
+    C = np.sqrt(2.0 / n) * np.cos(np.pi * (2 * j + 1) * k / (2 * n))
+    C[0, :] /= np.sqrt(2.0)  # orthonormal DCT-II
+    ref = np.sqrt(n / s) * C[S.rows] * S.signs[None, :]
+    assert np.allclose(S.dense(), ref, rtol=0, atol=1e-13)
+    assert len(set(S.rows.tolist())) == s and S.rows.min() >= 0 and S.rows.max() < n
+    x = np.random.default_rng(2).standard_normal(n)
+    mean_sq = np.mean([np.sum(SubsampledDCT(sd, n, s).apply(x) ** 2) for sd in range(400)])
+    assert mean_sq == pytest.approx(np.sum(x ** 2), rel=0.05)
+    N, d, s2 = 4096, 60, 120
+    Q, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((N, d)))
+    lo, hi = 1 - np.sqrt(d / s2), 1 + np.sqrt(d / s2)
+    for sd in range(10):
+        sv = np.linalg.svd(SubsampledDCT(sd, N, s2).apply_cols(Q), compute_uv=False)
+        assert sv.min() > 0.9 * lo and sv.max() < 1.1 * hi
+
+
 def test_golden_table_matches():
     with open(GOLDEN) as f:
         g = json.load(f)
