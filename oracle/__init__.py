@@ -7,7 +7,9 @@ with the CUDA path (the two sides only share the seeded input generators in
 ``workloads``); each function cites the part of the paper it follows.
 
 Modules:
-  sketch   -- the hash-defined sparse-sign embedding S (Section 3, eq. (sketch))
+  sketch   -- the hash-defined sparse-sign embedding S (Section 3, eq. (sketch)),
+              and the subsampled randomised DCT of the paper's experiments
+              (Section 6), which the GPU path does not use
   sdr      -- one cycle of Algorithm 1, the restart driver and the sequence
               driver of Section 3.6 (exact and inexact recycling)
   adjoint  -- gradients of L = ||x(theta) - x_t||^2 through A(theta) x = b
