@@ -53,9 +53,9 @@ UNIT = "ms/system"
 # one cycle per system in the parity tests); overwritten by the GPU arm's own count
 # whenever it runs in the same process.
 STEP_EQUIV_PER_SYSTEM = 400
-# DRAM bytes (read + write) per row of one k_spmv_dots launch, from the ncu capture in
-# profiles/spmv_dots_cd3d_96.md (107.0 MB per launch at 884,736 rows); set to None when the
-# kernel changes until it is captured again.
+# DRAM bytes (read + write) per row of one k_spmv_dots launch, from an ncu capture of that
+# kernel at 96^3 (dram__bytes_read.sum + dram__bytes_write.sum, 110.6 MB per launch at
+# 884,736 rows); set to None when the kernel changes until it is captured again.
 SPMV_DRAM_BYTES_PER_ROW = (106.546e6 + 4.053e6) / 884736
 
 
@@ -618,7 +618,8 @@ def run_oracle_subprocess(steps=ORACLE_SAMPLE_STEPS):
 def cpu_baseline(step_equiv):
     r = run_oracle_subprocess()
     per_system_ms = r["per_step"] * step_equiv * 1e3
-    return dict(value=per_system_ms, unit=UNIT, cores=1, kind="oracle",
+    return dict(value=per_system_ms, unit=UNIT, cores=1, kind="oracle", extrapolated=True,
+                sampled_step_equivalents=r["info"]["steps"] + 1, step_equivalents_per_system=step_equiv,
                 sample=(f"FP64 numpy oracle, 1 thread: first {r['info']['steps']} Arnoldi steps of system 1 "
                         f"(N=2,097,152) plus one true-residual check took {r['info']['seconds']:.1f} s; "
                         f"scaled by {step_equiv:.0f} step-equivalents per system"))
@@ -661,7 +662,9 @@ def run_reference(args, rank, world):
                 data="synthetic", impl="reference",
                 config=dict(workload=WORKLOAD["workload"], N=2097152, m=100, k=20, t=2, s=480, zeta=8,
                             systems=20, rel_tol=1e-8),
-                cpu_baseline=dict(kind="oracle", cores=1, value=value, unit=UNIT,
+                cpu_baseline=dict(kind="oracle", cores=1, value=value, unit=UNIT, extrapolated=True,
+                                  sampled_step_equivalents=ORACLE_SAMPLE_STEPS + 1,
+                                  step_equivalents_per_system=STEP_EQUIV_PER_SYSTEM,
                                   sample=(f"each step: FP64 numpy oracle (1 thread) on {ORACLE_SAMPLE_STEPS} Arnoldi "
                                           f"steps + one check of system 1, scaled by {STEP_EQUIV_PER_SYSTEM} "
                                           f"step-equivalents per system; {wall:.0f} s for the timed steps")),

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define SDR_ABI_VERSION 2
+#define SDR_ABI_VERSION 3
 
 typedef struct sdr_handle sdr_handle; /* opaque */
 
@@ -47,7 +47,8 @@ typedef enum {
   SDR_ERR_OOM = 3,           /* device allocation failed in sdr_create */
   SDR_ERR_NOT_CONVERGED = 4, /* max_cycles reached; x holds the last iterate */
   SDR_ERR_BREAKDOWN = 5,     /* H(j+1,j) = 0 or a non-finite value with res >= tol */
-  SDR_ERR_RANK = 6,          /* the sketched least-squares matrix lost full rank */
+  SDR_ERR_RANK = 6,          /* sdr_recycle / sdr_recycle_import: the installed SAU is
+                                numerically rank-deficient; the space was dropped */
   SDR_ERR_NOT_IMPLEMENTED = 7
 } sdr_status;
 
@@ -78,6 +79,17 @@ typedef enum {
  *              cycles of each refinement step; at most 40 steps).
  *   inner_rel_tol  refined form: relative tolerance of each inner solve
  *              (0 selects 1e-4).
+ *   stale_check  0: off.  1: for a handle whose SAU may be stale (the inexact
+ *              variant of Section 3.6, sdr_recycle mode 1): when a restart
+ *              cycle of sdr_solve ends unconverged with its last true
+ *              residual res > 4 * sres (its sketched residual), SAU of the
+ *              new recycle space is recomputed as S A U (k products with A)
+ *              before the next cycle.  With an exact SAU the true residual
+ *              lies in the embedded subspace, so res <= sres / (1 - eps) <=
+ *              4 sres for any embedding with eps <= 3/4 (Section 3, Eq.
+ *              (sketch)); a larger ratio can only come from a stale SAU.
+ *              Counted in sdr_stats.sau_refreshes.  Ignored by
+ *              sdr_solve_batch and by SDR_PREC_F32_REFINED handles.
  *   test_flags bit 0: take the truncated-SVD path of the harmonic-Ritz step
  *              even when the full-rank certificate holds (for tests);
  *              bit 1: launch every kernel directly instead of replaying each
@@ -98,7 +110,8 @@ typedef struct {
   int32_t precision;
   int32_t test_flags;
   double inner_rel_tol;
-  int32_t reserved[4]; /* must be zero */
+  int32_t stale_check;
+  int32_t reserved[3]; /* must be zero */
 } sdr_params;
 
 /* Square CSR matrix; all pointers are device pointers owned by the caller. */
@@ -123,6 +136,8 @@ typedef struct {
   int32_t full_svd_cycles; /* cycles that needed the truncated-SVD path */
   int32_t kernel_launches; /* kernels of this library launched by the call */
   int32_t refinements;     /* SDR_PREC_F32_REFINED: float64 refinement steps (0 otherwise) */
+  int32_t sau_refreshes;   /* stale_check: SAU recomputations the rule triggered */
+  int32_t pad0;
   double final_res;        /* last true residual norm */
   double tol;              /* rel_tol * ||b|| */
   double final_rel_res;    /* final_res / ||b|| */
@@ -144,10 +159,17 @@ typedef struct {
   double safety;       /* safety factor after the cycle */
 } sdr_cycle_log;
 
-/* Create a handle.  p: host pointer to parameters.  n_max: largest n any
- * later call uses.  stream: a cudaStream_t (NULL = legacy default stream).
- * out: host pointer receiving the handle.  Allocates all device workspace
- * on the current device and builds the sketch's per-tile index tables.
+/* Create a handle: fix Algorithm 1's inputs (m, t, k, safety) and the
+ * subspace embedding S of Section 3 (Eq. (sketch); here the sparse-sign
+ * operator defined by s, zeta and seed, drawn once so that SU and SAU stay
+ * valid across a sequence, Section 3.6), and allocate the cycle's storage:
+ * the basis V (n_max x (m+1)), SV, SAV (s x m), the recycle triple U, SU,
+ * SAU (Section 3.5) and the QR factors of SAW.
+ *   p: host pointer to parameters.  n_max: largest n any later call uses.
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ *   out: host pointer receiving the handle.
+ * Allocates all device workspace on the current device and builds the
+ * sketch's per-tile index tables.  Synchronous.
  * Errors: INVALID_ARG (parameter out of range), OOM, CUDA. */
 sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_handle** out);
 
@@ -158,7 +180,9 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
  *   b: device pointer, n entries.   x: device pointer, n entries, in: x0,
  *   out: solution.   stats: host pointer or NULL.
  * On return U, SU, SAU describe the recycle space for the next system.
- * Returns OK, NOT_CONVERGED (x holds the last iterate), BREAKDOWN, RANK,
+ * Returns OK, NOT_CONVERGED (x holds the last iterate), BREAKDOWN (a cycle
+ * ended with H(j+1, j) = 0 and res >= tol, or a non-finite value appeared;
+ * a NaN or an Inf in A, b or x0 is caught before any cycle, x unchanged),
  * INVALID_ARG or CUDA. */
 sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x, sdr_stats* stats);
 
@@ -196,7 +220,9 @@ sdr_status sdr_recycle_batch(int32_t count, sdr_handle* const* hs, const sdr_csr
  * Synchronous: returns when the new SAU is in place.  Errors: INVALID_ARG
  * (h NULL, mode outside 0..2, or in mode 0 with a non-empty recycle space an
  * A_next that is NULL, has a NULL array, n outside 1..n_max or nnz outside
- * 0..2^31 - 1), CUDA. */
+ * 0..2^31 - 1), RANK (mode 0: the recomputed SAU is numerically
+ * rank-deficient, |R_pp| <= s eps max_q ||SAU(:, q)|| in its QR; the recycle
+ * space is dropped and the handle stays usable), CUDA. */
 sdr_status sdr_recycle(sdr_handle* h, const sdr_csr* A_next, int32_t mode);
 
 /* Release all device memory of the handle and the handle itself (h must not
@@ -225,10 +251,15 @@ sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y);
  *   zeta: nonzeros per column, 1 <= zeta <= min(s, 32).
  *   stream: a cudaStream_t (NULL = legacy default stream).  The call enqueues
  *   its kernels on it and returns; y is ready when the stream gets there.
+ * Non-finite input: if x holds a NaN or an Inf, every y[i] is set to NaN
+ * (the call still returns SDR_OK; the caller tests y).  x == 0 gives y == 0.
  * Scratch: one file-scope device array of 8,256 bytes, which every GPU that
  * loads this library keeps until the process exits.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  Every call
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture.  The kept address is not refreshed after
+ * cudaDeviceReset: do not call this entry point again on a device that was
+ * reset.  Every call
  * shares the array and clears it before use, so calls whose work overlaps on
  * the GPU (other streams, or other host threads, before an earlier call's
  * kernels have finished) race and corrupt each other's results.
@@ -290,8 +321,10 @@ sdr_status sdr_recycle_export(sdr_handle* h, int64_t n, double* U, double* SU, d
  * kdim <= k + 1; kdim = 0 empties the space.  U's columns are taken as they
  * are (the next cycle assumes nothing of their scaling).  Synchronous.
  * Errors: INVALID_ARG (h NULL, n outside 1..n_max, kdim out of range, U NULL
- * with kdim > 0, or A invalid when it is needed), NOT_IMPLEMENTED (a float32
- * handle), CUDA. */
+ * with kdim > 0, or A invalid when it is needed), RANK (SAU, given or
+ * computed, is numerically rank-deficient as in sdr_recycle: Algorithm 1's
+ * least squares needs SAW = [SAU, SAV] of full column rank; the space is
+ * dropped), NOT_IMPLEMENTED (a float32 handle), CUDA. */
 sdr_status sdr_recycle_import(sdr_handle* h, const sdr_csr* A, int64_t n, int32_t kdim,
                               const double* U, const double* SU, const double* SAU);
 

@@ -75,6 +75,24 @@ def sketched_ls(SAW: np.ndarray, Sr0: np.ndarray):
     return y, sres
 
 
+def sau_rank_deficient(SAU: np.ndarray) -> bool:
+    """Whether a sketched recycle block SAU (s x kd) is numerically
+    rank-deficient for Algorithm 1's least squares, which needs R^{-1} from the
+    QR of SAW = [SAU, SAV].  Reading (the paper is silent): deficient when some
+    diagonal entry of R in SAU = QR has |R_pp| <= s * eps * max_q ||SAU(:, q)||,
+    or a value is not finite."""
+    if SAU.shape[1] == 0:
+        return False
+    if not np.all(np.isfinite(SAU)):
+        return True
+    s = SAU.shape[0]
+    maxn = float(np.max(np.linalg.norm(SAU, axis=0)))
+    if maxn == 0.0:
+        return True
+    R = np.linalg.qr(SAU, mode="r")
+    return bool(np.any(np.abs(np.diag(R)) <= s * EPS * maxn))
+
+
 def numerical_rank(sig: np.ndarray, d: int) -> int:
     """ell = #{sigma_i > sigma_1 * d * eps} (truncated economic SVD, Section 3.5)."""
     if sig.size == 0 or sig[0] == 0.0:
@@ -259,12 +277,24 @@ class Solve:
     SAU: np.ndarray
     matvecs: int
     cycle_log: list = field(default_factory=list)
+    sau_refreshes: int = 0
+
+
+STALE_RATIO = 4.0  # res > STALE_RATIO * sres at a cycle's last check marks SAU stale
 
 
 def solve(A, b, S, m, k, t, rel_tol, safety0=1.4, max_cycles=200, U=None, SU=None, SAU=None,
-          x0=None, persist_safety=False, record=False, cycle_hook=None) -> Solve:
+          x0=None, persist_safety=False, record=False, cycle_hook=None, stale_check=False) -> Solve:
     """Restarted GMRES-SDR for A x = b: repeat Algorithm 1 on the current
-    residual, x <- x + x_tilde, r0 <- r0 - A x_tilde, until res < tol."""
+    residual, x <- x + x_tilde, r0 <- r0 - A x_tilde, until res < tol.
+
+    stale_check (failure detection for the inexact variant of Section 3.6):
+    with an exact SAU = S A U the true residual r lies in the subspace the
+    sketch embeds, so ||r|| <= ||S r|| / (1 - eps) (Section 3, Eq. (sketch)),
+    i.e. res <= 4 sres for any eps <= 3/4.  When a cycle ends unconverged with
+    res > 4 sres at its last check, SAU can only be stale: SAU of the new
+    recycle space is then recomputed as S A U (k products) before the next
+    cycle."""
     N = A.n
     x = np.zeros(N) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     tol = rel_tol * float(np.linalg.norm(b))
@@ -274,6 +304,7 @@ def solve(A, b, S, m, k, t, rel_tol, safety0=1.4, max_cycles=200, U=None, SU=Non
     sres_all, checks_all, log = [], [], []
     safety = safety0
     cycles = 0
+    refreshes = 0
     converged = res < tol
     while not converged and cycles < max_cycles:
         if cycle_hook is not None:
@@ -291,7 +322,12 @@ def solve(A, b, S, m, k, t, rel_tol, safety0=1.4, max_cycles=200, U=None, SU=Non
             log.append(c)
         safety = c.safety if persist_safety else safety0
         converged = c.converged
-    return Solve(x, converged, cycles, res, tol, sres_all, checks_all, U, SU, SAU, matvecs, log)
+        if (stale_check and not converged and cycles < max_cycles and U.shape[1] and c.checks
+                and c.checks[-1][2] > STALE_RATIO * c.checks[-1][1]):
+            SAU = S.apply_cols(csr_matmat(A, U))
+            matvecs += U.shape[1]
+            refreshes += 1
+    return Solve(x, converged, cycles, res, tol, sres_all, checks_all, U, SU, SAU, matvecs, log, refreshes)
 
 
 def solve_sequence(As, bs, S, m, k, t, rel_tol, exact=True, fixed_matrix=False, **kw):

@@ -59,6 +59,8 @@ struct sdr_handle {
   double* d_tmp = nullptr;  // n_max scratch vector (A u)
   Prof prof;
   int launches = 0;  // kernels launched by the current call
+  int sau_refreshes = 0;   // stale_check: SAU recomputations in the current sdr_solve
+  int extra_matvecs = 0;   // products with A outside the cycles' own count (those recomputations)
   int prec = SDR_PREC_F64;   // storage type of the tall arrays: double, or float (refined form)
   void* rhs32 = nullptr;     // refined form: float32 right-hand side of the inner solve
   void* dx32 = nullptr;      // refined form: float32 inner solution
@@ -211,6 +213,7 @@ struct StreamGuard {
 
 template <typename T>
 static sdr_status issue_sau(sdr_handle* h, const sdr_csr* A, int64_t n);
+static sdr_status verify_sau_rank(sdr_handle* h);
 
 extern "C" {
 
@@ -264,6 +267,8 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   if (p->precision != SDR_PREC_F64 && p->precision != SDR_PREC_F32_REFINED) return SDR_ERR_INVALID_ARG;
   if (!(p->inner_rel_tol >= 0.0 && p->inner_rel_tol < 1.0)) return SDR_ERR_INVALID_ARG;
   if (n_max >= ((int64_t)1 << 31)) return SDR_ERR_INVALID_ARG;
+  if (p->stale_check != 0 && p->stale_check != 1) return SDR_ERR_INVALID_ARG;
+  if (p->reserved[0] || p->reserved[1] || p->reserved[2]) return SDR_ERR_INVALID_ARG;
   sdr_handle* h = new sdr_handle();
   h->p = *p;
   if (!(h->p.inner_rel_tol > 0.0)) h->p.inner_rel_tol = 1e-4;
@@ -543,7 +548,13 @@ sdr_status run_complete_init(CycleRun<T>& r) {
   SDR_CK(cudaStreamSynchronize(r.h->st));
   r.hc = *r.h->hc;
   r.converged = r.hc.converged != 0;
-  r.active = !r.converged && r.cycles < r.max_cycles;
+  // a NaN or an Inf in b, x0 or A shows in ||b||, ||A||_inf or ||b - A x0||:
+  // no cycle is issued and the solve ends with SDR_ERR_BREAKDOWN, x unchanged
+  if (!std::isfinite(r.hc.bnorm) || !std::isfinite(r.hc.anorm_inf) || !std::isfinite(r.hc.res)) {
+    r.converged = false;
+    r.status = SDR_ERR_BREAKDOWN;
+  }
+  r.active = !r.converged && r.status == SDR_OK && r.cycles < r.max_cycles;
   return SDR_OK;
 }
 
@@ -646,6 +657,8 @@ struct SolveCtx {
 sdr_status solve_begin_f64(sdr_handle* h, const sdr_csr* A, const double* b, double* x, SolveCtx& c) {
   cudaStream_t st = h->st;
   h->launches = 0;
+  h->sau_refreshes = 0;
+  h->extra_matvecs = 0;
   // anything a failed earlier call left on the control stream comes first
   SDR_CK(cudaEventRecord(h->evJoin, h->st2));
   SDR_CK(cudaStreamWaitEvent(st, h->evJoin, 0));
@@ -693,6 +706,8 @@ sdr_status solve_end(sdr_handle* h, const CycleRun<double>* run_f64, const Ctl& 
     stats->full_svd_cycles = full_svd;
     stats->kernel_launches = h->launches;
     stats->refinements = refinements;
+    stats->sau_refreshes = h->sau_refreshes;
+    stats->matvecs += h->extra_matvecs;
     stats->final_res = final_res;
     stats->tol = tol;
     stats->bnorm = bnorm;
@@ -719,6 +734,8 @@ extern "C" {
 sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x, sdr_stats* stats) {
   if (!h || !csr_ok(h, A) || !b || !x) return SDR_ERR_INVALID_ARG;
   StreamGuard guard(h);
+  h->sau_refreshes = 0;
+  h->extra_matvecs = 0;
   if (h->prec == SDR_PREC_F64) {
     SolveCtx c;
     sdr_status s = solve_begin_f64(h, A, b, x, c);
@@ -726,6 +743,17 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
     while (s == SDR_OK && c.run.active) {
       s = run_issue<double>(c.run);
       if (s == SDR_OK) s = run_complete<double>(c.run);
+      // stale_check: a cycle whose last true residual exceeds 4 sres had a stale
+      // SAU; recompute it for the new recycle space before the next cycle
+      const Ctl& hc = c.run.hc;
+      if (s == SDR_OK && c.run.active && h->p.stale_check && h->kh > 0 && hc.res > 4.0 * hc.sres) {
+        const sdr_csr cur{c.Ad.n, c.Ad.nnz, c.Ad.rowptr, c.Ad.col, c.Ad.val, c.Ad.val32};
+        const int l0 = h->launches;
+        s = issue_sau<double>(h, &cur, c.Ad.n);
+        h->launches += l0;
+        ++h->sau_refreshes;
+        h->extra_matvecs += h->kh;
+      }
     }
     if (s != SDR_OK) return s;
     return solve_finish_f64(h, c, stats);
@@ -863,11 +891,17 @@ sdr_status sdr_recycle_batch(int32_t count, sdr_handle* const* hs, const sdr_csr
       return SDR_ERR_INVALID_ARG;
     }
   }
+  sdr_status worst = SDR_OK;
   for (int i = 0; i < count; ++i) {
     SDR_CK(cudaStreamSynchronize(hs[i]->st));
     SDR_CK(prof_collect(hs[i]));
+    if (mode == 0) {
+      const sdr_status s = verify_sau_rank(hs[i]);
+      if (s == SDR_ERR_CUDA) return s;
+      if (s != SDR_OK && worst == SDR_OK) worst = s;
+    }
   }
-  return SDR_OK;
+  return worst;
 }
 
 }  // extern "C"
@@ -924,6 +958,23 @@ static sdr_status recompute_su(sdr_handle* h, int64_t n) {
   return SDR_OK;
 }
 
+// After a recycle space is installed (exact recompute or import): test SAU's
+// numerical column rank.  A rank-deficient SAU leaves R^{-1} of Algorithm 1's
+// least squares undefined, so the space is dropped and SDR_ERR_RANK returned.
+static sdr_status verify_sau_rank(sdr_handle* h) {
+  if (h->kh == 0) return SDR_OK;
+  int* flag = ctl_int_field(h->ws.ctl, offsetof(Ctl, rank_sau));
+  SDR_CK(launch_sau_rank(h->ws.SAU[h->cu], h->ws.s, h->kh, flag, h->st));
+  int hflag = 0;
+  SDR_CK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  SDR_CK(cudaStreamSynchronize(h->st));
+  if (hflag) {
+    h->kh = 0;
+    return SDR_ERR_RANK;
+  }
+  return SDR_OK;
+}
+
 extern "C" {
 
 sdr_status sdr_recycle(sdr_handle* h, const sdr_csr* A_next, int32_t mode) {
@@ -937,8 +988,9 @@ sdr_status sdr_recycle(sdr_handle* h, const sdr_csr* A_next, int32_t mode) {
   if (mode != 0) return SDR_ERR_INVALID_ARG;
   if (h->kh == 0) return SDR_OK;
   if (!csr_ok(h, A_next)) return SDR_ERR_INVALID_ARG;
-  return h->prec == SDR_PREC_F64 ? recompute_sau<double>(h, A_next, A_next->n)
-                                 : recompute_sau<float>(h, A_next, A_next->n);
+  const sdr_status s = h->prec == SDR_PREC_F64 ? recompute_sau<double>(h, A_next, A_next->n)
+                                               : recompute_sau<float>(h, A_next, A_next->n);
+  return s != SDR_OK ? s : verify_sau_rank(h);
 }
 
 sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y) {
@@ -1065,8 +1117,11 @@ sdr_status sdr_recycle_import(sdr_handle* h, const sdr_csr* A, int64_t n, int32_
     sdr_status s = recompute_su<double>(h, n);
     if (s != SDR_OK) return s;
   }
-  if (!SAU) return recompute_sau<double>(h, A, n);
-  return SDR_OK;
+  if (!SAU) {
+    const sdr_status s = recompute_sau<double>(h, A, n);
+    if (s != SDR_OK) return s;
+  }
+  return verify_sau_rank(h);
 }
 
 }  // extern "C"

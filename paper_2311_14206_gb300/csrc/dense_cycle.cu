@@ -826,8 +826,11 @@ __global__ void __launch_bounds__(512, 1) k_ce_eig(WS ws) {
   Ctl* c = ws.ctl;
   if (c->jf <= 0) return;
   const int n = c->ell;
-  if (n <= 0) return;
   CeLayout L = ce_layout(ws.dscr);
+  if (n <= 0) {  // SAW of numerical rank 0 (e.g. a breakdown on the first column): no candidates
+    if (threadIdx.x == 0) L.cnt[0] = 0;
+    return;
+  }
   extern __shared__ float shf[];
   const int ldh = n + 1;
   float* H = shf;                 // n x n, ld n+1
@@ -1209,7 +1212,7 @@ __global__ void k_ce_select(WS ws) {
   __shared__ int ord[KC];
   __shared__ int zc_of[KC];
   __shared__ int nsel;
-  const int nc = L.cnt[0];
+  const int nc = n > 0 ? L.cnt[0] : 0;  // rank 0: nothing to select, no recycle columns
   if (threadIdx.x == 0) {
     for (int i = 0; i < nc; ++i) ord[i] = i;
     for (int i = 1; i < nc; ++i) {

@@ -409,4 +409,72 @@ cudaError_t launch_step_dense(const WS& ws, int j, int kh, int ubuf, unsigned lo
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Numerical rank of the sketched recycle block SAU (s x kd), for the calls that
+// install a recycle space (sdr_recycle, sdr_recycle_import).  Algorithm 1
+// solves its least squares problem through R^{-1} of the QR of SAW =
+// [SAU, SAV], which needs SAU of full column rank.  Gram-Schmidt with one
+// re-orthogonalisation pass gives the diagonal |R_pp| of that QR; the block
+// counts as rank-deficient when some |R_pp| <= s * eps * max_q ||SAU(:, q)||
+// (or a value is not finite).  One CTA; Q (s x kd) in dynamic shared memory.
+// ---------------------------------------------------------------------------
+constexpr int RK_T = 512;
+__global__ void __launch_bounds__(RK_T) k_sau_rank(const double* __restrict__ SAU, int s, int kd, int* flag) {
+  extern __shared__ double rk_dyn[];
+  double* Q = rk_dyn;                  // s x kd, column-major
+  double* c = Q + (size_t)s * kd;      // the column being reduced
+  __shared__ double dots[K_MAX];
+  __shared__ double red[RK_T / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double maxn = 0.0;
+  bool bad = false;
+  for (int q = 0; q < kd; ++q) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) {
+      const double v = SAU[i + (int64_t)q * s];
+      a = fma(v, v, a);
+    }
+    a = block_sum(a, red);
+    if (!isfinite(a)) bad = true;
+    maxn = fmax(maxn, sqrt(a));
+  }
+  const double thresh = (double)s * 2.220446049250313e-16 * maxn;
+  for (int p = 0; p < kd && !bad; ++p) {
+    for (int i = threadIdx.x; i < s; i += blockDim.x) c[i] = SAU[i + (int64_t)p * s];
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int q = wid; q < p; q += nw) {  // dots[q] = Q(:, q) . c, one warp per column
+        double d = 0.0;
+        for (int i = lane; i < s; i += 32) d = fma(Q[i + (size_t)q * s], c[i], d);
+        d = warp_sum(d);
+        if (lane == 0) dots[q] = d;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < s; i += blockDim.x) {
+        double v = c[i];
+        for (int q = 0; q < p; ++q) v = fma(-dots[q], Q[i + (size_t)q * s], v);
+        c[i] = v;
+      }
+      __syncthreads();
+    }
+    double rr = 0.0;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) rr = fma(c[i], c[i], rr);
+    const double rpp = sqrt(block_sum(rr, red));
+    if (!(rpp > thresh)) bad = true;  // uniform: every thread holds the same rpp
+    const double inv = rpp > 0.0 ? 1.0 / rpp : 0.0;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) Q[i + (size_t)p * s] = c[i] * inv;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *flag = (bad || !(maxn > 0.0)) ? 1 : 0;
+}
+
+cudaError_t launch_sau_rank(const double* SAU, int s, int kd, int* flag, cudaStream_t st) {
+  const size_t smem = ((size_t)s * kd + s) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_sau_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_sau_rank<<<1, RK_T, smem, st>>>(SAU, s, kd, flag);
+  return cudaGetLastError();
+}
+
 }  // namespace sdr

@@ -69,6 +69,9 @@ cudaError_t launch_cycle_head(const WS& ws, int kh, unsigned long long* accR, in
 cudaError_t launch_cycle_qr(const WS& ws, const double* SAU, int kh, cudaStream_t st);
 // Arnoldi step j, small dense part: h(j+1,j), SV(:,j+1), SAV(:,j), QR update, sres, control.
 cudaError_t launch_step_dense(const WS& ws, int j, int kh, int ubuf, unsigned long long* accR, cudaStream_t st);
+// *flag = 1 when the sketched recycle block SAU (s x kd, kd <= K_MAX) is
+// numerically rank-deficient (|R_pp| <= s eps max ||SAU(:, q)||), else 0.
+cudaError_t launch_sau_rank(const double* SAU, int s, int kd, int* flag, cudaStream_t st);
 // max |U(:, l)| of kdim columns into ctl->umax[ubuf] (after an import).
 template <typename T>
 cudaError_t launch_umax(const WS& ws, const T* U, int kdim, int ubuf, cudaStream_t st);

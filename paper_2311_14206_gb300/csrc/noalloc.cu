@@ -55,7 +55,10 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_sketch(const double* __restri
   __shared__ unsigned long long acc_s[S_MAX];
   __shared__ unsigned long long red[32];
   const double mx = __longlong_as_double((long long)sc[SC_MAX]);
-  if (!(mx > 0.0)) return;  // x == 0: the cleared accumulators already hold S x
+  // x == 0: the cleared accumulators already hold S x.  A NaN or an Inf in x
+  // (max |x| with exponent field 0x7FF) has no fixed-point window: nothing is
+  // accumulated and k_na_finish writes NaN to every y[i].
+  if (!(mx > 0.0) || bexp_of_bits(sc[SC_MAX]) == 0x7FF) return;
   const int top = window_top(mx, win_bits);
   unsigned long long lo[NA_RPT], hi[NA_RPT];
 #pragma unroll
@@ -104,12 +107,19 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_sketch(const double* __restri
 
 __global__ void k_na_finish(const unsigned long long* sc, int s, int win_bits, double scale, double* __restrict__ y) {
   const double mx = __longlong_as_double((long long)sc[SC_MAX]);
+  if (bexp_of_bits(sc[SC_MAX]) == 0x7FF) {  // x holds a NaN or an Inf: S x is not finite
+    for (int i = threadIdx.x; i < s; i += blockDim.x) y[i] = __longlong_as_double(0x7FF8000000000000ll);
+    return;
+  }
   const int top = window_top(mx > 0.0 ? mx : 1.0, win_bits);
   for (int i = threadIdx.x; i < s; i += blockDim.x)
     y[i] = mx > 0.0 ? int128_to_double(sc[2 * i], sc[2 * i + 1], top - 126) * scale : 0.0;
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device (by the first
+// call on that device, with it current) and kept for the life of the process.
+// The cache is not refreshed after cudaDeviceReset: a caller that resets a
+// device must not call this entry point again on it.
 std::mutex g_mu;
 unsigned long long* g_addr[128] = {};
 

@@ -54,6 +54,7 @@ struct Ctl {
   double gram[M_MAX + 2][T_MAX];          // v_hat_c . v_hat_{c-1-d}, d = 0..t-2
   double coef[T_MAX + 1];                 // a_0 (w) and a_1.. (window) for the update
   double hnext_sq;                        // ||v_hat_{j+1}||^2 (reduced in the dense step)
+  int rank_sau;                           // the last installed SAU is numerically rank-deficient
 };
 
 // The Arnoldi kernels of step j run while the dense step and the true-residual

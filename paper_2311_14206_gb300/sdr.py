@@ -26,7 +26,7 @@ class sdr_params(ctypes.Structure):
                 ("zeta", ctypes.c_int32), ("seed", ctypes.c_uint64), ("rel_tol", ctypes.c_double),
                 ("safety0", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("persist_safety", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("test_flags", ctypes.c_int32), ("inner_rel_tol", ctypes.c_double),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("stale_check", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 SDR_PREC_F64 = 0
@@ -42,7 +42,8 @@ class sdr_stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int32), ("converged", ctypes.c_int32), ("matvecs", ctypes.c_int32),
                 ("sketches", ctypes.c_int32), ("true_res_evals", ctypes.c_int32), ("arnoldi_steps", ctypes.c_int32),
                 ("recycle_dim", ctypes.c_int32), ("full_svd_cycles", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int32), ("refinements", ctypes.c_int32), ("final_res", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int32), ("refinements", ctypes.c_int32),
+                ("sau_refreshes", ctypes.c_int32), ("pad0", ctypes.c_int32), ("final_res", ctypes.c_double),
                 ("tol", ctypes.c_double), ("final_rel_res", ctypes.c_double), ("bnorm", ctypes.c_double)]
 
     def as_dict(self):
@@ -167,11 +168,13 @@ class CSRDevice:
 
 
 def make_params(m, k, t, s, zeta, seed, rel_tol, safety0=1.4, max_cycles=200, persist_safety=0,
-                force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0, graphs=True) -> sdr_params:
+                force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0, graphs=True,
+                stale_check=False) -> sdr_params:
     p = sdr_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety)
     p.precision = precision
     p.test_flags = (1 if force_svd else 0) | (0 if graphs else 2)
     p.inner_rel_tol = inner_rel_tol
+    p.stale_check = 1 if stale_check else 0
     return p
 
 
@@ -239,11 +242,20 @@ def sdr_sketch(h, x: torch.Tensor, s: int) -> torch.Tensor:
 
 def sdr_sketch_noalloc(x: torch.Tensor, s: int, zeta: int, seed: int, y: torch.Tensor = None) -> torch.Tensor:
     """y = S x through the allocation-free entry point (y preallocated by the
-    caller, or here by torch when y is None)."""
+    caller, or here by torch when y is None).  x and y must be contiguous
+    float64 CUDA tensors on one device, y with at least s entries: the C call
+    takes raw pointers and would read or write past a smaller array."""
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+        raise SdrError(1, "sdr_sketch_noalloc: x must be a contiguous float64 CUDA tensor")
     if y is None:
         y = torch.empty(s, dtype=torch.float64, device=x.device)
-    _check(load_library().sdr_sketch_noalloc(_ptr(x), x.numel(), s, zeta, seed, _ptr(y), _stream()),
-           "sdr_sketch_noalloc")
+    if not y.is_cuda or y.dtype != torch.float64 or not y.is_contiguous() or y.device != x.device:
+        raise SdrError(1, "sdr_sketch_noalloc: y must be a contiguous float64 CUDA tensor on x's device")
+    if y.numel() < s:
+        raise SdrError(1, f"sdr_sketch_noalloc: y has {y.numel()} entries, fewer than s = {s}")
+    with torch.cuda.device(x.device):
+        _check(load_library().sdr_sketch_noalloc(_ptr(x), x.numel(), s, zeta, seed, _ptr(y), _stream()),
+               "sdr_sketch_noalloc")
     return y
 
 
@@ -317,9 +329,9 @@ class Solver:
 
     def __init__(self, n_max, m, k, t, s, zeta=8, seed=231114206, rel_tol=1e-8, safety0=1.4, max_cycles=200,
                  persist_safety=0, force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0, graphs=True,
-                 stream=None):
+                 stream=None, stale_check=False):
         self.params = make_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety, force_svd,
-                                  precision, inner_rel_tol, graphs)
+                                  precision, inner_rel_tol, graphs, stale_check)
         self.n_max, self.s = n_max, s
         self.stream = stream  # a torch.cuda.Stream the handle issues on (None: the current stream)
         self.h = sdr_create(self.params, n_max,

@@ -28,7 +28,7 @@ def test_library_exports_every_declared_symbol():
     lib = ctypes.CDLL(_build.LIB)
     missing = [f for f in declared_functions() if not hasattr(lib, f)]
     assert not missing, missing
-    assert lib.sdr_abi_version() == 2
+    assert lib.sdr_abi_version() == 3
 
 
 def test_host_side_validation_without_gpu():
@@ -53,7 +53,7 @@ def test_struct_layouts_match_the_header():
     import paper_2311_14206_gb300.sdr as S
     assert ctypes.sizeof(S.sdr_params) == 88
     assert ctypes.sizeof(S.sdr_csr) == 48
-    assert ctypes.sizeof(S.sdr_stats) == 72
+    assert ctypes.sizeof(S.sdr_stats) == 80
     assert ctypes.sizeof(S.sdr_cycle_log) == 56
     assert ctypes.sizeof(S.sdr_trace_entry) == 24
     assert len(S.KERNEL_CLASSES) == 21
