@@ -96,7 +96,10 @@ typedef enum {
  *              restart cycle from a captured CUDA graph.  With graphs (the
  *              default) sdr_solve first copies A, b and x into buffers the
  *              handle owns, so that one graph per cycle state serves every
- *              later solve of the same size.
+ *              later solve of the same size;
+ *              bit 2: compute the recycle product U_new = [U V] P of a float64
+ *              handle on the 32-bit integer pipe instead of the tensor cores
+ *              (both are exact: the results are bit-identical).
  */
 #define SDR_PREC_F64 0
 #define SDR_PREC_F32_REFINED 1

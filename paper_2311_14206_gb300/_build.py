@@ -11,7 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsdr.so")
-SOURCES = ["sketch.cu", "arnoldi.cu", "dense_step.cu", "dense_cycle.cu", "api.cu", "noalloc.cu", "adjoint.cu"]
+SOURCES = ["sketch.cu", "arnoldi.cu", "dense_step.cu", "dense_cycle.cu", "api.cu", "noalloc.cu", "adjoint.cu",
+           "recycle_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=default"]
 

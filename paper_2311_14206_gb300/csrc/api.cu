@@ -278,7 +278,11 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   cudaGetDevice(&h->device);
   WS& ws = h->ws;
   ws.n = n_max;
-  ws.ldv = n_max;
+  // tall arrays: columns start on 256-byte boundaries, and a column holds at
+  // least one entry past an odd n (the tensor-core recycle product copies
+  // column segments of an even number of rows)
+  ws.ldv = (n_max + 32) & ~(int64_t)31;
+  ws.recycle_int = (p->test_flags & 4) ? 1 : 0;
   ws.m = p->m;
   ws.k = p->k;
   ws.t = p->t;
@@ -292,7 +296,7 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
   ws.grid_max = (nsm > 0 ? nsm : 152) * 8;  // 152 SMs on GB300, if the query fails
-  const int64_t N = n_max;
+  const int64_t N = ws.ldv;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
   // tall arrays in the storage type (8 or 4 bytes per element)
@@ -320,7 +324,7 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   chk(cudaMallocHost((void**)&h->hc, sizeof(Ctl)));
   h->use_graphs = (p->test_flags & 2) == 0;
   const int tileR = sketch_tile_rows(p->zeta);
-  const int64_t ntiles = (N + tileR - 1) / tileR;
+  const int64_t ntiles = (n_max + tileR - 1) / tileR;
   ws.ntiles = (int)ntiles;
   chk(halloc(h, &h->sk_ent, (size_t)ntiles * tileR * p->zeta));
   chk(halloc(h, &h->sk_ptr, (size_t)ntiles * PTR_STRIDE));
@@ -398,7 +402,7 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
     init.force_svd = (p->test_flags & 1) ? 1 : 0;
     chk(cudaMemcpyAsync(ws.ctl, &init, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
   }
-  chk(launch_sketch_build(ws, N, h->sk_ent, h->sk_ptr, h->st));
+  chk(launch_sketch_build(ws, n_max, h->sk_ent, h->sk_ptr, h->st));
   chk(cudaStreamSynchronize(h->st));
   if (e != cudaSuccess) {
     sdr_status st = cuda_status(e);
@@ -586,6 +590,7 @@ sdr_status run_complete(CycleRun<T>& r) {
   }
   r.converged = hc.converged != 0;
   if (!r.converged && (hc.bd_dense || !std::isfinite(hc.res))) r.status = SDR_ERR_BREAKDOWN;
+  if (hc.tc_error) r.status = SDR_ERR_CUDA;  // a bounded wait of the recycle product ran out
   r.active = !r.converged && r.status == SDR_OK && r.cycles < r.max_cycles;
   return SDR_OK;
 }

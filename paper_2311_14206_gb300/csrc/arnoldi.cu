@@ -1036,6 +1036,9 @@ template <typename T>
 cudaError_t launch_recycle_gemm(const WS& ws, const T* U, const T* const* vcol, T* Unew, int kh,
                                 int ucur, int unext, cudaStream_t st) {
   Cols<T> V{vcol[0], (const T*)ws.Vs};
+  if (sizeof(T) == sizeof(double) && !ws.recycle_int)
+    return launch_recycle_tc(ws, (const double*)U, (const double*)vcol[0], (const double*)ws.Vs, (double*)Unew, kh,
+                             ucur, unext, st);
   const int nsm = ws.grid_max / 8;
   const int dcap = kh + ws.m;  // W has kh + jf <= kh + m columns; kprime <= k + 1 = kmax
   const int grid = 2 * nsm;

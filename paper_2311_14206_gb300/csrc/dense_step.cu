@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(DT) k_cycle_head(WS ws, int kh, unsigned long 
     c->breakdown = 0;
     c->bd_dense = 0;
     c->rankfail = 0;
+    c->tc_error = 0;
     c->kprime = 0;
     c->ell = 0;
     c->svd_path = 0;

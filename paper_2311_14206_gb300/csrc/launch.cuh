@@ -51,6 +51,10 @@ cudaError_t launch_check_gemv(const WS& ws, const T* U, const T* const* vcol, co
 template <typename T>
 cudaError_t launch_recycle_gemm(const WS& ws, const T* U, const T* const* vcol, T* Unew,
                                 int kh, int ucur, int unext, cudaStream_t st);
+// U_new = [U V(:,0:jf)] P' on the tcgen05 tensor cores (float64 only; exact,
+// bit-identical to the integer-pipe product).  v0 = V(:, 0), vs = V(:, 1..).
+cudaError_t launch_recycle_tc(const WS& ws, const double* U, const double* v0, const double* vs, double* Unew,
+                              int kh, int ucur, int unext, cudaStream_t st);
 // y = A x (plain SpMV, used for A U in the exact recycling variant).
 template <typename T>
 cudaError_t launch_spmv(CsrDev A, const T* x, T* y, cudaStream_t st);

@@ -55,6 +55,7 @@ struct Ctl {
   double coef[T_MAX + 1];                 // a_0 (w) and a_1.. (window) for the update
   double hnext_sq;                        // ||v_hat_{j+1}||^2 (reduced in the dense step)
   int rank_sau;                           // the last installed SAU is numerically rank-deficient
+  int tc_error;                           // a bounded wait of the tensor-core recycle kernel ran out
 };
 
 // The Arnoldi kernels of step j run while the dense step and the true-residual
@@ -82,8 +83,9 @@ struct CycleLog {
 // Device workspace: pointers and sizes, passed by value to kernels.
 struct WS {
   int64_t n;        // current system size
-  int64_t ldv;      // leading dimension of tall arrays (n_max)
+  int64_t ldv;      // leading dimension of tall arrays (n_max rounded up to a multiple of 32)
   int m, k, t, s, zeta, kmax, dmax;
+  int recycle_int;  // 1: the recycle product on the integer pipe instead of the tensor cores
   uint64_t seed;
   double inv_sqrt_zeta;
   int win_bits;     // log2 bound on terms per sketch row (window headroom)

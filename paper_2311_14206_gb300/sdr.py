@@ -169,10 +169,10 @@ class CSRDevice:
 
 def make_params(m, k, t, s, zeta, seed, rel_tol, safety0=1.4, max_cycles=200, persist_safety=0,
                 force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0, graphs=True,
-                stale_check=False) -> sdr_params:
+                stale_check=False, integer_recycle=False) -> sdr_params:
     p = sdr_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety)
     p.precision = precision
-    p.test_flags = (1 if force_svd else 0) | (0 if graphs else 2)
+    p.test_flags = (1 if force_svd else 0) | (0 if graphs else 2) | (4 if integer_recycle else 0)
     p.inner_rel_tol = inner_rel_tol
     p.stale_check = 1 if stale_check else 0
     return p
@@ -186,15 +186,17 @@ def sdr_create(params: sdr_params, n_max: int, stream=None) -> ctypes.c_void_p:
     return h
 
 
-def sdr_solve(h, A: CSRDevice, b: torch.Tensor, x: torch.Tensor, allow_not_converged=True):
-    """Solve in place into x; returns (status, stats dict)."""
+def sdr_solve(h, A: CSRDevice, b: torch.Tensor, x: torch.Tensor, allow_not_converged=True, allow=()):
+    """Solve in place into x; returns (status, stats dict).  Statuses other than
+    OK (and NOT_CONVERGED when allow_not_converged) raise SdrError, unless
+    listed in `allow` (for instance SDR_ERR_BREAKDOWN = 5)."""
     lib = load_library()
     if b.dtype != torch.float64 or x.dtype != torch.float64 or not (b.is_cuda and x.is_cuda):
         raise TypeError("b and x must be float64 CUDA tensors")
     csr = A.c_struct()
     stats = sdr_stats()
     st = lib.sdr_solve(h, ctypes.byref(csr), _ptr(b), _ptr(x), ctypes.byref(stats))
-    _check(st, "sdr_solve", ok=(0, 4) if allow_not_converged else (0,))
+    _check(st, "sdr_solve", ok=((0, 4) if allow_not_converged else (0,)) + tuple(allow))
     return st, stats.as_dict()
 
 
@@ -329,9 +331,9 @@ class Solver:
 
     def __init__(self, n_max, m, k, t, s, zeta=8, seed=231114206, rel_tol=1e-8, safety0=1.4, max_cycles=200,
                  persist_safety=0, force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0, graphs=True,
-                 stream=None, stale_check=False):
+                 stream=None, stale_check=False, integer_recycle=False):
         self.params = make_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety, force_svd,
-                                  precision, inner_rel_tol, graphs, stale_check)
+                                  precision, inner_rel_tol, graphs, stale_check, integer_recycle)
         self.n_max, self.s = n_max, s
         self.stream = stream  # a torch.cuda.Stream the handle issues on (None: the current stream)
         self.h = sdr_create(self.params, n_max,

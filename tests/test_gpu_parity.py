@@ -332,3 +332,32 @@ def test_trace_entries(P):
     assert P.sdr_trace_get(solver.h) == []
     P.sdr_profile(solver.h, False)
     solver.close()
+
+
+# ------------------------------------------------- recycle product on tensor cores
+@pytest.mark.parametrize("side,m,k,s,tol,maxc", [(17, 40, 10, 120, 1e-10, 200), (20, 128, 31, 200, 1e-15, 3),
+                                                 (24, 60, 20, 200, 1e-10, 200)])
+def test_recycle_product_tensor_cores_bit_identical(P, side, m, k, s, tol, maxc):
+    """The recycle product U_new = [U V] P on the tcgen05 tensor cores (exact
+    integer digit products) equals the integer-pipe product bit for bit, so the
+    whole solve is bit-identical; sizes cover a ragged last tile (17^3 rows,
+    odd), the widest SAW (d = kh + m = 32 + 128 = 160 columns: three full
+    cycles of 128 steps toward an unreachable tolerance) and several cycles of
+    recycling.  The solve also matches the oracle."""
+    A = W.make_cd3d(side, (20.0, 10.0, 5.0))
+    b = W.rhs(A.n, 11)
+    out = []
+    for integer in (False, True):
+        solver = P.Solver(A.n, m, k, 2, s, 8, SEED, tol, max_cycles=maxc, integer_recycle=integer)
+        x, st, stats = solver.solve(P.CSRDevice.from_numpy(A), dev(b))
+        sres, log = solver.history()
+        U, SU, SAU = P.sdr_recycle_export(solver.h, A.n, s)
+        out.append((x.cpu().numpy(), st, stats, np.array(sres), U.cpu().numpy()))
+        solver.close()
+    (x0, st0, s0, h0, U0), (x1, st1, s1, h1, U1) = out
+    assert st0 == st1 and s0["cycles"] >= 2 and s0["cycles"] == s1["cycles"]
+    assert np.array_equal(U0, U1)
+    assert np.array_equal(x0, x1) and np.array_equal(h0, h1)
+    ref = osdr.solve(A, b, SparseSign(SEED, A.n, s, 8), m=m, k=k, t=2, rel_tol=tol, max_cycles=maxc)
+    assert np.linalg.norm(x0 - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+    assert abs(s0["cycles"] - ref.cycles) <= 1
