@@ -90,6 +90,16 @@ typedef enum {
  *              (sketch)); a larger ratio can only come from a stale SAU.
  *              Counted in sdr_stats.sau_refreshes.  Ignored by
  *              sdr_solve_batch and by SDR_PREC_F32_REFINED handles.
+ *   sketch_kind  0: the sparse-sign embedding (s rows, zeta nonzeros +-1/sqrt(zeta)
+ *              per column, rows and signs from a counter-based hash of seed).
+ *              1: the subsampled randomised DCT of the paper's experiments
+ *              (Section 6): S = sqrt(n/s) P F E, E a diagonal of random signs,
+ *              F the orthonormal DCT-II, P a selection of s distinct
+ *              frequencies.  Its draws (E and P) are inputs, set by
+ *              sdr_set_sketch_draws for one system size n before any solve
+ *              (zeta and seed are then unused).  Applied by direct summation
+ *              with a cosine table: s n multiply-adds per sketch in FP64,
+ *              against the sparse sign's zeta n additions; n_max < 2^29.
  *   test_flags bit 0: take the truncated-SVD path of the harmonic-Ritz step
  *              even when the full-rank certificate holds (for tests);
  *              bit 1: launch every kernel directly instead of replaying each
@@ -114,7 +124,8 @@ typedef struct {
   int32_t test_flags;
   double inner_rel_tol;
   int32_t stale_check;
-  int32_t reserved[3]; /* must be zero */
+  int32_t sketch_kind;
+  int32_t reserved[2]; /* must be zero */
 } sdr_params;
 
 /* Square CSR matrix; all pointers are device pointers owned by the caller. */
@@ -236,8 +247,9 @@ sdr_status sdr_destroy(sdr_handle* h);
 
 /* y = S x: apply the handle's subspace embedding S (Section 3, Eq. (sketch)) to
  * a length-n vector.
- *   x: device pointer (n entries, 1 <= n <= n_max).  y: device pointer
- *   (s entries), overwritten.
+ *   x: device pointer (n entries, 1 <= n <= n_max; for a DCT handle n must be
+ *   the size its draws were set for).  y: device pointer (s entries),
+ *   overwritten.
  * Synchronous.  Errors: INVALID_ARG (NULL pointer or n out of range), CUDA. */
 sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y);
 
@@ -306,6 +318,31 @@ sdr_status sdr_value_gradient(const sdr_csr* A, const double* lambda, const doub
  * memory only.  Errors: INVALID_ARG (h NULL). */
 sdr_status sdr_get_history(sdr_handle* h, double* sres, int32_t cap_steps, int32_t* n_steps,
                            sdr_cycle_log* log, int32_t cap_cycles, int32_t* n_cycles);
+
+/* Set the random draws of a DCT sketch (sketch_kind 1): the subsampled
+ * randomised DCT S = sqrt(n/s) P F E of Section 6 for systems of size n.
+ *   n: system size (1 <= n <= n_max); every later call must use this n.
+ *   signs: host pointer, n entries, each +1 or -1 (the diagonal E).
+ *   rows: host pointer, s entries, strictly increasing in [0, n) (the
+ *   frequencies P selects).
+ * Copies the draws to the device, builds the cosine table, drops the recycle
+ * space (sketched with another operator) and returns when done.
+ * Errors: INVALID_ARG (not a DCT handle, n out of range, a sign other than
+ * +-1, rows not strictly increasing in [0, n)), CUDA. */
+sdr_status sdr_set_sketch_draws(sdr_handle* h, int64_t n, const int8_t* signs, const int32_t* rows);
+
+/* Givens sines and cosines of every Arnoldi step of the last sdr_solve, in
+ * the order of sdr_get_history (Section 4.5, Theorem on Givens sines and
+ * sketched GMRES angles; Section 5, the augmented cycle through the whitened
+ * basis).  Step j's rotation has |s_j| = sin of the angle between S r_{j-1}
+ * and S A [U V_j], so that ||S r_j|| = |s_j| ||S r_{j-1}||, and
+ * |c_j| = sqrt(1 - s_j^2); both are read off the QR of SAW that each step
+ * updates (no extra work on the device).  The Corollary that follows the
+ * Theorem turns them into a progressive bound on the true residual.
+ *   sines, cosines: host pointers with room for cap doubles (either may be
+ *   NULL).  n_steps: host pointer receiving the number of steps (may be NULL).
+ * Reads host memory only.  Errors: INVALID_ARG (h NULL, cap < 0). */
+sdr_status sdr_get_givens(sdr_handle* h, double* sines, double* cosines, int32_t cap, int32_t* n_steps);
 
 /* Current number of recycle columns (0 for a fresh handle; at most k + 1).
  * Errors: INVALID_ARG (h or kdim NULL). */

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring): never imported by the
 product path.
 
-Usage: python -m oracle.gen_golden [sketch | batch]
+Usage: python -m oracle.gen_golden [sketch | batch | paper_cd | paper_cd_dct]
 """
 import json
 import os
@@ -87,9 +87,59 @@ def write_batch_large():
         json.dump(doc, f, indent=1)
 
 
+# The paper's Section 6.3 sequence (three convection-diffusion problems,
+# n = 500, alpha = 0, 5, 20, b = ones, 80 Arnoldi steps + 20 recycled columns,
+# t = 2, at most 10 restarts, target 1e-2 relative to ||b||) with the sparse-sign
+# sketch at s = 480, the largest sketch the library's handles take: exact
+# recycling, the inexact variant, and the inexact variant with the stale-SAU
+# rule.
+PAPER_CD = dict(n=500, alpha=[0.0, 5.0, 20.0], m=80, k=20, t=2, s=480, zeta=8, rel_tol=1e-2, max_cycles=10,
+                seed=231114206)
+
+
+def write_paper_cd(dct=False):
+    """dct: the paper's own sketch (a subsampled randomised DCT, Section 6) at
+    s = 480 instead of the sparse sign (exact and inexact variants)."""
+    import workloads as W
+    from . import sdr as O
+    from .sketch import SubsampledDCT
+    p = PAPER_CD
+    As = [W.make_cd_paper(p["n"], a) for a in p["alpha"]]
+    N = As[0].n
+    b = np.ones(N)
+    S = SubsampledDCT(p["seed"], N, p["s"]) if dct else SparseSign(p["seed"], N, p["s"], p["zeta"])
+    kw = dict(m=p["m"], k=p["k"], t=p["t"], rel_tol=p["rel_tol"], max_cycles=p["max_cycles"])
+    doc = dict(description="Oracle runs of the paper's Section 6.3 sequence with the %s sketch at s = 480; "
+                           "written by oracle.gen_golden." % ("subsampled DCT" if dct else "sparse-sign"),
+               params=p, variants={})
+    variants = (("exact", True, False), ("inexact", False, False)) if dct else \
+        (("exact", True, False), ("inexact", False, False), ("inexact_stale_check", False, True))
+    for name, exact, stale in variants:
+        t0 = time.time()
+        out = O.solve_sequence(As, [b] * 3, S, exact=exact, stale_check=stale, **kw)
+        runs = []
+        for i, r in enumerate(out):
+            steps = sum(len(c) for c in r.sres_per_cycle)
+            checks = sum(len(c) for c in r.checks)
+            runs.append(dict(converged=bool(r.converged), cycles=int(r.cycles), arnoldi_steps=int(steps),
+                             checks=int(checks), matvecs=int(r.matvecs), sau_refreshes=int(r.sau_refreshes),
+                             rel_res=float(r.res / np.linalg.norm(b)),
+                             first_cycle_sres=[float(v) for v in r.sres_per_cycle[0]]))
+        doc["variants"][name] = dict(problems=runs, total_matvecs=int(sum(r_["matvecs"] for r_ in runs)),
+                                     oracle_seconds=time.time() - t0)
+        print(name, [(r_["converged"], r_["cycles"], r_["matvecs"]) for r_ in runs], flush=True)
+    name = "paper_cd_dct_s480.json" if dct else "paper_cd_sparse_sign_s480.json"
+    with open(os.path.join(GOLDEN, name), "w") as f:
+        json.dump(doc, f, indent=1)
+
+
 if __name__ == "__main__":
     what = sys.argv[1:] or ["sketch"]
     if "sketch" in what:
         write_sketch_table()
     if "batch" in what:
         write_batch_large()
+    if "paper_cd" in what:
+        write_paper_cd()
+    if "paper_cd_dct" in what:
+        write_paper_cd(dct=True)

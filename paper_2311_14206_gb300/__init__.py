@@ -16,6 +16,8 @@ from .sdr import (  # noqa: F401
     sdr_create,
     sdr_destroy,
     sdr_get_history,
+    sdr_get_givens,
+    sdr_set_sketch_draws,
     sdr_profile,
     sdr_profile_get,
     sdr_trace,

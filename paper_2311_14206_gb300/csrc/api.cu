@@ -55,6 +55,7 @@ struct sdr_handle {
   int cu = 0;  // current recycle buffer
   int kh = 0;  // current recycle dimension
   std::vector<double> hist;
+  std::vector<double> hist_givens;  // (sine, cosine) per step
   std::vector<CycleLog> log;
   double* d_tmp = nullptr;  // n_max scratch vector (A u)
   Prof prof;
@@ -117,7 +118,8 @@ int ceil_log2(int64_t v) {
 
 bool csr_ok(const sdr_handle* h, const sdr_csr* A) {
   return A && A->n > 0 && A->n <= h->n_max && A->nnz >= 0 && A->rowptr && A->col && A->val &&
-         A->nnz < ((int64_t)1 << 31) && (h->prec == SDR_PREC_F64 || A->val32);
+         A->nnz < ((int64_t)1 << 31) && (h->prec == SDR_PREC_F64 || A->val32) &&
+         (h->ws.sketch_kind == 0 || A->n == h->ws.dct_n);  // a DCT sketch is drawn for one size
 }
 
 CsrDev to_dev(const sdr_csr* A) { return CsrDev{A->n, A->nnz, A->rowptr, A->col, A->val, A->val32}; }
@@ -268,7 +270,9 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   if (!(p->inner_rel_tol >= 0.0 && p->inner_rel_tol < 1.0)) return SDR_ERR_INVALID_ARG;
   if (n_max >= ((int64_t)1 << 31)) return SDR_ERR_INVALID_ARG;
   if (p->stale_check != 0 && p->stale_check != 1) return SDR_ERR_INVALID_ARG;
-  if (p->reserved[0] || p->reserved[1] || p->reserved[2]) return SDR_ERR_INVALID_ARG;
+  if (p->sketch_kind != 0 && p->sketch_kind != 1) return SDR_ERR_INVALID_ARG;
+  if (p->sketch_kind == 1 && n_max >= ((int64_t)1 << 29)) return SDR_ERR_INVALID_ARG;
+  if (p->reserved[0] || p->reserved[1]) return SDR_ERR_INVALID_ARG;
   sdr_handle* h = new sdr_handle();
   h->p = *p;
   if (!(h->p.inner_rel_tol > 0.0)) h->p.inner_rel_tol = 1e-4;
@@ -283,6 +287,8 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   // column segments of an even number of rows)
   ws.ldv = (n_max + 32) & ~(int64_t)31;
   ws.recycle_int = (p->test_flags & 4) ? 1 : 0;
+  ws.sketch_kind = p->sketch_kind;
+  ws.dct_n = 0;  // set by sdr_set_sketch_draws
   ws.m = p->m;
   ws.k = p->k;
   ws.t = p->t;
@@ -291,7 +297,9 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   ws.kmax = p->k + 1;
   ws.dmax = D_MAX;
   ws.seed = p->seed;
-  ws.inv_sqrt_zeta = 1.0 / std::sqrt((double)p->zeta);
+  // the sparse sign's 1/sqrt(zeta) is applied when an accumulator is read; the
+  // DCT sketch scales each row as it accumulates
+  ws.inv_sqrt_zeta = p->sketch_kind == 1 ? 1.0 : 1.0 / std::sqrt((double)p->zeta);
   ws.win_bits = ceil_log2(n_max) + 1;
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
@@ -306,7 +314,13 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
     chk(halloc(h, &b, count * esz));
     *q = b;
   };
-  tall(&ws.Vs, (size_t)N * p->m);
+  // the V slab has a front column before V(:, 1): the recycle product copies
+  // V(:, 0) there so that V(:, 0:m) is one 2D array
+  {
+    void* slab = nullptr;
+    tall(&slab, (size_t)N * (p->m + 1));
+    ws.Vs = slab ? (void*)((unsigned char*)slab + (size_t)N * esz) : nullptr;
+  }
   tall(&ws.R[0], (size_t)N);
   tall(&ws.R[1], (size_t)N);
   tall(&ws.Wv, (size_t)N);
@@ -380,6 +394,20 @@ sdr_status sdr_create(const sdr_params* p, int64_t n_max, void* stream, sdr_hand
   chk(halloc(h, &ws.yexp, (size_t)4));
   chk(halloc(h, &ws.dscr, ce_scratch_doubles()));
   chk(halloc(h, &ws.hist, (size_t)HIST_MAX));
+  if (p->sketch_kind == 1) {
+    signed char* sg = nullptr;
+    int* fk = nullptr;
+    double *cs = nullptr, *sc = nullptr;
+    chk(halloc(h, &sg, (size_t)n_max));
+    chk(halloc(h, &fk, (size_t)S_MAX));
+    chk(halloc(h, &cs, (size_t)n_max + 1));
+    chk(halloc(h, &sc, (size_t)S_MAX));
+    ws.dct_sign = sg;
+    ws.dct_k = fk;
+    ws.dct_cos = cs;
+    ws.dct_scale = sc;
+  }
+  chk(halloc(h, &ws.hist_givens, (size_t)2 * HIST_MAX));
   chk(halloc(h, &ws.log, (size_t)LOG_MAX));
   chk(halloc(h, &ws.ctl, (size_t)1));
   if (e != cudaSuccess) {
@@ -460,6 +488,10 @@ sdr_status issue_cycle(sdr_handle* h, const WS& ws, const CsrDev& Ad, const T* b
   for (int j = 0; j <= m; ++j) {
     if (j >= SPEC_LAG) SDR_CK(cudaStreamWaitEvent(st, h->evD[j - SPEC_LAG], 0));
     if (j < m) {
+      if (ws.sketch_kind && j >= 1)  // the DCT sketch of v_hat_j (the sparse sign is fused into the SpMV)
+        SDR_LAUNCH(h, SDR_K_SKETCH,
+                   launch_sketch_vec<T>(ws, vcol[j], ws.n, ws.accV + (int64_t)j * 2 * S_MAX,
+                                        ctl_int_field(ws.ctl, offsetof(Ctl, vtop) + j * sizeof(int)), st));
       SDR_LAUNCH(h, SDR_K_SPMV_DOTS, launch_spmv_dots<T>(ws, Ad, vcol, j, st));
     } else {
       SDR_LAUNCH(h, SDR_K_SKETCH, launch_sketch_col<T>(ws, vcol[m], m, st));
@@ -694,6 +726,10 @@ sdr_status solve_end(sdr_handle* h, const CycleRun<double>* run_f64, const Ctl& 
   h->hist.assign(nh, 0.0);
   h->log.assign(nl, CycleLog());
   if (nh) SDR_CK(cudaMemcpyAsync(h->hist.data(), ws.hist, nh * sizeof(double), cudaMemcpyDeviceToHost, st));
+  h->hist_givens.assign(2 * (size_t)nh, 0.0);
+  if (nh)
+    SDR_CK(cudaMemcpyAsync(h->hist_givens.data(), ws.hist_givens, 2 * nh * sizeof(double), cudaMemcpyDeviceToHost,
+                           st));
   if (nl) SDR_CK(cudaMemcpyAsync(h->log.data(), ws.log, nl * sizeof(CycleLog), cudaMemcpyDeviceToHost, st));
   SDR_CK(cudaStreamSynchronize(st));
   SDR_CK(prof_collect(h));
@@ -1000,6 +1036,7 @@ sdr_status sdr_recycle(sdr_handle* h, const sdr_csr* A_next, int32_t mode) {
 
 sdr_status sdr_sketch(sdr_handle* h, const double* x, int64_t n, double* y) {
   if (!h || !x || !y || n <= 0 || n > h->n_max) return SDR_ERR_INVALID_ARG;
+  if (h->ws.sketch_kind && n != h->ws.dct_n) return SDR_ERR_INVALID_ARG;
   StreamGuard guard(h);
   WS ws = h->ws;
   ws.n = n;
@@ -1026,6 +1063,43 @@ sdr_status sdr_get_history(sdr_handle* h, double* sres, int32_t cap_steps, int32
   if (n_cycles) *n_cycles = nl;
   if (sres && cap_steps > 0) std::memcpy(sres, h->hist.data(), sizeof(double) * (nh < cap_steps ? nh : cap_steps));
   if (log && cap_cycles > 0) std::memcpy(log, h->log.data(), sizeof(CycleLog) * (nl < cap_cycles ? nl : cap_cycles));
+  return SDR_OK;
+}
+
+sdr_status sdr_set_sketch_draws(sdr_handle* h, int64_t n, const int8_t* signs, const int32_t* rows) {
+  if (!h || h->ws.sketch_kind != 1 || n < 1 || n > h->n_max || !signs || !rows) return SDR_ERR_INVALID_ARG;
+  const int s = h->ws.s;
+  for (int i = 0; i < s; ++i)
+    if (rows[i] < 0 || rows[i] >= n || (i > 0 && rows[i] <= rows[i - 1])) return SDR_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i)
+    if (signs[i] != 1 && signs[i] != -1) return SDR_ERR_INVALID_ARG;
+  StreamGuard guard(h);
+  std::vector<double> scale(s);
+  for (int i = 0; i < s; ++i) scale[i] = (rows[i] == 0 ? 1.0 : std::sqrt(2.0)) / std::sqrt((double)s);
+  WS& ws = h->ws;
+  SDR_CK(cudaMemcpyAsync((void*)ws.dct_sign, signs, (size_t)n, cudaMemcpyHostToDevice, h->st));
+  SDR_CK(cudaMemcpyAsync((void*)ws.dct_k, rows, (size_t)s * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  SDR_CK(cudaMemcpyAsync((void*)ws.dct_scale, scale.data(), (size_t)s * sizeof(double), cudaMemcpyHostToDevice,
+                         h->st));
+  SDR_CK(launch_dct_table((double*)ws.dct_cos, n, h->st));
+  SDR_CK(cudaStreamSynchronize(h->st));
+  if (ws.dct_n != n) {  // graphs captured with another size are stale
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+  }
+  ws.dct_n = n;
+  h->kh = 0;  // a recycle space sketched with another operator is dropped
+  return SDR_OK;
+}
+
+sdr_status sdr_get_givens(sdr_handle* h, double* sines, double* cosines, int32_t cap, int32_t* n_steps) {
+  if (!h || cap < 0) return SDR_ERR_INVALID_ARG;
+  const int nh = (int)(h->hist_givens.size() / 2);
+  if (n_steps) *n_steps = nh;
+  for (int i = 0; i < nh && i < cap; ++i) {
+    if (sines) sines[i] = h->hist_givens[2 * (size_t)i];
+    if (cosines) cosines[i] = h->hist_givens[2 * (size_t)i + 1];
+  }
   return SDR_OK;
 }
 
@@ -1098,6 +1172,7 @@ sdr_status sdr_recycle_export(sdr_handle* h, int64_t n, double* U, double* SU, d
 sdr_status sdr_recycle_import(sdr_handle* h, const sdr_csr* A, int64_t n, int32_t kdim, const double* U,
                               const double* SU, const double* SAU) {
   if (!h || n <= 0 || n > h->n_max || kdim < 0 || kdim > h->ws.kmax) return SDR_ERR_INVALID_ARG;
+  if (h->ws.sketch_kind && n != h->ws.dct_n) return SDR_ERR_INVALID_ARG;
   if (h->prec != SDR_PREC_F64) return SDR_ERR_NOT_IMPLEMENTED;
   if (kdim > 0 && !U) return SDR_ERR_INVALID_ARG;
   StreamGuard guard(h);

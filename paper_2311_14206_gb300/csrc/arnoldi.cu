@@ -217,7 +217,7 @@ __global__ void k_residual(WS ws, CsrDev A, const T* __restrict__ b, const T* __
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = (int64_t)tile * tileR;
     const int ncols = (int)(n - r0 < (int64_t)tileR ? n - r0 : (int64_t)tileR);
-    tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
+    if (!ws.sketch_kind) tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
     for (int i = threadIdx.x; i < tileR; i += blockDim.x) {
       double v = 0.0;
       if (i < ncols) {
@@ -231,7 +231,10 @@ __global__ void k_residual(WS ws, CsrDev A, const T* __restrict__ b, const T* __
       }
       vals[i] = v;
     }
-    tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
+    if (ws.sketch_kind)
+      tile_dct_accumulate<SK_RPT>(ws, r0, ncols, vals, top, lo, hi);
+    else
+      tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
   }
 #pragma unroll
   for (int k = 0; k < SK_RPT; ++k) {
@@ -591,6 +594,14 @@ cudaError_t launch_spmv_dots(const WS& ws, CsrDev A, const T* const* vcol, int j
   win.nw = j - win.lo + 1;
   for (int a = 0; a < T_MAX; ++a) win.v[a] = a < win.nw ? vcol[win.lo + a] : nullptr;
   if (j == 0) return launch_spmv_t<T, 1, false>(ws, A, win, j, st);  // S r0 came with r0
+  if (ws.sketch_kind) {  // the DCT sketch of v_hat_j is a separate launch before this one
+    switch (win.nw) {
+      case 1: return launch_spmv_t<T, 1, false>(ws, A, win, j, st);
+      case 2: return launch_spmv_t<T, 2, false>(ws, A, win, j, st);
+      case 3: return launch_spmv_t<T, 3, false>(ws, A, win, j, st);
+      default: return launch_spmv_t<T, 4, false>(ws, A, win, j, st);
+    }
+  }
   switch (win.nw) {
     case 1: return launch_spmv_t<T, 1, true>(ws, A, win, j, st);
     case 2: return launch_spmv_t<T, 2, true>(ws, A, win, j, st);
@@ -621,9 +632,12 @@ __global__ void __launch_bounds__(SK_THREADS) k_sketch_col(WS ws, const T* __res
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = (int64_t)tile * tileR;
     const int ncols = (int)(n - r0 < (int64_t)tileR ? n - r0 : (int64_t)tileR);
-    tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
+    if (!ws.sketch_kind) tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
     for (int i = threadIdx.x; i < tileR; i += blockDim.x) vals[i] = i < ncols ? (double)x[r0 + i] : 0.0;
-    tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
+    if (ws.sketch_kind)
+      tile_dct_accumulate<SK_RPT>(ws, r0, ncols, vals, top, lo, hi);
+    else
+      tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
   }
 #pragma unroll
   for (int k = 0; k < SK_RPT; ++k) {

@@ -512,311 +512,325 @@ __device__ inline float block_sum_f(float v, float* red) {
   return r;
 }
 
+
+// ---------------------------------------------------------------------------
+// FP32 eigenvalues of the upper-Hessenberg H by the implicitly double-shifted
+// (Francis) QR iteration, as set out in Golub and Van Loan, Matrix
+// Computations (4th ed.), Section 7.5: Algorithm 7.5.1 (one Francis step on an
+// unreduced Hessenberg block) inside the deflation loop of Algorithm 7.5.2.
+// Only the eigenvalues are wanted, so each step transforms the active block
+// H(lo:hi, lo:hi) alone.  Reflectors are the Householder vectors of
+// Algorithm 5.1.1, v = (1, v1, v2) with P = I - beta v v^T.  Each double-shift
+// step starts its bulge at the largest m in [lo, hi-2] where the subdiagonal
+// entry H(m, m-1) is small enough that the first reflector's effect on it is
+// negligible (Wilkinson, The Algebraic Eigenvalue Problem, on two consecutive
+// small subdiagonal elements): starting at lo instead destroys, in FP32, the
+// accuracy of eigenvalues of a nearly decoupled leading part.  H is scaled by
+// a power of two to a norm of order one first, so that the products in the
+// first column of (H - s1 I)(H - s2 I) neither underflow nor overflow.
+//
+// GPU arrangement (QR_WARPS warps, one named barrier per bulge position):
+// at the step whose reflector acts on indices a, a+1, a+2, warp 0 updates the
+// neighbourhood of the bulge (rows a..a+2 on columns up to a+3, then columns
+// a..a+2 on rows a..a+3) and forms the next reflector, QR_RW warps apply the
+// row transformation to columns a+4..hi and QR_CW warps the column
+// transformation to rows lo..a-1.  The three parts touch disjoint entries.
+// ---------------------------------------------------------------------------
 __device__ inline float& HF(float* H, int ldh, int i, int j) { return H[i + j * ldh]; }
 
-// Column part of one 3x3 (or 2x2) reflector of the bulge chase on rows
-// l + off + stride t <= imax, with every load (at most NS rows) issued first.
-template <int NS>
-__device__ __forceinline__ void col_update(float* H, int ldh, int k, int l, int imax, int off, int stride, bool three,
-                                           float qq, float rq, float xx, float yy, float zz) {
-  float b0[NS], b1[NS], b2[NS];
-#pragma unroll
-  for (int t = 0; t < NS; ++t) {
-    const int i = l + off + stride * t;
-    const bool in = i <= imax;
-    b0[t] = in ? HF(H, ldh, i, k) : 0.f;
-    b1[t] = in ? HF(H, ldh, i, k + 1) : 0.f;
-    b2[t] = (in && three) ? HF(H, ldh, i, k + 2) : 0.f;
-  }
-#pragma unroll
-  for (int t = 0; t < NS; ++t) {
-    const int i = l + off + stride * t;
-    if (i <= imax) {
-      const float pp = xx * b0[t] + yy * b1[t] + zz * b2[t];
-      if (three) HF(H, ldh, i, k + 2) = b2[t] - pp * rq;
-      HF(H, ldh, i, k + 1) = b1[t] - pp * qq;
-      HF(H, ldh, i, k) = b0[t] - pp;
-    }
-  }
-}
-
-// Row part of a reflector on columns c0 + off + stride t <= c1 (rows k..k+2,
-// or k..k+1 when !three), with every load (at most NS columns) issued first.
-template <int NS>
-__device__ __forceinline__ void row_update_range(float* H, int ldh, int k, int c0, int c1, int off, int stride,
-                                                 bool three, float qq, float rq, float xx, float yy, float zz) {
-  float a0[NS], a1[NS], a2[NS];
-#pragma unroll
-  for (int t = 0; t < NS; ++t) {
-    const int jj = c0 + off + stride * t;
-    const bool in = jj <= c1;
-    a0[t] = in ? HF(H, ldh, k, jj) : 0.f;
-    a1[t] = in ? HF(H, ldh, k + 1, jj) : 0.f;
-    a2[t] = (in && three) ? HF(H, ldh, k + 2, jj) : 0.f;
-  }
-#pragma unroll
-  for (int t = 0; t < NS; ++t) {
-    const int jj = c0 + off + stride * t;
-    if (jj <= c1) {
-      const float pp = a0[t] + qq * a1[t] + rq * a2[t];
-      if (three) HF(H, ldh, k + 2, jj) = a2[t] - pp * zz;
-      HF(H, ldh, k + 1, jj) = a1[t] - pp * yy;
-      HF(H, ldh, k, jj) = a0[t] - pp * xx;
-    }
-  }
-}
-
-// Warps of the QR iteration: warp 0 on the region around the bulge, QR_RW on
-// the row part and QR_CW on the column part of the rest.
 constexpr int QR_RW = 2, QR_CW = 2, QR_WARPS = 1 + QR_RW + QR_CW;
 __device__ __forceinline__ void qr_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * QR_WARPS) : "memory"); }
 
-// Francis double-shift QR on the upper-Hessenberg H (n x n, ld ldh), the
-// first QR_WARPS warps of the block; eigenvalues into wr, wi.  Returns false
-// when the iteration limit is reached.  All these warps follow the same
-// control flow (their decisions are read from the same shared values); shared
-// writes outside the bulge chase are made by warp 0 between barriers.
-//
-// Each step k of the bulge chase applies one reflector to rows k..k+2 (columns
-// k..nn) and to columns k..k+2 (rows l..min(k+3, nn)).  Warp 0 takes the 4 x 4
-// region rows and columns k..k+3 (in registers, every lane the same
-// arithmetic; lane 0 stores) and forms the next reflector from its column k;
-// the other warps take the rest: QR_RW warps the row part on columns k+4..nn,
-// QR_CW warps the column part on rows l..k-1.  The parts touch disjoint
-// elements, each element gets the operations of the one-warp order, and the
-// next step's inputs from other warps (column k+4 of rows k+1..k+2, row k of
-// columns k+1..k+3) are complete after the one barrier between steps.
-// rs: 8 floats of shared memory.
-__device__ bool hqr_f32_2w(float* H, int ldh, int n, float* wr, float* wi, float* rs) {
-  const int tid = threadIdx.x;
-  const int lane = tid & 31, wrp = tid >> 5;
-  const float eps = 1.1920929e-7f;
-  float an = 0.f;
+// Householder vector of (x, y, z) (z = 0 and three = false for a 2-vector):
+// P (x, y, z)^T = (mu, 0, 0)^T with P = I - beta v v^T, v = (1, v1, v2).
+struct Refl {
+  float beta, v1, v2;
+};
+__device__ __forceinline__ Refl house3(float x, float y, float z) {
+  Refl h{0.f, 0.f, 0.f};
+  // P depends only on the direction of (x, y, z): scale it to a maximum
+  // magnitude of one so that the squares below neither underflow nor overflow
+  const float mx = fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z)));
+  if (!(mx > 0.f) || !isfinite(mx)) return h;
+  const float is = 1.f / mx;
+  x *= is;
+  y *= is;
+  z *= is;
+  const float sig = y * y + z * z;
+  if (sig == 0.f) return h;  // already of the form (x, 0, 0): P = I
+  const float mu = sqrtf(x * x + sig);
+  const float w = x <= 0.f ? x - mu : -sig / (x + mu);  // the first entry of x - mu e1, without cancellation
+  h.v1 = y / w;
+  h.v2 = z / w;
+  h.beta = 2.f * w * w / (sig + w * w);
+  return h;
+}
+
+// Left transformation of rows a, a+1 (, a+2) on columns j0 + off + stride t
+// <= j1: every load (at most NS columns per thread) is issued before any store.
+template <int NS>
+__device__ __forceinline__ void refl_rows(float* H, int ldh, int a, bool three, Refl P, int j0, int j1, int off,
+                                          int stride) {
+  float r0[NS], r1[NS], r2[NS];
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int j = j0 + off + stride * t;
+    const bool in = j <= j1;
+    r0[t] = in ? HF(H, ldh, a, j) : 0.f;
+    r1[t] = in ? HF(H, ldh, a + 1, j) : 0.f;
+    r2[t] = (in && three) ? HF(H, ldh, a + 2, j) : 0.f;
+  }
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int j = j0 + off + stride * t;
+    if (j <= j1) {
+      const float w = P.beta * (r0[t] + P.v1 * r1[t] + P.v2 * r2[t]);
+      HF(H, ldh, a, j) = r0[t] - w;
+      HF(H, ldh, a + 1, j) = r1[t] - w * P.v1;
+      if (three) HF(H, ldh, a + 2, j) = r2[t] - w * P.v2;
+    }
+  }
+}
+
+// Right transformation of columns a, a+1 (, a+2) on rows i0 + off + stride t <= i1.
+template <int NS>
+__device__ __forceinline__ void refl_cols(float* H, int ldh, int a, bool three, Refl P, int i0, int i1, int off,
+                                          int stride) {
+  float c0[NS], c1[NS], c2[NS];
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int i = i0 + off + stride * t;
+    const bool in = i <= i1;
+    c0[t] = in ? HF(H, ldh, i, a) : 0.f;
+    c1[t] = in ? HF(H, ldh, i, a + 1) : 0.f;
+    c2[t] = (in && three) ? HF(H, ldh, i, a + 2) : 0.f;
+  }
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int i = i0 + off + stride * t;
+    if (i <= i1) {
+      const float w = P.beta * (c0[t] + P.v1 * c1[t] + P.v2 * c2[t]);
+      HF(H, ldh, i, a) = c0[t] - w;
+      HF(H, ldh, i, a + 1) = c1[t] - w * P.v1;
+      if (three) HF(H, ldh, i, a + 2) = c2[t] - w * P.v2;
+    }
+  }
+}
+
+// Eigenvalues of the 2 x 2 block [[p, q], [r, s]] from its trace and
+// determinant: two real values (the larger-magnitude root first, the other
+// from the product) or a conjugate pair.
+__device__ __forceinline__ void eig2x2(float p, float q, float r, float s, float& re1, float& im1, float& re2,
+                                       float& im2) {
+  const float half = 0.5f * (p - s);
+  const float disc = half * half + q * r;
+  const float mid = 0.5f * (p + s);
+  if (disc >= 0.f) {
+    const float root = sqrtf(disc);
+    const float big = mid + copysignf(root, mid);
+    const float det = p * s - q * r;
+    re1 = big;
+    re2 = big != 0.f ? det / big : mid - root;
+    im1 = im2 = 0.f;
+  } else {
+    const float root = sqrtf(-disc);
+    re1 = re2 = mid;
+    im1 = root;
+    im2 = -root;
+  }
+}
+
+// Runs on the first QR_WARPS warps of the block; returns false when the
+// iteration limit is reached (the eigenvalues not yet found are set to NaN).
+// sh: 8 floats of shared memory for passing the next reflector's input.
+__device__ bool francis_eigenvalues(float* H, int ldh, int n, float* wr, float* wi, float* sh) {
+  const int tid = threadIdx.x, lane = tid & 31, wrp = tid >> 5;
+  const float ulp = 1.1920929e-7f;
+  float hnorm = 0.f;  // a scale for the deflation test where both diagonal entries vanish
   for (int idx = lane; idx < n * n; idx += 32) {
     const int i = idx % n, j = idx / n;
-    if (i <= j + 1) an += fabsf(HF(H, ldh, i, j));
+    if (i <= j + 1) hnorm += fabsf(HF(H, ldh, i, j));
   }
-  an = warp_sum_f(an);
-  int nn = n - 1, total = 0;
-  float tsh = 0.f;
-  while (nn >= 0) {
-    int its = 0;
-    while (true) {
-      // the largest l <= nn with a negligible H(l, l-1) (0 if none): 32
-      // candidates per round, one per lane, the largest found by a ballot
-      int l = 0;
-      for (int base = nn; base > 0; base -= 32) {
-        const int cand = base - lane;
-        bool hit = false;
-        if (cand > 0) {
-          float s = fabsf(HF(H, ldh, cand - 1, cand - 1)) + fabsf(HF(H, ldh, cand, cand));
-          if (s == 0.f) s = an;
-          hit = fabsf(HF(H, ldh, cand, cand - 1)) <= eps * s;
-        }
-        const unsigned msk = __ballot_sync(0xffffffffu, hit);
-        if (msk) {
-          l = base - (__ffs(msk) - 1);
-          break;
-        }
+  for (int o = 16; o > 0; o >>= 1) hnorm += __shfl_xor_sync(0xffffffffu, hnorm, o);
+  int hexp = 0;
+  frexpf(hnorm > 0.f ? hnorm : 1.f, &hexp);
+  const float hscale = ldexpf(1.f, -hexp);  // exact: eigenvalues scale back by 2^hexp
+  qr_bar();
+  for (int idx = tid; idx < n * n; idx += 32 * QR_WARPS) {
+    const int i = idx % n, j = idx / n;
+    if (i <= j + 1) HF(H, ldh, i, j) *= hscale;
+  }
+  hnorm *= hscale;
+  qr_bar();
+  int hi = n - 1, steps = 0, since = 0;
+  const int cap = 40 * n;
+  while (hi >= 0) {
+    // deflation (Algorithm 7.5.2): the largest lo <= hi with a negligible
+    // H(lo, lo-1), which is set to zero; candidates tested 32 at a time
+    int lo = 0;
+    for (int top = hi; top > 0; top -= 32) {
+      const int cand = top - lane;
+      bool small = false;
+      if (cand > 0) {
+        float d = fabsf(HF(H, ldh, cand - 1, cand - 1)) + fabsf(HF(H, ldh, cand, cand));
+        if (d == 0.f) d = hnorm;
+        small = fabsf(HF(H, ldh, cand, cand - 1)) <= ulp * d;
       }
-      qr_bar();
-      if (l > 0 && tid == 0) HF(H, ldh, l, l - 1) = 0.f;
-      qr_bar();
-      float x = HF(H, ldh, nn, nn);
-      if (l == nn) {
-        if (tid == 0) { wr[nn] = x + tsh; wi[nn] = 0.f; }
-        nn -= 1;
+      const unsigned hits = __ballot_sync(0xffffffffu, small);
+      if (hits) {
+        lo = top - (__ffs(hits) - 1);
         break;
       }
-      float y = HF(H, ldh, nn - 1, nn - 1);
-      float w = HF(H, ldh, nn, nn - 1) * HF(H, ldh, nn - 1, nn);
-      if (l == nn - 1) {
-        const float p = 0.5f * (y - x), q = p * p + w;
-        float z = sqrtf(fabsf(q));
-        x += tsh;
-        if (tid == 0) {
-          if (q >= 0.f) {
-            z = p + copysignf(z, p);
-            wr[nn - 1] = wr[nn] = x + z;
-            if (z != 0.f) wr[nn] = x - w / z;
-            wi[nn - 1] = wi[nn] = 0.f;
-          } else {
-            wr[nn - 1] = wr[nn] = x + p;
-            wi[nn - 1] = z;
-            wi[nn] = -z;
-          }
-        }
-        nn -= 2;
+    }
+    qr_bar();
+    if (lo > 0 && tid == 0) HF(H, ldh, lo, lo - 1) = 0.f;
+    qr_bar();
+    if (lo == hi) {  // a 1 x 1 block
+      if (tid == 0) {
+        wr[hi] = ldexpf(HF(H, ldh, hi, hi), hexp);
+        wi[hi] = 0.f;
+      }
+      hi -= 1;
+      since = 0;
+      continue;
+    }
+    if (lo == hi - 1) {  // a 2 x 2 block
+      if (tid == 0) {
+        eig2x2(HF(H, ldh, hi - 1, hi - 1), HF(H, ldh, hi - 1, hi), HF(H, ldh, hi, hi - 1), HF(H, ldh, hi, hi),
+               wr[hi - 1], wi[hi - 1], wr[hi], wi[hi]);
+        wr[hi - 1] = ldexpf(wr[hi - 1], hexp);
+        wi[hi - 1] = ldexpf(wi[hi - 1], hexp);
+        wr[hi] = ldexpf(wr[hi], hexp);
+        wi[hi] = ldexpf(wi[hi], hexp);
+      }
+      hi -= 2;
+      since = 0;
+      continue;
+    }
+    if (steps >= cap) {
+      for (int i = tid; i <= hi; i += 32 * QR_WARPS) {
+        wr[i] = NAN;
+        wi[i] = 0.f;
+      }
+      qr_bar();
+      return false;
+    }
+    ++steps;
+    ++since;
+    // the double shift: trace and determinant of the trailing 2 x 2 block; an
+    // ad hoc real shift after every ten steps without deflation
+    float tr, dt;
+    if (since % 10 == 0) {
+      const float g = HF(H, ldh, hi, hi) + 1.5f * (fabsf(HF(H, ldh, hi, hi - 1)) + fabsf(HF(H, ldh, hi - 1, hi - 2)));
+      tr = 2.f * g;
+      dt = g * g;
+    } else {
+      const float p = HF(H, ldh, hi - 1, hi - 1), q = HF(H, ldh, hi - 1, hi);
+      const float r = HF(H, ldh, hi, hi - 1), s = HF(H, ldh, hi, hi);
+      tr = p + s;
+      dt = p * s - q * r;
+    }
+    // where the bulge starts, and the first column (x, y, z) of
+    // (H - s1 I)(H - s2 I) from there (Algorithm 7.5.1): the largest m with a
+    // negligible |H(m, m-1)| (|y| + |z|) against |x| times the neighbouring
+    // diagonal, or lo; candidates tested 32 at a time
+    int m0 = lo;
+    float x = 0.f, y = 0.f, z = 0.f;
+    for (int top = hi - 2; top >= lo; top -= 32) {
+      const int cand = top - lane;
+      bool stop = false;
+      float cx = 0.f, cy = 0.f, cz = 0.f;
+      if (cand >= lo) {
+        const float g00 = HF(H, ldh, cand, cand), g01 = HF(H, ldh, cand, cand + 1);
+        const float g10 = HF(H, ldh, cand + 1, cand), g11 = HF(H, ldh, cand + 1, cand + 1);
+        cx = g00 * g00 + g01 * g10 - tr * g00 + dt;
+        cy = g10 * (g00 + g11 - tr);
+        cz = g10 * HF(H, ldh, cand + 2, cand + 1);
+        stop = cand == lo || fabsf(HF(H, ldh, cand, cand - 1)) * (fabsf(cy) + fabsf(cz)) <=
+                                 ulp * fabsf(cx) * (fabsf(HF(H, ldh, cand - 1, cand - 1)) + fabsf(g00) + fabsf(g11));
+      }
+      const unsigned hits = __ballot_sync(0xffffffffu, stop);
+      if (hits) {
+        const int src = __ffs(hits) - 1;
+        m0 = top - src;
+        x = __shfl_sync(0xffffffffu, cx, src);
+        y = __shfl_sync(0xffffffffu, cy, src);
+        z = __shfl_sync(0xffffffffu, cz, src);
         break;
       }
-      if (its >= 60 || total >= 60 * n) {
-        for (int i = tid; i <= nn; i += 32 * QR_WARPS) { wr[i] = NAN; wi[i] = 0.f; }
-        qr_bar();
-        return false;
-      }
-      if (its == 10 || its == 20) {  // exceptional shift
-        tsh += x;
-        qr_bar();
-        if (wrp == 0)
-          for (int i = lane; i <= nn; i += 32) HF(H, ldh, i, i) -= x;
-        qr_bar();
-        const float s = fabsf(HF(H, ldh, nn, nn - 1)) + fabsf(HF(H, ldh, nn - 1, nn - 2));
-        x = y = 0.75f * s;
-        w = -0.4375f * s * s;
-      }
-      ++its;
-      ++total;
-      // where the double shift starts: the largest m in [l, nn-2] whose
-      // first column (p, q, r) of (H - sigma1)(H - sigma2) decouples from row
-      // m-1 (or m = l), 32 candidates per round as above
-      int m = l;
-      float p = 0.f, q = 0.f, r = 0.f;
-      for (int base = nn - 2; base >= l; base -= 32) {
-        const int cand = base - lane;
-        bool stop = false;
-        float pc = 0.f, qc = 0.f, rc = 0.f;
-        if (cand >= l) {
-          const float z = HF(H, ldh, cand, cand);
-          const float rr = x - z, ss = y - z;
-          pc = (rr * ss - w) / HF(H, ldh, cand + 1, cand) + HF(H, ldh, cand, cand + 1);
-          qc = HF(H, ldh, cand + 1, cand + 1) - z - rr - ss;
-          rc = HF(H, ldh, cand + 2, cand + 1);
-          const float inv = 1.f / (fabsf(pc) + fabsf(qc) + fabsf(rc));
-          pc *= inv; qc *= inv; rc *= inv;
-          if (cand == l) {
-            stop = true;
+    }
+    // bulge chase: the reflector of step a acts on indices a, a+1 (, a+2); a
+    // start m0 > lo also transforms column m0 - 1, whose fill below the
+    // subdiagonal is the negligible part dropped with the zeroing below
+    for (int a = m0; a <= hi - 1; ++a) {
+      const bool three = a + 2 <= hi;
+      const Refl P = house3(x, y, three ? z : 0.f);
+      const int q = a > lo ? a - 1 : lo;      // first column of the row transformation
+      const int near = a + 3 < hi ? a + 3 : hi;  // last column near the bulge, last row of the column transformation
+      float nx = 0.f, ny = 0.f, nz = 0.f;
+      if (P.beta != 0.f) {
+        if (wrp == 0) {
+          // rows a..a+2 on columns q..near, then columns a..a+2 on rows a..near:
+          // each lane takes one column, then one row; lane-parallel within the warp
+          if (lane <= near - q) {
+            const int j = q + lane;
+            const float r0 = HF(H, ldh, a, j), r1 = HF(H, ldh, a + 1, j), r2 = three ? HF(H, ldh, a + 2, j) : 0.f;
+            const float w = P.beta * (r0 + P.v1 * r1 + P.v2 * r2);
+            HF(H, ldh, a, j) = r0 - w;
+            HF(H, ldh, a + 1, j) = r1 - w * P.v1;
+            if (three) HF(H, ldh, a + 2, j) = r2 - w * P.v2;
+          }
+          __syncwarp();
+          if (lane <= near - a) {
+            const int i = a + lane;
+            const float c0 = HF(H, ldh, i, a), c1 = HF(H, ldh, i, a + 1), c2 = three ? HF(H, ldh, i, a + 2) : 0.f;
+            const float w = P.beta * (c0 + P.v1 * c1 + P.v2 * c2);
+            HF(H, ldh, i, a) = c0 - w;
+            HF(H, ldh, i, a + 1) = c1 - w * P.v1;
+            if (three) HF(H, ldh, i, a + 2) = c2 - w * P.v2;
+          }
+          __syncwarp();
+          if (lane == 0) {
+            if (a > lo) {  // the bulge column below the subdiagonal is now zero
+              HF(H, ldh, a + 1, a - 1) = 0.f;
+              if (three) HF(H, ldh, a + 2, a - 1) = 0.f;
+            }
+            if (a + 1 <= hi - 1) {  // the next reflector's input: column a of rows a+1..a+3
+              nx = HF(H, ldh, a + 1, a);
+              ny = HF(H, ldh, a + 2, a);
+              nz = a + 3 <= hi ? HF(H, ldh, a + 3, a) : 0.f;
+            }
+          }
+        } else if (wrp <= QR_RW) {
+          const int off = 32 * (wrp - 1) + lane, stride = 32 * QR_RW;
+          if (hi - (near + 1) < 2 * stride) {
+            refl_rows<2>(H, ldh, a, three, P, near + 1, hi, off, stride);
           } else {
-            const float u = fabsf(HF(H, ldh, cand, cand - 1)) * (fabsf(qc) + fabsf(rc));
-            const float v = fabsf(pc) * (fabsf(HF(H, ldh, cand - 1, cand - 1)) + fabsf(z) +
-                                         fabsf(HF(H, ldh, cand + 1, cand + 1)));
-            stop = u <= eps * v;
+            refl_rows<(D_MAX + 32 * QR_RW - 1) / (32 * QR_RW)>(H, ldh, a, three, P, near + 1, hi, off, stride);
+          }
+        } else {
+          const int off = 32 * (wrp - 1 - QR_RW) + lane, stride = 32 * QR_CW;
+          if (a - 1 - lo < 2 * stride) {
+            refl_cols<2>(H, ldh, a, three, P, lo, a - 1, off, stride);
+          } else {
+            refl_cols<(D_MAX + 32 * QR_CW - 1) / (32 * QR_CW)>(H, ldh, a, three, P, lo, a - 1, off, stride);
           }
         }
-        const unsigned msk = __ballot_sync(0xffffffffu, stop);
-        if (msk) {
-          const int src = __ffs(msk) - 1;
-          m = base - src;
-          p = __shfl_sync(0xffffffffu, pc, src);
-          q = __shfl_sync(0xffffffffu, qc, src);
-          r = __shfl_sync(0xffffffffu, rc, src);
-          break;
-        }
+      } else if (wrp == 0 && lane == 0 && a + 1 <= hi - 1) {
+        nx = HF(H, ldh, a + 1, a);
+        ny = HF(H, ldh, a + 2, a);
+        nz = a + 3 <= hi ? HF(H, ldh, a + 3, a) : 0.f;
+      }
+      float* slot = sh + 4 * (a & 1);  // alternating slots: one barrier per step suffices
+      if (tid == 0) {
+        slot[0] = nx;
+        slot[1] = ny;
+        slot[2] = nz;
       }
       qr_bar();
-      if (wrp == 0)
-        for (int i = m + 2 + lane; i <= nn; i += 32) {
-          HF(H, ldh, i, i - 2) = 0.f;
-          if (i != m + 2) HF(H, ldh, i, i - 3) = 0.f;
-        }
-      qr_bar();
-      float s = copysignf(sqrtf(p * p + q * q + r * r), p);
-      float xnorm = 0.f;
-      for (int k = m; k <= nn - 1; ++k) {
-        const bool three = k != nn - 1;
-        const bool has_next = k + 1 <= nn - 1;
-        float np = 0.f, nq = 0.f, nr = 0.f;
-        if (s != 0.f) {
-          const float ps = p + s;
-          // the values only locate the eigenvalues (refined in FP64 later):
-          // approximate reciprocals are enough
-          const float is = __fdividef(1.f, s), ip = __fdividef(1.f, ps);
-          const float xx = ps * is, yy = q * is, zz = r * is, qq = q * ip, rq = r * ip;
-          if (wrp == 0) {
-            if (lane == 0) {
-              if (k == m) {
-                if (l != m) HF(H, ldh, k, k - 1) = -HF(H, ldh, k, k - 1);
-              } else {
-                HF(H, ldh, k, k - 1) = -s * xnorm;
-              }
-            }
-            // the 4 x 4 region: row part on columns k..hc, column part on rows k..rb
-            const int hc = nn < k + 3 ? nn : k + 3;
-            const int rb = hc;
-            float bl[4][4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int c2 = 0; c2 < 4; ++c2)
-                bl[i][c2] = (k + i <= nn && k + c2 <= hc) ? HF(H, ldh, k + i, k + c2) : 0.f;
-#pragma unroll
-            for (int c2 = 0; c2 < 4; ++c2) {
-              if (k + c2 <= hc) {
-                const float a2 = three ? bl[2][c2] : 0.f;
-                const float pp = bl[0][c2] + qq * bl[1][c2] + rq * a2;
-                if (three) bl[2][c2] = a2 - pp * zz;
-                bl[1][c2] = bl[1][c2] - pp * yy;
-                bl[0][c2] = bl[0][c2] - pp * xx;
-              }
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              if (k + i <= rb) {
-                const float b2 = three ? bl[i][2] : 0.f;
-                const float pp = xx * bl[i][0] + yy * bl[i][1] + zz * b2;
-                if (three) bl[i][2] = b2 - pp * rq;
-                bl[i][1] = bl[i][1] - pp * qq;
-                bl[i][0] = bl[i][0] - pp;
-              }
-            }
-            __syncwarp();
-            if (lane == 0) {
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int c2 = 0; c2 < 4; ++c2)
-                  if (k + i <= nn && k + c2 <= hc) HF(H, ldh, k + i, k + c2) = bl[i][c2];
-            }
-            if (has_next) {
-              np = bl[1][0];
-              nq = bl[2][0];
-              nr = (k + 1 != nn - 1) ? bl[3][0] : 0.f;
-            }
-          } else if (wrp <= QR_RW) {
-            // row part on columns k+4..nn
-            const int off = 32 * (wrp - 1) + lane, stride = 32 * QR_RW;
-            if (nn - k - 4 < 64) {
-              row_update_range<1>(H, ldh, k, k + 4, nn, off, stride, three, qq, rq, xx, yy, zz);
-            } else {
-              row_update_range<(D_MAX + 32 * QR_RW - 1) / (32 * QR_RW)>(H, ldh, k, k + 4, nn, off, stride, three, qq,
-                                                                         rq, xx, yy, zz);
-            }
-          } else {
-            // column part on rows l..k-1
-            const int off = 32 * (wrp - 1 - QR_RW) + lane, stride = 32 * QR_CW;
-            if (k - 1 - l < 64) {
-              col_update<1>(H, ldh, k, l, k - 1, off, stride, three, qq, rq, xx, yy, zz);
-            } else {
-              col_update<(D_MAX + 32 * QR_CW - 1) / (32 * QR_CW)>(H, ldh, k, l, k - 1, off, stride, three, qq, rq,
-                                                                  xx, yy, zz);
-            }
-          }
-        } else if (wrp == 0 && has_next) {
-          np = HF(H, ldh, k + 1, k);
-          nq = HF(H, ldh, k + 2, k);
-          nr = (k + 1 != nn - 1) ? HF(H, ldh, k + 3, k) : 0.f;
-        }
-        float* slot = rs + 4 * (k & 1);
-        if (tid == 0) {
-          slot[0] = np;
-          slot[1] = nq;
-          slot[2] = nr;
-        }
-        qr_bar();
-        if (has_next) {
-          p = slot[0];
-          q = slot[1];
-          r = slot[2];
-          xnorm = fabsf(p) + fabsf(q) + fabsf(r);
-          if (xnorm != 0.f) {
-            const float inv = __fdividef(1.f, xnorm);
-            p *= inv;
-            q *= inv;
-            r *= inv;
-          }
-          const float ss = p * p + q * q + r * r;  // an approximate root is enough here
-          s = copysignf(ss > 0.f ? ss * rsqrtf(ss) : 0.f, p);
-        }
-      }
+      x = slot[0];
+      y = slot[1];
+      z = slot[2];
     }
   }
   return true;
@@ -886,7 +900,7 @@ __global__ void __launch_bounds__(512, 1) k_ce_eig(WS ws) {
   __syncthreads();
   __shared__ float rsl[8];
   if (threadIdx.x < 32 * QR_WARPS) {
-    const bool good = hqr_f32_2w(H, ldh, n, wr, wi, rsl);
+    const bool good = francis_eigenvalues(H, ldh, n, wr, wi, rsl);
     if (threadIdx.x == 0) ok = good ? 1 : 0;
   }
   __syncthreads();

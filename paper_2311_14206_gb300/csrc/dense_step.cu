@@ -294,13 +294,24 @@ __global__ void __launch_bounds__(DT) k_step_dense(WS ws, int j, int kh, int ubu
   }
   __syncthreads();
   // 4. QR update
+  const double sres_prev = c->sres;  // ||S r_{j-1}|| = ||z(p:s)||, kept by the previous step
   const double sres = qr_add_column(ws, p, sm, &rank_flag);
   for (int i = threadIdx.x; i < s; i += blockDim.x) ws.z[i] = sm.z[i];
   // 5. residual control (Algorithm 1): check the true residual when
   //    sres < tol / safety, at the last step, or after a breakdown.
   __shared__ int do_check;
   if (threadIdx.x == 0) {
-    if (c->hist_n < HIST_MAX) ws.hist[c->hist_n] = sres;
+    if (c->hist_n < HIST_MAX) {
+      ws.hist[c->hist_n] = sres;
+      // Givens sine and cosine of this step (Section 4.5, Theorem on Givens
+      // sines; Section 5): the reflector of column p maps z(p:s), of norm
+      // ||S r_{j-1}||, to (z_p, z(p+1:s)); a Givens QR of the whitened
+      // Hessenberg matrix produces the same pair, |c| = |z_p| / ||S r_{j-1}||
+      // and |s| = ||S r_j|| / ||S r_{j-1}||
+      const bool ok = sres_prev > 0.0;
+      ws.hist_givens[2 * c->hist_n] = ok ? sres / sres_prev : 0.0;
+      ws.hist_givens[2 * c->hist_n + 1] = ok ? fabs(sm.z[p]) / sres_prev : 0.0;
+    }
     c->hist_n += 1;
     c->sres = sres;
     c->step = j + 1;

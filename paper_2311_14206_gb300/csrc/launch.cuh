@@ -22,6 +22,8 @@ cudaError_t launch_sketch_vec(const WS& ws, const T* x, int64_t n, unsigned long
 // y = scale * acc * 2^(top-126) / sqrt(zeta) for s rows; zeroes acc.
 cudaError_t launch_sketch_finish(const WS& ws, unsigned long long* acc, const int* top_dev, double* y,
                                  cudaStream_t st);
+// cos(pi m / (2n)) for m = 0 .. n into tab (the DCT sketch's cosine table).
+cudaError_t launch_dct_table(double* tab, int64_t n, cudaStream_t st);
 // *top_dev = window for max|x| (reduction over x).
 template <typename T>
 cudaError_t launch_maxabs_top(const WS& ws, const T* x, int64_t n, int* top_dev, cudaStream_t st);

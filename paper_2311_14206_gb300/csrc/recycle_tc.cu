@@ -22,7 +22,8 @@
 //
 // One persistent CTA per SM (576 threads, warp-specialised):
 //   warp 17 (lane 0)   loads 128-row x 16-column tiles of W into shared memory
-//                      with cp.async.bulk (one copy per column segment);
+//                      with 2D TMA copies (cp.async.bulk.tensor): one copy per
+//                      chunk, from a tensor map over the V slab or over U;
 //   warps 8-15         quantise and split them into the seven fp16 digit planes
 //                      (K-major core matrices, no swizzle);
 //   warp 16 (lane 0)   issues the tcgen05.mma (M = 128, N = 224, K = 16) and
@@ -32,6 +33,8 @@
 //                      output columns), combine, round and store U_new.
 // Every wait on an mbarrier is bounded; a wait that runs out sets ctl->tc_error,
 // the CTA stops issuing work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
 #include "launch.cuh"
@@ -47,7 +50,7 @@ constexpr int TC_NC = 32;      // output columns per digit block of B (K_MAX)
 constexpr int TC_N = TC_DIG * TC_NC;        // 224: MMA N
 constexpr int TC_GROUPS = 2 * TC_DIG - 1;   // 13 digit-pair groups
 constexpr int TC_KPAD = D_MAX;              // 160: K extent of B
-constexpr int TC_NSTG = 3;                  // staging buffers (fp64 tiles)
+constexpr int TC_NSTG = 4;                  // staging buffers (fp64 tiles)
 constexpr int TC_NAB = 3;                   // digit-plane buffers
 constexpr int TC_TMEM_COLS = 512;
 constexpr int TC_THREADS = 576;             // 18 warps
@@ -68,8 +71,8 @@ constexpr int OFF_B = 0;
 constexpr int OFF_A = OFF_B + B_BYTES;
 constexpr int OFF_Z = OFF_A + TC_NAB * A_BUF_BYTES;
 constexpr int OFF_STG = OFF_Z + A_DIGIT_BYTES;
-constexpr int TC_SMEM = OFF_STG + TC_NSTG * STG_BYTES;  // 210,944
-static_assert(TC_SMEM <= 225 * 1024, "shared memory of the tensor-core recycle kernel");
+constexpr int TC_SMEM = OFF_STG + TC_NSTG * STG_BYTES + 128;  // + slack to align the base to 128 bytes
+static_assert(TC_SMEM + 1536 <= 227 * 1024, "shared memory of the tensor-core recycle kernel");
 constexpr long long TC_SPIN = 4000000000LL;  // clock cycles (about two seconds) per wait
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -115,10 +118,14 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, volatile 
   return true;
 }
 
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(saddr(bar))
-               : "memory");
+// 2D TMA copy of the box at (x = first row, y = first column) of a tensor map
+// into shared memory; rows and columns outside the map are filled with zeros.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
@@ -167,43 +174,56 @@ __device__ __forceinline__ uint32_t digit_pair_f16(uint32_t w0, uint32_t w1, int
   return r;
 }
 
-template <typename T>
-__device__ __forceinline__ const T* w_column(const T* U, const T* v0, const T* vs, int64_t ld, int kh, int l) {
-  return l < kh ? U + (int64_t)l * ld : (l == kh ? v0 : vs + (int64_t)(l - kh - 1) * ld);
-}
-
 __device__ __forceinline__ int column_delta(const Ctl* c, int ubuf, int kh, int l) {
   const unsigned long long mb = l < kh ? c->umax[ubuf][l] : c->vmax[l - kh];
   const int e = bexp_of_bits(mb);
   return e == 0 ? 0 : -(e - 1022);
 }
 
+// The K order of the MMA: nV chunks of 16 columns of the V slab (V(:, 0) is
+// copied into the slab's front column before the launch, so V(:, 0:jf) is
+// contiguous), then nU chunks of U.  Slot l' of that order holds column
+// wcol(l') of W = [U, V(:, 0:jf)], or nothing (-1) in the padding.
+__device__ __forceinline__ int slot_column(int lp, int nV, int kh, int jf) {
+  if (lp < nV * TC_KC) return lp < jf ? kh + lp : -1;
+  const int j = lp - nV * TC_KC;
+  return j < kh ? j : -1;
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_recycle_tc(WS ws, const double* __restrict__ U, const double* __restrict__ v0, const double* __restrict__ vs,
+    k_recycle_tc(WS ws, const __grid_constant__ CUtensorMap mapV, const __grid_constant__ CUtensorMap mapU,
                  double* __restrict__ Unew, int kh, int ucur, int unext) {
   Ctl* c = ws.ctl;
   const int kp = c->kprime, jf = c->jf;
   if (kp <= 0 || jf <= 0) return;
   const int d = kh + jf;
-  if (d > TC_KPAD || kp > TC_NC) {  // cannot happen (d <= K_MAX + M_MAX, kp <= K_MAX)
+  const int nV = (jf + TC_KC - 1) / TC_KC, nU = (kh + TC_KC - 1) / TC_KC;
+  if ((nV + nU) * TC_KC > TC_KPAD || kp > TC_NC) {  // cannot happen (jf <= M_MAX, kh <= K_MAX, kp <= K_MAX)
     if (threadIdx.x == 0 && blockIdx.x == 0) c->tc_error = 1;
     return;
   }
-  extern __shared__ __align__(128) unsigned char tc_smem[];
+  extern __shared__ __align__(128) unsigned char tc_raw[];
+  unsigned char* tc_smem = tc_raw + ((128u - (saddr(tc_raw) & 127u)) & 127u);  // 128-byte aligned (TMA)
   __shared__ __align__(8) uint64_t stg_full[TC_NSTG], stg_empty[TC_NSTG], a_full[TC_NAB], a_empty[TC_NAB];
   __shared__ __align__(8) uint64_t acc_full, acc_empty;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
-  __shared__ int dl[TC_KPAD];
+  __shared__ int dl[TC_KPAD];    // per K slot: 2^delta scale of its W column
+  __shared__ int slot_ok[TC_KPAD];
   __shared__ int fx[TC_NC];
   __shared__ unsigned int um_s[TC_NC];  // high words of max |U_new(:, q)| (only the exponent is used)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ld = ws.ldv, n = ws.n;
   const int64_t ntiles = (n + TC_M - 1) / TC_M;
-  const int nkc = (d + TC_KC - 1) / TC_KC;
+  const int nkc = nV + nU;
+  (void)d;
 
   // ---- set-up: scales, B = the seven digit planes of P'', the zero tile, barriers
-  for (int l = tid; l < TC_KPAD; l += blockDim.x) dl[l] = l < d ? column_delta(c, ucur, kh, l) : 0;
+  for (int lp = tid; lp < TC_KPAD; lp += blockDim.x) {
+    const int l = slot_column(lp, nV, kh, jf);
+    dl[lp] = l >= 0 ? column_delta(c, ucur, kh, l) : 0;
+    slot_ok[lp] = l >= 0 ? 1 : 0;
+  }
   for (int q = tid; q < TC_NC; q += blockDim.x) {
     fx[q] = q < kp ? ws.Pexp[q] : 0;
     um_s[q] = 0u;
@@ -211,9 +231,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   {
     uint16_t* B = (uint16_t*)(tc_smem + OFF_B);  // fp16 bit patterns
     for (int idx = tid; idx < TC_KPAD * TC_NC; idx += blockDim.x) {
-      const int l = idx / TC_NC, q = idx % TC_NC;
+      const int lp = idx / TC_NC, q = idx % TC_NC;
+      const int l = slot_column(lp, nV, kh, jf);
       long long v = 0;
-      if (l < d && q < kp) {
+      if (l >= 0 && q < kp) {
         const unsigned long long b = ws.Pq[l + (int64_t)q * D_MAX];  // packed (hi << 32) | lo, value hi 2^26 + lo
         v = (long long)(int)(b >> 32) * 67108864ll + (long long)(b & 0xFFFFFFFFull);
       }
@@ -221,7 +242,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int a = 0; a < TC_DIG; ++a) {
         const int row = TC_NC * a + q;  // B row: digit a of output column q
-        const int off = ((l >> 3) * B_ROWS_CM + (row >> 3)) * 64 + (row & 7) * 8 + (l & 7);
+        const int off = ((lp >> 3) * B_ROWS_CM + (row >> 3)) * 64 + (row & 7) * 8 + (lp & 7);
         const int digit = (int)((u >> (8 * a)) & 0xFF) - 128;
         B[off] = __half_as_ushort(__int2half_rn(digit));
       }
@@ -259,17 +280,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t sc = 0;
       const uint32_t stg0 = saddr(tc_smem + OFF_STG);
       for (int64_t tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
-        const int64_t r0 = tile * TC_M;
-        const int nr = (int)(n - r0 < TC_M ? n - r0 : TC_M);
-        const uint32_t seg = (uint32_t)((nr + 1) & ~1) * 8u;  // a 16-byte multiple (ld is a multiple of 32)
+        const int r0 = (int)(tile * TC_M);
         for (int kc = 0; kc < nkc; ++kc, ++sc) {
           const int slot = (int)(sc % TC_NSTG);
           if (!bar_wait(&stg_empty[slot], ((sc / TC_NSTG) & 1) ^ 1, &abort_flag)) break;
-          const int ncols = d - kc * TC_KC < TC_KC ? d - kc * TC_KC : TC_KC;
-          bar_arrive_tx(&stg_full[slot], seg * (uint32_t)ncols);
-          for (int i = 0; i < ncols; ++i)
-            bulk_g2s(stg0 + (uint32_t)(slot * STG_BYTES + i * STG_COL_BYTES),
-                     w_column(U, v0, vs, ld, kh, kc * TC_KC + i) + r0, seg, &stg_full[slot]);
+          bar_arrive_tx(&stg_full[slot], STG_BYTES);  // the whole box, out-of-range parts zero-filled
+          const uint32_t dst = stg0 + (uint32_t)(slot * STG_BYTES);
+          if (kc < nV)
+            tma_load_2d(dst, &mapV, r0, kc * TC_KC, &stg_full[slot]);
+          else
+            tma_load_2d(dst, &mapU, r0, (kc - nV) * TC_KC, &stg_full[slot]);
         }
       }
     }
@@ -288,9 +308,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint32_t ulo[8], uhi[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int cl = 8 * cg + i, l = kc * TC_KC + cl;
+          const int cl = 8 * cg + i, lp = kc * TC_KC + cl;
           long long v = 0;
-          if (l < d && r < nr) v = q52_value(stg[cl * TC_M + r], dl[l]);
+          if (slot_ok[lp] && r < nr) v = q52_value(stg[cl * TC_M + r], dl[lp]);
           const unsigned long long u = (unsigned long long)v + DIGIT_OFFSET;
           ulo[i] = (uint32_t)u;
           uhi[i] = (uint32_t)(u >> 32);
@@ -411,6 +431,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 }  // namespace
 
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+// 2D tensor map over n rows x cols columns (leading dimension ld) of float64,
+// boxes of 128 rows x 16 columns, no swizzle, zero fill outside.
+cudaError_t make_map(CUtensorMap* map, const double* base, int64_t n, int64_t cols, int64_t ld) {
+  if (!g_encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)cols};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(double)};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_M, (cuuint32_t)TC_KC};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)base, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+}  // namespace
+
 cudaError_t launch_recycle_tc(const WS& ws, const double* U, const double* v0, const double* vs, double* Unew,
                               int kh, int ucur, int unext, cudaStream_t st) {
   static bool attr = false;
@@ -419,10 +463,19 @@ cudaError_t launch_recycle_tc(const WS& ws, const double* U, const double* v0, c
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  // V(:, 0) into the slab's front column, so that the V part of W is one 2D array
+  double* front = (double*)vs - ws.ldv;
+  cudaError_t e = cudaMemcpyAsync(front, v0, (size_t)ws.n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  CUtensorMap mapV, mapU;
+  e = make_map(&mapV, front, ws.n, (int64_t)ws.m + 1, ws.ldv);
+  if (e != cudaSuccess) return e;
+  e = make_map(&mapU, U, ws.n, ws.kmax, ws.ldv);
+  if (e != cudaSuccess) return e;
   const int nsm = ws.grid_max / 8;
   const int64_t ntiles = (ws.n + TC_M - 1) / TC_M;
   const int grid = (int)(ntiles < nsm ? ntiles : nsm);
-  k_recycle_tc<<<grid > 0 ? grid : 1, TC_THREADS, TC_SMEM, st>>>(ws, U, v0, vs, Unew, kh, ucur, unext);
+  k_recycle_tc<<<grid > 0 ? grid : 1, TC_THREADS, TC_SMEM, st>>>(ws, mapV, mapU, Unew, kh, ucur, unext);
   return cudaGetLastError();
 }
 

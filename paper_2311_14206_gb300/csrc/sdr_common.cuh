@@ -86,6 +86,15 @@ struct WS {
   int64_t ldv;      // leading dimension of tall arrays (n_max rounded up to a multiple of 32)
   int m, k, t, s, zeta, kmax, dmax;
   int recycle_int;  // 1: the recycle product on the integer pipe instead of the tensor cores
+  // sketch family: 0 the sparse sign (hash-defined, zeta nonzeros per column);
+  // 1 the subsampled randomised DCT of the paper's experiments (Section 6),
+  // S = sqrt(n/s) P F E, defined for one system size dct_n
+  int sketch_kind;
+  int64_t dct_n;
+  const signed char* dct_sign;  // E: n random signs (+1 / -1)
+  const int* dct_k;             // P: the s selected DCT-II frequencies
+  const double* dct_cos;        // cos(pi m / (2n)), m = 0 .. n
+  const double* dct_scale;      // per row: sqrt(n/s) alpha_k (alpha_0 = 1/sqrt(n), else sqrt(2/n))
   uint64_t seed;
   double inv_sqrt_zeta;
   int win_bits;     // log2 bound on terms per sketch row (window headroom)
@@ -131,6 +140,7 @@ struct WS {
   int* yexp;     // [0]: exponent of y'' scale
   double* dscr;  // dense scratch for the cycle-end kernel
   double* hist;  // HIST_MAX sres values
+  double* hist_givens;  // 2 x HIST_MAX: Givens sine and cosine of each step (Section 4.5, Section 5)
   CycleLog* log; // LOG_MAX entries
   Ctl* ctl;
 };
@@ -243,6 +253,16 @@ __host__ __device__ inline int window_top(double bound, int win_bits) {
   int e;
   frexp(bound > 0.0 ? bound : 1e-300, &e);
   return e + win_bits + 2;
+}
+
+// Add a double d to a 128-bit accumulator counting in units of 2^(top - 126)
+// (rounded to the unit; |d| < 2^top by the choice of the window).
+__device__ inline void add_double128(unsigned long long& lo, unsigned long long& hi, double d, int top) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0 || ex == 0x7FF) return;  // zero (subnormals are below any unit here) or not finite
+  const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  add_shifted128(lo, hi, (b >> 63) ? -mant : mant, (ex - 1075) - (top - 126));
 }
 
 // ---------------------------------------------------------------------------
@@ -389,6 +409,45 @@ __device__ inline void tile_sketch_accumulate(const WS& ws, int ncols, double* v
         a += (c & 0x8000) ? -v : v;
       }
       add_shifted128(lo[k], hi[k], a, sh);
+    }
+  }
+  __syncthreads();
+}
+
+// The same for the subsampled randomised DCT (sketch_kind 1; Section 6): row r
+// of S x is dct_scale[r] sum_i E_i x_i cos(pi (2i + 1) k_r / (2n)).  Each
+// thread forms the tile's partial sum of each of its rows in FP64, in index
+// order (so the result does not depend on the grid), and adds it to its
+// 128-bit accumulators.  The cosine comes from the table of cos(pi m / (2n)),
+// m = 0 .. n, by the symmetries of cos over [0, 4n).  vals holds the tile
+// (zero beyond ncols) and is overwritten; all threads of the block call it.
+template <int RPT>
+__device__ inline void tile_dct_accumulate(const WS& ws, int64_t r0, int ncols, double* vals, int top,
+                                           unsigned long long* lo, unsigned long long* hi) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < ncols; i += blockDim.x)
+    if (ws.dct_sign[r0 + i] < 0) vals[i] = -vals[i];
+  __syncthreads();
+  const unsigned int n = (unsigned int)ws.dct_n, n2 = 2u * n, n4 = 4u * n;  // n < 2^29 (checked on the host)
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int row = threadIdx.x + k * blockDim.x;
+    if (row < ws.s) {
+      const unsigned long long f = (unsigned long long)ws.dct_k[row];
+      unsigned int m = (unsigned int)(((2ull * (unsigned long long)r0 + 1ull) * f) % n4);  // (2i + 1) f mod 4n
+      const unsigned int step = (unsigned int)((2ull * f) % n4);
+      double acc0 = 0.0, acc1 = 0.0;
+      for (int i = 0; i < ncols; ++i) {
+        const unsigned int a = m > n2 ? n4 - m : m;  // cos(pi a / 2n) = cos(pi m / 2n)
+        const double cv = a > n ? -__ldg(ws.dct_cos + (n2 - a)) : __ldg(ws.dct_cos + a);
+        if (i & 1)
+          acc1 = fma(vals[i], cv, acc1);
+        else
+          acc0 = fma(vals[i], cv, acc0);
+        m += step;
+        if (m >= n4) m -= n4;
+      }
+      add_double128(lo[k], hi[k], (acc0 + acc1) * ws.dct_scale[row], top);
     }
   }
   __syncthreads();

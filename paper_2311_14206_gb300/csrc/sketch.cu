@@ -110,9 +110,12 @@ __global__ void k_sketch_vec(WS ws, const T* __restrict__ x, int64_t n, unsigned
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = (int64_t)tile * tileR;
     const int ncols = (int)(n - r0 < (int64_t)tileR ? n - r0 : (int64_t)tileR);
-    tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
+    if (!ws.sketch_kind) tile_sketch_prefetch(ws, tileR, tile, ent_s, ptr_s);
     for (int i = threadIdx.x; i < tileR; i += blockDim.x) vals[i] = i < ncols ? (double)x[r0 + i] : 0.0;
-    tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, red, top, lo, hi);
+    if (ws.sketch_kind)
+      tile_dct_accumulate<SK_RPT>(ws, r0, ncols, vals, top, lo, hi);
+    else
+      tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, red, top, lo, hi);
   }
 #pragma unroll
   for (int k = 0; k < SK_RPT; ++k) {
@@ -192,6 +195,19 @@ cudaError_t launch_maxabs_top(const WS& ws, const T* x, int64_t n, int* top_dev,
   if (grid > ws.grid_max) grid = ws.grid_max;
   if (grid < 1) grid = 1;
   k_maxabs_top<T><<<grid, 256, 0, st>>>(ws, x, n, scratch, top_dev);
+  return cudaGetLastError();
+}
+
+// Cosine table of the DCT sketch: tab[m] = cos(pi m / (2n)), m = 0 .. n.
+__global__ void k_dct_table(double* tab, int64_t n) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m <= n; m += (int64_t)gridDim.x * blockDim.x)
+    tab[m] = cospi((double)m / (double)(2 * n));
+}
+
+cudaError_t launch_dct_table(double* tab, int64_t n, cudaStream_t st) {
+  int64_t g = (n + 256) / 256;
+  if (g > 4096) g = 4096;
+  k_dct_table<<<(int)g, 256, 0, st>>>(tab, n);
   return cudaGetLastError();
 }
 

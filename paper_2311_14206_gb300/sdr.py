@@ -26,7 +26,7 @@ class sdr_params(ctypes.Structure):
                 ("zeta", ctypes.c_int32), ("seed", ctypes.c_uint64), ("rel_tol", ctypes.c_double),
                 ("safety0", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("persist_safety", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("test_flags", ctypes.c_int32), ("inner_rel_tol", ctypes.c_double),
-                ("stale_check", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("stale_check", ctypes.c_int32), ("sketch_kind", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 SDR_PREC_F64 = 0
@@ -94,6 +94,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sdr_sketch_noalloc": ([vp, i64, i32, i32, ctypes.c_uint64, vp, vp], i32),
         "sdr_get_history": ([vp, P(ctypes.c_double), i32, P(i32), P(sdr_cycle_log), i32, P(i32)], i32),
         "sdr_recycle_dim": ([vp, P(i32)], i32),
+        "sdr_get_givens": ([vp, P(ctypes.c_double), P(ctypes.c_double), i32, P(i32)], i32),
+        "sdr_set_sketch_draws": ([vp, i64, vp, vp], i32),
         "sdr_recycle_export": ([vp, i64, vp, vp, vp], i32),
         "sdr_recycle_import": ([vp, P(sdr_csr), i64, i32, vp, vp, vp], i32),
         "sdr_profile": ([vp, i32], i32),
@@ -169,12 +171,13 @@ class CSRDevice:
 
 def make_params(m, k, t, s, zeta, seed, rel_tol, safety0=1.4, max_cycles=200, persist_safety=0,
                 force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0, graphs=True,
-                stale_check=False, integer_recycle=False) -> sdr_params:
+                stale_check=False, integer_recycle=False, sketch_kind=0) -> sdr_params:
     p = sdr_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety)
     p.precision = precision
     p.test_flags = (1 if force_svd else 0) | (0 if graphs else 2) | (4 if integer_recycle else 0)
     p.inner_rel_tol = inner_rel_tol
     p.stale_check = 1 if stale_check else 0
+    p.sketch_kind = sketch_kind
     return p
 
 
@@ -272,6 +275,26 @@ def sdr_get_history(h, cap_steps=1 << 15, cap_cycles=512):
     return list(sres[:min(ns.value, cap_steps)]), log
 
 
+def sdr_set_sketch_draws(h, signs, rows):
+    """Random draws of a DCT-sketch handle: signs (n values +-1) and rows (s
+    strictly increasing frequencies), host arrays."""
+    import numpy as np
+    sg = np.ascontiguousarray(np.asarray(signs), dtype=np.int8)
+    rw = np.ascontiguousarray(np.asarray(rows), dtype=np.int32)
+    _check(load_library().sdr_set_sketch_draws(h, sg.size, sg.ctypes.data_as(ctypes.c_void_p),
+                                               rw.ctypes.data_as(ctypes.c_void_p)), "sdr_set_sketch_draws")
+
+
+def sdr_get_givens(h, cap_steps=1 << 15):
+    """(sines, cosines) of the Givens rotations of every Arnoldi step of the last solve."""
+    s = (ctypes.c_double * cap_steps)()
+    c = (ctypes.c_double * cap_steps)()
+    n = ctypes.c_int32()
+    _check(load_library().sdr_get_givens(h, s, c, cap_steps, ctypes.byref(n)), "sdr_get_givens")
+    k = min(n.value, cap_steps)
+    return list(s[:k]), list(c[:k])
+
+
 def sdr_recycle_dim(h) -> int:
     k = ctypes.c_int32()
     _check(load_library().sdr_recycle_dim(h, ctypes.byref(k)), "sdr_recycle_dim")
@@ -331,9 +354,9 @@ class Solver:
 
     def __init__(self, n_max, m, k, t, s, zeta=8, seed=231114206, rel_tol=1e-8, safety0=1.4, max_cycles=200,
                  persist_safety=0, force_svd=False, precision=SDR_PREC_F64, inner_rel_tol=0.0, graphs=True,
-                 stream=None, stale_check=False, integer_recycle=False):
+                 stream=None, stale_check=False, integer_recycle=False, sketch_kind=0):
         self.params = make_params(m, k, t, s, zeta, seed, rel_tol, safety0, max_cycles, persist_safety, force_svd,
-                                  precision, inner_rel_tol, graphs, stale_check, integer_recycle)
+                                  precision, inner_rel_tol, graphs, stale_check, integer_recycle, sketch_kind)
         self.n_max, self.s = n_max, s
         self.stream = stream  # a torch.cuda.Stream the handle issues on (None: the current stream)
         self.h = sdr_create(self.params, n_max,
@@ -347,6 +370,12 @@ class Solver:
 
     def recycle(self, A_next=None, mode=0):
         return sdr_recycle(self.h, A_next, mode)
+
+    def set_sketch_draws(self, signs, rows):
+        """DCT-sketch handles: the random signs (n of them) and the s selected rows."""
+        if len(rows) != self.s:
+            raise SdrError(1, f"set_sketch_draws: {len(rows)} rows for s = {self.s}")
+        sdr_set_sketch_draws(self.h, signs, rows)
 
     def history(self):
         return sdr_get_history(self.h)

@@ -361,3 +361,36 @@ def test_recycle_product_tensor_cores_bit_identical(P, side, m, k, s, tol, maxc)
     ref = osdr.solve(A, b, SparseSign(SEED, A.n, s, 8), m=m, k=k, t=2, rel_tol=tol, max_cycles=maxc)
     assert np.linalg.norm(x0 - ref.x) / np.linalg.norm(ref.x) <= 1e-6
     assert abs(s0["cycles"] - ref.cycles) <= 1
+
+
+# ------------------------------------------------------- Givens-sine estimator
+def test_givens_sines_match_oracle(P):
+    """Per-step Givens sines and cosines of the GPU's cycles (read off its QR of
+    SAW) against the oracle's Section 5 construction (QR of [SAU, SV], G, Givens
+    rotations) for the first two cycles of the 64 x 64 workload; the second
+    cycle is augmented (k recycled columns).  Bars: |ds| <= 1e-8 s + 1e-12 and
+    |dc| <= 1e-7 c + 1e-10 (c = sqrt(1 - s^2) amplifies the error of s when s
+    is close to one)."""
+    from oracle import givens as G
+    A = W.make_cd2d(64, (10.0, 10.0))
+    b = W.rhs(A.n)
+    m, k, t, s, zeta, tol = 50, 10, 2, 120, 8, 1e-8
+    solver = P.Solver(A.n, m, k, t, s, zeta, SEED, tol)
+    x, st, stats = solver.solve(P.CSRDevice.from_numpy(A), dev(b))
+    sines, cosines = P.sdr_get_givens(solver.h)
+    sres, log = solver.history()
+    solver.close()
+    assert len(sines) == len(sres)
+    ref = osdr.solve(A, b, SparseSign(SEED, A.n, s, zeta), m=m, k=k, t=t, rel_tol=tol, record=True)
+    off = 0
+    for cyc, g in zip(ref.cycle_log[:2], log[:2]):
+        info = cyc.info
+        rs, rc, rsres = G.givens_sines(info["SAU_in"], info["SV"], info["H"], info["beta"])
+        n = min(len(rs), g["steps"])
+        gs, gc = np.asarray(sines[off:off + n]), np.asarray(cosines[off:off + n])
+        assert np.all(np.abs(gs - rs[:n]) <= 1e-8 * rs[:n] + 1e-12), (off, np.max(np.abs(gs - rs[:n])))
+        assert np.all(np.abs(gc - rc[:n]) <= 1e-7 * rc[:n] + 1e-10), (off, np.max(np.abs(gc - rc[:n])))
+        # the Theorem's recurrence on the GPU's own numbers
+        prev = np.concatenate([[gs[0] and sres[off] / gs[0]], sres[off:off + n - 1]])
+        assert np.allclose(np.asarray(sres[off:off + n]), gs * prev, rtol=1e-12)
+        off += g["steps"]

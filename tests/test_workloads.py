@@ -161,3 +161,15 @@ def test_vcdiff_torch_values_match_numpy_and_differentiate():
         e[c] = 1e-6
         fd = (W.make_vcdiff(n, theta + e).val - W.make_vcdiff(n, theta - e).val) @ u / 2e-6
         assert g[c].item() == pytest.approx(fd, rel=1e-6)
+
+
+def test_dct_draws_are_the_oracle_sketch_draws():
+    """The DCT sketch's random signs and rows handed to the library are the ones
+    the oracle's SubsampledDCT draws for the same (seed, n, s)."""
+    from oracle.sketch import SubsampledDCT
+    for seed, n, s in ((231114206, 4096, 120), (7, 250000, 480), (1, 1001, 37)):
+        signs, rows = W.dct_draws(seed, n, s)
+        S = SubsampledDCT(seed, n, s)
+        assert np.array_equal(signs.astype(np.float64), S.signs)
+        assert np.array_equal(rows.astype(np.int64), S.rows)
+        assert np.all(np.diff(rows) > 0) and rows[0] >= 0 and rows[-1] < n

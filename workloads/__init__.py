@@ -24,4 +24,5 @@ from .configs import (  # noqa: F401
     theta_field,
     target_field,
     batch_systems,
+    dct_draws,
 )

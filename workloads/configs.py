@@ -70,6 +70,16 @@ def batch_systems(count: int = 64, nmin: int = 32, nmax: int = 512, seed: int = 
     return [(int(n), (float(c[0]), float(c[1]))) for n, c in zip(sides, conv)]
 
 
+def dct_draws(seed: int, n: int, s: int):
+    """Random draws of the subsampled randomised DCT sketch of the paper's
+    experiments (Section 6): n signs +-1 and s distinct rows sorted
+    increasingly, from PCG64 seeded [seed, n, s] (signs first, then rows)."""
+    g = np.random.default_rng([seed, n, s])
+    signs = g.choice(np.array([-1.0, 1.0]), n)
+    rows = np.sort(g.choice(n, s, replace=False))
+    return signs.astype(np.int8), rows.astype(np.int32)
+
+
 def vcdiff_problem(n: int, sd: float = 0.5, conv=(10.0, 10.0)):
     theta = theta_field(n, sd)
     return make_vcdiff(n, theta, conv), theta
