@@ -578,6 +578,86 @@ def run_form_batch(args):
         clocks=b_["clocks"])
 
 
+# --------------------------------------------------------------------------- the paper's Section 6.3 experiment
+PAPER_CD = dict(workload="cd_paper_section_6_3", n=500, alpha=(0.0, 5.0, 20.0), m=80, k=20, t=2, s=480, zeta=8,
+                rel_tol=1e-2, max_cycles=10, seed=231114206)
+# the counts of the paper's table for this experiment (MATLAB, DCT sketch with s = 640), context only
+PAPER_CD_TABLE = dict(gmres_sdr_exact=1971, gmres_sdr_inexact=1886)
+
+
+def run_form_paper_cd(args):
+    """The paper's Section 6.3 sequence (three 2D convection-diffusion problems,
+    n = 500, alpha = 0, 5, 20, b = ones, 80 Arnoldi steps + 20 recycled, at most
+    10 restarts, target 1e-2 relative) through the C ABI: exact recycling, the
+    inexact variant and the inexact variant with the stale-SAU rule, with the
+    sparse sign and with the paper's subsampled DCT (s = 480).  Reports products
+    with A (Arnoldi steps + true-residual checks + the k products of each exact
+    recycle, counted as the paper counts matrix-vector products) and the time
+    per problem, beside the oracle's counts for the same runs."""
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_2311_14206_gb300 as P
+
+    cfg = PAPER_CD
+    As = [W.make_cd_paper(cfg["n"], a) for a in cfg["alpha"]]
+    N = As[0].n
+    mats = [P.CSRDevice.from_numpy(A) for A in As]
+    b = torch.ones(N, dtype=torch.float64, device="cuda")
+    gold = {}
+    for sk, fname in (("sparse_sign", "paper_cd_sparse_sign_s480.json"), ("dct", "paper_cd_dct_s480.json")):
+        path = os.path.join(ROOT, "tests", "golden", fname)
+        if os.path.exists(path):
+            with open(path) as f:
+                gold[sk] = json.load(f)["variants"]
+    runs = {}
+    for sk in ("sparse_sign", "dct"):
+        for variant in ("exact", "inexact", "inexact_stale_check"):
+            if sk == "dct" and variant == "inexact_stale_check":
+                continue
+            solver = P.Solver(N, cfg["m"], cfg["k"], cfg["t"], cfg["s"], cfg["zeta"], cfg["seed"], cfg["rel_tol"],
+                              max_cycles=cfg["max_cycles"], stale_check=variant == "inexact_stale_check",
+                              sketch_kind=1 if sk == "dct" else 0)
+            if sk == "dct":
+                solver.set_sketch_draws(*W.dct_draws(cfg["seed"], N, cfg["s"]))
+            probs, total_mv, total_ms = [], 0, 0.0
+            for rep in range(2):  # the first pass captures the cycle graphs
+                probs, total_mv, total_ms = [], 0, 0.0
+                solver.recycle(None, 2)
+                for i, Ad in enumerate(mats):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    extra = 0
+                    if i > 0:
+                        kd = P.sdr_recycle_dim(solver.h)
+                        solver.recycle(Ad, 0 if variant == "exact" else 1)
+                        extra = kd if variant == "exact" else 0
+                    x, st, stats = solver.solve(Ad, b)
+                    torch.cuda.synchronize()
+                    ms = 1e3 * (time.perf_counter() - t0)
+                    mv = stats["arnoldi_steps"] + stats["true_res_evals"] + extra + stats["refresh_matvecs"]
+                    probs.append(dict(converged=bool(stats["converged"]), cycles=stats["cycles"], matvecs=mv,
+                                      rel_res=stats["final_rel_res"], ms=ms, sau_refreshes=stats["sau_refreshes"]))
+                    total_mv += mv
+                    total_ms += ms
+            solver.close()
+            ref = gold.get(sk, {}).get(variant)
+            runs[f"{sk}/{variant}"] = dict(
+                problems=probs, total_matvecs=total_mv, total_ms=total_ms,
+                oracle_total_matvecs=ref["total_matvecs"] if ref else None,
+                oracle_converged=[r_["converged"] for r_ in ref["problems"]] if ref else None)
+    ex = runs["sparse_sign/exact"]
+    return dict(
+        metric="Section 6.3 sequence: time per problem and products with A", value=ex["total_ms"] / 3.0,
+        unit="ms/system", n_gpus=1, steps=1, warmup=1, ms_per_step=ex["total_ms"], higher_is_better=False,
+        scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+        config=dict(workload=cfg["workload"], N=N, m=cfg["m"], k=cfg["k"], t=cfg["t"], s=cfg["s"],
+                    zeta=cfg["zeta"], rel_tol=cfg["rel_tol"], max_cycles=cfg["max_cycles"],
+                    timing="host wall clock per problem (each solve synchronises every cycle), second pass"),
+        runs=runs, paper_table_matvecs=PAPER_CD_TABLE,
+        note="the paper's counts were taken in MATLAB with a DCT sketch of s = 640; context, not a target")
+
+
 # --------------------------------------------------------------------------- oracle arm
 # Arnoldi steps of the bounded oracle sample: about 10-15 s of one host core on the GPU box.
 # The oracle's cost per step grows with the steps of its cycle (its basis is an N x (m+1)
@@ -686,7 +766,8 @@ def main():
                     "(for profiler captures; the bench line names it)")
     ap.add_argument("--systems", type=int, default=0, help="systems of the sequence kept on the device")
     ap.add_argument("--workload", default=WORKLOAD["workload"],
-                    choices=[WORKLOAD["workload"], F32IR["workload"], ADJ["workload"], BATCH["workload"]])
+                    choices=[WORKLOAD["workload"], F32IR["workload"], ADJ["workload"], BATCH["workload"],
+                             PAPER_CD["workload"]])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -701,10 +782,10 @@ def main():
         torch.distributed.init_process_group("nccl")
     import __graft_entry__ as g
     g.build()
-    if args.workload in (F32IR["workload"], ADJ["workload"], BATCH["workload"]):
+    if args.workload in (F32IR["workload"], ADJ["workload"], BATCH["workload"], PAPER_CD["workload"]):
         if rank == 0:
             fn = {F32IR["workload"]: run_form_f32ir, ADJ["workload"]: run_form_adjoint,
-                  BATCH["workload"]: run_form_batch}[args.workload]
+                  BATCH["workload"]: run_form_batch, PAPER_CD["workload"]: run_form_paper_cd}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     res = run_gpu(args, rank, world)

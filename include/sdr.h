@@ -151,7 +151,7 @@ typedef struct {
   int32_t kernel_launches; /* kernels of this library launched by the call */
   int32_t refinements;     /* SDR_PREC_F32_REFINED: float64 refinement steps (0 otherwise) */
   int32_t sau_refreshes;   /* stale_check: SAU recomputations the rule triggered */
-  int32_t pad0;
+  int32_t refresh_matvecs; /* products with A those recomputations took (in matvecs) */
   double final_res;        /* last true residual norm */
   double tol;              /* rel_tol * ||b|| */
   double final_rel_res;    /* final_res / ||b|| */

@@ -558,7 +558,7 @@ sdr_status launch_cycle(CycleRun<T>& r) {
 // copied to the pinned host copy (read by run_complete_init).
 template <typename T>
 sdr_status run_begin(CycleRun<T>& r, sdr_handle* h, const CsrDev& Ad, const T* b, T* x, double rel_tol,
-                     int max_cycles) {
+                     int max_cycles, bool keep_logs = false) {
   r.h = h;
   r.ws = h->ws;
   r.ws.n = Ad.n;
@@ -573,7 +573,7 @@ sdr_status run_begin(CycleRun<T>& r, sdr_handle* h, const CsrDev& Ad, const T* b
   r.converged = false;
   r.status = SDR_OK;
   unsigned long long* accR = r.ws.acc + 2 * S_MAX;
-  SDR_LAUNCH(h, SDR_K_SOLVE_INIT, launch_solve_init_x<T>(r.ws, Ad, b, x, rel_tol, h->st));
+  SDR_LAUNCH(h, SDR_K_SOLVE_INIT, launch_solve_init_x<T>(r.ws, Ad, b, x, rel_tol, h->st, keep_logs));
   SDR_LAUNCH(h, SDR_K_RESIDUAL0, launch_residual<T>(r.ws, Ad, b, x, (T*)r.ws.R[0], accR, -1, 0, h->st));
   SDR_CK(cudaMemcpyAsync(h->hc, r.ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st));
   return SDR_OK;
@@ -640,8 +640,8 @@ sdr_status run_finish(CycleRun<T>& r) {
 // result.  tol = rel_tol ||b||.
 template <typename T>
 sdr_status run_cycles(sdr_handle* h, const CsrDev& Ad, const T* b, T* x, double rel_tol, int max_cycles,
-                      CycleRun<T>& r) {
-  sdr_status s = run_begin<T>(r, h, Ad, b, x, rel_tol, max_cycles);
+                      CycleRun<T>& r, bool keep_logs = false) {
+  sdr_status s = run_begin<T>(r, h, Ad, b, x, rel_tol, max_cycles, keep_logs);
   if (s == SDR_OK) s = run_complete_init<T>(r);
   while (s == SDR_OK && r.active) {
     s = run_issue<T>(r);
@@ -748,6 +748,7 @@ sdr_status solve_end(sdr_handle* h, const CycleRun<double>* run_f64, const Ctl& 
     stats->kernel_launches = h->launches;
     stats->refinements = refinements;
     stats->sau_refreshes = h->sau_refreshes;
+    stats->refresh_matvecs = h->extra_matvecs;
     stats->matvecs += h->extra_matvecs;
     stats->final_res = final_res;
     stats->tol = tol;
@@ -848,7 +849,7 @@ sdr_status sdr_solve(sdr_handle* h, const sdr_csr* A, const double* b, double* x
     SDR_LAUNCH(h, SDR_K_REFINE, launch_to_f32(r64, (float*)h->rhs32, (float*)h->dx32, Ad.n, st));
     run = CycleRun<float>();
     const sdr_status rs = run_cycles<float>(h, Ad, (const float*)h->rhs32, (float*)h->dx32, h->p.inner_rel_tol,
-                                            h->p.max_cycles, run);
+                                            h->p.max_cycles, run, /*keep_logs=*/true);
     if (rs != SDR_OK) return rs;
     cycles += run.cycles;
     full_svd += run.full_svd;

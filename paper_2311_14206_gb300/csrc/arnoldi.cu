@@ -123,7 +123,8 @@ __device__ inline unsigned long long reduce_parts_max(const double* part, int nb
 // Solve start: ||b||, max|b|, max|x0|, ||A||_inf, tol.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_solve_init(WS ws, CsrDev A, const T* __restrict__ b, const T* __restrict__ x, double rel_tol) {
+__global__ void k_solve_init(WS ws, CsrDev A, const T* __restrict__ b, const T* __restrict__ x, double rel_tol,
+                             int keep_logs) {
   __shared__ double red[32];
   __shared__ unsigned long long redu[32];
   double bb = 0.0;
@@ -164,10 +165,12 @@ __global__ void k_solve_init(WS ws, CsrDev A, const T* __restrict__ b, const T* 
       c->bmax = __longlong_as_double((long long)m1);
       c->xmax = m2;
       c->anorm_inf = __longlong_as_double((long long)m3);
-      c->hist_n = 0;
-      c->log_n = 0;
-      c->matvecs = 0;
-      c->sketches = 0;
+      if (!keep_logs) {  // a refinement's inner solve appends to the outer solve's logs and counts
+        c->hist_n = 0;
+        c->log_n = 0;
+        c->matvecs = 0;
+        c->sketches = 0;
+      }
       c->done = 0;
       c->converged = 0;
       c->check = 0;
@@ -183,8 +186,9 @@ static int grid_rows(int64_t n, int tpb, int gmax) {
 }
 
 template <typename T>
-cudaError_t launch_solve_init_x(const WS& ws, CsrDev A, const T* b, const T* x, double rel_tol, cudaStream_t st) {
-  k_solve_init<T><<<grid_rows(A.n, 256, ws.grid_max), 256, 0, st>>>(ws, A, b, x, rel_tol);
+cudaError_t launch_solve_init_x(const WS& ws, CsrDev A, const T* b, const T* x, double rel_tol, cudaStream_t st,
+                                bool keep_logs) {
+  k_solve_init<T><<<grid_rows(A.n, 256, ws.grid_max), 256, 0, st>>>(ws, A, b, x, rel_tol, keep_logs ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -1119,7 +1123,7 @@ cudaError_t launch_add_f32(double* x64, const float* d32, int64_t n, cudaStream_
 }
 
 #define SDR_INSTANTIATE_ARNOLDI(T)                                                                          \
-  template cudaError_t launch_solve_init_x<T>(const WS&, CsrDev, const T*, const T*, double, cudaStream_t);   \
+  template cudaError_t launch_solve_init_x<T>(const WS&, CsrDev, const T*, const T*, double, cudaStream_t, bool); \
   template cudaError_t launch_residual<T>(const WS&, CsrDev, const T*, const T*, T*, unsigned long long*, int, \
                                           int, cudaStream_t);                                                 \
   template cudaError_t launch_spmv_dots<T>(const WS&, CsrDev, const T* const*, int, cudaStream_t);            \

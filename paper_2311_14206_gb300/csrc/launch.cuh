@@ -32,7 +32,8 @@ cudaError_t launch_maxabs_top(const WS& ws, const T* x, int64_t n, int* top_dev,
 // Solve start: ||b||, max|b|, ||A||_inf, tol into ctl.
 // Tall vectors hold T (double, or float for the refined form's inner solver).
 template <typename T>
-cudaError_t launch_solve_init_x(const WS& ws, CsrDev A, const T* b, const T* x, double rel_tol, cudaStream_t st);
+cudaError_t launch_solve_init_x(const WS& ws, CsrDev A, const T* b, const T* x, double rel_tol, cudaStream_t st,
+                                bool keep_logs = false);
 // r = b - A x into rout; ||r||, max|r| into ctl (res, rmax); S r into accR (window from
 // ctl bmax + anorm_inf * xmax_bits).  mode 0: unconditional (solve start, x = x0);
 // mode 1: only when ctl->check, and the last CTA applies the residual control.

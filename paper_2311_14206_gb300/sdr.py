@@ -43,7 +43,7 @@ class sdr_stats(ctypes.Structure):
                 ("sketches", ctypes.c_int32), ("true_res_evals", ctypes.c_int32), ("arnoldi_steps", ctypes.c_int32),
                 ("recycle_dim", ctypes.c_int32), ("full_svd_cycles", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int32), ("refinements", ctypes.c_int32),
-                ("sau_refreshes", ctypes.c_int32), ("pad0", ctypes.c_int32), ("final_res", ctypes.c_double),
+                ("sau_refreshes", ctypes.c_int32), ("refresh_matvecs", ctypes.c_int32), ("final_res", ctypes.c_double),
                 ("tol", ctypes.c_double), ("final_rel_res", ctypes.c_double), ("bnorm", ctypes.c_double)]
 
     def as_dict(self):

@@ -15,7 +15,8 @@ outputs it computes within seconds, and properties that hold at any size:
     of SAU against S (A_next u) formed by the oracle's matvec and sketch;
   * the next system's first 12 sketched residuals against the oracle's cycle
     started from the recycle space the GPU handed over.
-This file runs last: it holds about 2 GB of device memory for its handle.
+This file runs near the end of the suite: it holds about 2 GB of device memory
+for its handle.
 """
 import numpy as np
 import pytest
