@@ -12,10 +12,12 @@
 //   ||R||_F ||R^{-1}||_F < 1/(d eps) implies sigma_i > sigma_1 d eps for all i.
 // Otherwise a one-sided Jacobi SVD of R gives the truncated problem.
 //
-// Eigenpairs: Householder reduction to Hessenberg form, Francis double-shift
-// QR for the eigenvalues, inverse iteration with the Hessenberg matrix for the
-// selected eigenvectors, back-transformation, and an orthonormal real basis of
-// their span (real and imaginary parts of complex pairs).
+// Eigenpairs: FP32 Householder reduction to Hessenberg form and Francis
+// double-shift QR for candidate eigenvalues; for each candidate an FP64
+// eigenpair of M from FP32 factorisations with FP64 residuals (inverse
+// iteration, then the refinement of Dongarra, Moler and Wilkinson); the
+// selection of the k largest |mu|, and an orthonormal real basis of the span
+// of their eigenvectors (real and imaginary parts of complex pairs).
 #include <cooperative_groups.h>
 
 #include "launch.cuh"
@@ -28,7 +30,7 @@ constexpr int KC_MARGIN = 8;      // extra eigenvalue candidates beyond k
 constexpr int KC = K_MAX + KC_MARGIN + 1;  // candidates refined in FP64
 
 struct CeLayout {
-  double *C, *Rinv, *M, *Hc, *Vh, *As, *tauH, *wr, *wi, *Zr, *Pu, *colsq, *misc, *lu;
+  double *C, *Rinv, *M, *Hc, *Vh, *As, *tauH, *wr, *wi, *Zr, *Pu, *colsq, *misc;
   double *cmu, *cref, *cvec;  // candidate estimates, FP64 eigenvalues, FP64 vectors (re, im)
   int* sel;   // [K_MAX] eigenvalue index per inverse iteration
   int* zcol;  // [K_MAX] first Z column of that eigenvalue
@@ -57,13 +59,12 @@ __host__ __device__ inline CeLayout ce_layout(double* base) {
   L.cmu = L.misc + 64 + 3 * K_MAX;
   L.cref = L.cmu + 2 * KC;
   L.cvec = L.cref + 2 * KC;
-  L.lu = L.cvec + (int64_t)2 * KC * LDD;  // KC blocks of 2*LDD*LDD (complex LU)
   return L;
 }
 
 size_t ce_scratch_doubles() {
   return (size_t)6 * LDD * LDD + 3 * LDD + 2 * (size_t)LDD * K_MAX + 2 * LDD + 64 + 3 * K_MAX + 4 * KC +
-         (size_t)2 * KC * LDD + (size_t)KC * 2 * LDD * LDD + 64;
+         (size_t)2 * KC * LDD + 64;
 }
 
 // Column l of S[U V] / SAW (sketched basis / sketched image).
@@ -952,141 +953,177 @@ __global__ void __launch_bounds__(512, 1) k_ce_eig(WS ws) {
 size_t ce_eig_smem() { return ((size_t)(D_MAX + 1) * D_MAX + 2 * D_MAX + 64) * sizeof(float); }
 
 // ---------------------------------------------------------------------------
-// FP64 eigenpair of M for one candidate (one CTA each): LU with partial
-// pivoting of M - mu0 I (complex when Im mu0 != 0), three steps of inverse
-// iteration, and the Rayleigh quotient mu = x^H M x / x^H x.
+// FP64 eigenpair of M for one candidate mu0 (one CTA each), with every
+// dependent chain in FP32 and only independent row products in FP64 (a
+// full-warp FP64 instruction holds an SM sub-partition for tens of cycles on
+// this GPU, so a scalar FP64 chain, as in an FP64 LU, is slow):
+//  1. inverse iteration with the FP32 LU (partial pivoting) of M - mu0 I from
+//     x = (1, ..., 1): IV_STEPS solves give x0 to FP32 accuracy;
+//  2. x0 scaled to x0(s) = 1 at an entry s of largest magnitude, and lambda0
+//     the FP64 Rayleigh quotient x0^H M x0 / x0^H x0;
+//  3. the refinement of Dongarra, Moler and Wilkinson (Improving the accuracy
+//     of computed eigenvalues and eigenvectors, SIAM J. Numer. Anal. 20,
+//     1983): Newton's method for (M - lambda I) x = 0 with x(s) = 1, whose
+//     Jacobian is M - lambda I with column s replaced by -x, frozen at
+//     (lambda0, x0) and factored once in FP32.  Each step computes the FP64
+//     residual r = lambda x - M x, solves B z = r with the FP32 factors and
+//     sets x(i) += z(i) (i != s), lambda += z(s); the FP64 residual carries
+//     the accuracy.  The pair with the smallest max |r| seen is kept.
+// M is scaled by a power of two 2^-e (exact) before rounding to FP32.
 // ---------------------------------------------------------------------------
-struct cplx { double re, im; };
-__device__ inline cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-__device__ inline cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
-// 1 / d for a complex d: conj(d) / |d|^2 with |d|^2 scaled into range by a
-// power of two and its reciprocal from an FP32 estimate refined by two Newton
-// steps r <- r (2 - q r) (an FP64 division is a long instruction sequence on
-// this GPU; these are a few dependent FMAs).
-__device__ inline cplx crecip(cplx d) {
-  const double m = fmax(fabs(d.re), fabs(d.im));
-  if (!(m > 0.0) || !isfinite(m)) return cplx{0.0, 0.0};
-  const int e = (int)(((unsigned long long)__double_as_longlong(m) >> 52) & 0x7FF) - 1023;
-  const int ec = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
-  const double sc = __longlong_as_double((long long)((unsigned long long)(1023 - ec) << 52));  // 2^-ec
-  const double ar = d.re * sc, ai = d.im * sc;          // |scaled| in [1, 2)
-  const double q = fma(ar, ar, ai * ai);                 // in [1, 8)
-  double r = (double)__frcp_rn((float)q);
-  r = r * fma(-q, r, 2.0);
-  r = r * fma(-q, r, 2.0);
-  r = r * fma(-q, r, 2.0);
-  // 1/d = conj(d_s) / q * sc
-  return cplx{ar * r * sc, -ai * r * sc};
+constexpr int IV_T = 512;
+constexpr int IV_STEPS = 2;   // inverse-iteration solves before the refinement
+constexpr int DMW_STEPS = 3;  // refinement steps
+constexpr int IV_NQ = (D_MAX + 31) / 32;  // rows per lane in the LU update
+
+struct cf {
+  float re, im;
+};
+__device__ __forceinline__ cf cf_mul(cf a, cf b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+// 1 / d in FP32 (d scaled to a largest component of one first); 0 for d = 0.
+// The hardware reciprocal (within 2 ulp) suffices: these factors only
+// precondition the FP64 refinement.
+__device__ __forceinline__ cf cf_recip(cf d) {
+  const float m = fmaxf(fabsf(d.re), fabsf(d.im));
+  if (!(m > 0.f) || !isfinite(m)) return {0.f, 0.f};
+  const float im = __fdividef(1.f, m);
+  const float a = d.re * im, b = d.im * im;
+  const float r = __fdividef(im, a * a + b * b);
+  return {a * r, -b * r};
 }
 
+struct IvShared {
+  float pr, pi, ir, ii;  // pivot value and its reciprocal
+  int p;
+};
 
-__global__ void __launch_bounds__(512) k_ce_invit(WS ws) {
-  Ctl* c = ws.ctl;
-  if (c->jf <= 0) return;
-  const int n = c->ell;
-  CeLayout L = ce_layout(ws.dscr);
-  const int idx = blockIdx.x;
-  if (n <= 0 || idx >= L.cnt[0]) return;
-  const cplx mu0{L.cmu[2 * idx], L.cmu[2 * idx + 1]};
-  const bool cx = mu0.im != 0.0;
-  double* Ar = L.lu + (int64_t)idx * 2 * LDD * LDD;  // column-major n x n
-  double* Ai = Ar + (int64_t)LDD * LDD;
-  __shared__ double xr[D_MAX], xi[D_MAX];
-  __shared__ int perm[D_MAX];
-  __shared__ double red[32];
-  __shared__ double bc[4];
-  __shared__ unsigned long long redu[32];
-  const double* M = L.M;
-  double mnorm = 0.0;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e % n, j = e / n;
-    const double v = M[i + (int64_t)j * LDD];
-    Ar[i + (int64_t)j * LDD] = v - (i == j ? mu0.re : 0.0);
-    Ai[i + (int64_t)j * LDD] = (i == j) ? -mu0.im : 0.0;
-    mnorm = fmax(mnorm, fabs(v));
-  }
-  {  // block max via the u64 bit pattern of a non-negative double
-    unsigned long long b = (unsigned long long)__double_as_longlong(mnorm);
-    b = block_max_u64(b, redu);
-    mnorm = __longlong_as_double((long long)b);
-  }
-  const double tiny = fmax(mnorm, 1e-300) * 2.220446049250313e-16 * (double)n;
-  __syncthreads();
-  // LU with partial pivoting (pivot by |re| + |im|)
+// In-place FP32 LU with partial pivoting (pivot by |re| + |im|, ties the
+// lowest row) of the n x n matrix (Ar, Ai), column-major with leading
+// dimension ld, in shared memory: unit lower L below the diagonal, U on and
+// above it, rows exchanged across the whole matrix (L included) and perm[k]
+// the row exchanged with row k at step k.  A zero pivot is replaced by tiny.
+// Block-wide, two barriers per step.  Warp 0 stores the previous step's
+// multipliers (its registers) and pivot, and finds the pivot of column k;
+// then every warp forms the multipliers of its lanes' rows i = k + 1 + lane +
+// 32 q from column k, exchanges rows k and p on its columns j = wid (mod nw)
+// and updates them column by column, over the row strips below k only.
+__device__ void iv_lu(float* Ar, float* Ai, int ld, int n, bool cx, int* perm, float tiny, IvShared& sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  cf l[IV_NQ];
+#pragma unroll
+  for (int q = 0; q < IV_NQ; ++q) l[q] = cf{0.f, 0.f};
   for (int k = 0; k < n; ++k) {
-    unsigned long long best = 0ull;
-    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-      const double a = fabs(Ar[i + (int64_t)k * LDD]) + (cx ? fabs(Ai[i + (int64_t)k * LDD]) : 0.0);
-      // pack (magnitude bits, row) so that the max picks the largest, ties the lowest row
-      const unsigned long long key = ((unsigned long long)__double_as_longlong(a) & ~0x3FFull) |
-                                     (unsigned long long)(0x3FF - i);
-      best = key > best ? key : best;
+    if (wid == 0) {
+      if (k > 0) {  // the multipliers and the pivot of step k - 1 into column k - 1
+#pragma unroll
+        for (int q = 0; q < IV_NQ; ++q) {
+          if (k + 32 * q >= n) break;  // uniform
+          const int i = k + lane + 32 * q;
+          if (i < n) {
+            Ar[i + (k - 1) * ld] = l[q].re;
+            if (cx) Ai[i + (k - 1) * ld] = l[q].im;
+          }
+        }
+        if (lane == 0) {
+          Ar[(k - 1) + (k - 1) * ld] = sh.pr;
+          if (cx) Ai[(k - 1) + (k - 1) * ld] = sh.pi;
+        }
+        __syncwarp();
+      }
+      float best = -1.f;
+      int bi = k;
+#pragma unroll
+      for (int q = 0; q < IV_NQ; ++q) {
+        const int i = k + lane + 32 * q;
+        if (i < n) {
+          const float a = fabsf(Ar[i + k * ld]) + (cx ? fabsf(Ai[i + k * ld]) : 0.f);
+          if (a > best) {
+            best = a;
+            bi = i;
+          }
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        cf pv{Ar[bi + k * ld], cx ? Ai[bi + k * ld] : 0.f};
+        if (pv.re == 0.f && pv.im == 0.f) pv.re = tiny;
+        const cf iv = cf_recip(pv);
+        perm[k] = bi;
+        sh.p = bi;
+        sh.pr = pv.re;
+        sh.pi = pv.im;
+        sh.ir = iv.re;
+        sh.ii = iv.im;
+      }
     }
-    best = block_max_u64(best, redu);
-    const int p = 0x3FF - (int)(best & 0x3FF);
-    if (threadIdx.x == 0) perm[k] = p;
+    __syncthreads();
+    const int p = sh.p;
+    const cf inv{sh.ir, sh.ii};
+    // multipliers of this lane's rows from column k (row p holds the old row k's entry)
+#pragma unroll
+    for (int q = 0; q < IV_NQ; ++q) {
+      if (k + 1 + 32 * q >= n) break;  // uniform
+      const int i = k + 1 + lane + 32 * q;
+      if (i < n) {
+        const int src = i == p ? k : i;
+        l[q] = cf_mul(cf{Ar[src + k * ld], cx ? Ai[src + k * ld] : 0.f}, inv);
+      } else {
+        l[q] = cf{0.f, 0.f};
+      }
+    }
+    // row exchange on this warp's columns (one lane per column), then the update
     if (p != k) {
-      for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double t = Ar[k + (int64_t)j * LDD];
-        Ar[k + (int64_t)j * LDD] = Ar[p + (int64_t)j * LDD];
-        Ar[p + (int64_t)j * LDD] = t;
+      for (int j = wid + nw * lane; j < n; j += 32 * nw) {
+        if (j == k) continue;
+        float t = Ar[k + j * ld];
+        Ar[k + j * ld] = Ar[p + j * ld];
+        Ar[p + j * ld] = t;
         if (cx) {
-          t = Ai[k + (int64_t)j * LDD];
-          Ai[k + (int64_t)j * LDD] = Ai[p + (int64_t)j * LDD];
-          Ai[p + (int64_t)j * LDD] = t;
+          t = Ai[k + j * ld];
+          Ai[k + j * ld] = Ai[p + j * ld];
+          Ai[p + j * ld] = t;
+        }
+      }
+    }
+    __syncwarp();
+    int j = wid;
+    while (j <= k) j += nw;  // this warp's first column right of k
+    for (; j < n; j += nw) {
+      const float ur = Ar[k + j * ld], ui = cx ? Ai[k + j * ld] : 0.f;
+#pragma unroll
+      for (int q = 0; q < IV_NQ; ++q) {
+        if (k + 1 + 32 * q >= n) break;  // the strips below row k only (uniform)
+        const int i = k + 1 + lane + 32 * q;
+        if (i < n) {
+          if (cx) {
+            const float ar = Ar[i + j * ld], ai = Ai[i + j * ld];
+            Ar[i + j * ld] = ar - (l[q].re * ur - l[q].im * ui);
+            Ai[i + j * ld] = ai - (l[q].re * ui + l[q].im * ur);
+          } else {
+            Ar[i + j * ld] = fmaf(-l[q].re, ur, Ar[i + j * ld]);
+          }
         }
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      cplx d{Ar[k + (int64_t)k * LDD], cx ? Ai[k + (int64_t)k * LDD] : 0.0};
-      if (d.re == 0.0 && d.im == 0.0) {
-        d.re = tiny;
-        Ar[k + (int64_t)k * LDD] = tiny;
-      }
-      const cplx inv = crecip(d);
-      bc[0] = inv.re;
-      bc[1] = inv.im;
-    }
-    __syncthreads();
-    const cplx inv{bc[0], bc[1]};
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      if (cx) {
-        const cplx l = cmul(cplx{Ar[i + (int64_t)k * LDD], Ai[i + (int64_t)k * LDD]}, inv);
-        Ar[i + (int64_t)k * LDD] = l.re;
-        Ai[i + (int64_t)k * LDD] = l.im;
-      } else {
-        Ar[i + (int64_t)k * LDD] *= inv.re;
-      }
-    }
-    __syncthreads();
-    const int m = n - k - 1;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = k + 1 + e % m, j = k + 1 + e / m;
-      if (cx) {
-        const cplx l{Ar[i + (int64_t)k * LDD], Ai[i + (int64_t)k * LDD]};
-        const cplx u{Ar[k + (int64_t)j * LDD], Ai[k + (int64_t)j * LDD]};
-        const cplx a = csub(cplx{Ar[i + (int64_t)j * LDD], Ai[i + (int64_t)j * LDD]}, cmul(l, u));
-        Ar[i + (int64_t)j * LDD] = a.re;
-        Ai[i + (int64_t)j * LDD] = a.im;
-      } else {
-        Ar[i + (int64_t)j * LDD] = fma(-Ar[i + (int64_t)k * LDD], Ar[k + (int64_t)j * LDD], Ar[i + (int64_t)j * LDD]);
-      }
-    }
-    __syncthreads();
   }
-  // inverse iteration from x = (1, ..., 1); the reciprocals of U's diagonal
-  // are formed once, in parallel, so the back substitution only multiplies
-  __shared__ double udr[D_MAX], udi[D_MAX];
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const cplx inv = crecip(cplx{Ar[k + (int64_t)k * LDD], cx ? Ai[k + (int64_t)k * LDD] : 0.0});
-    udr[k] = inv.re;
-    udi[k] = inv.im;
+  // the last step's pivot (no multipliers below it)
+  if (threadIdx.x == 0) {
+    Ar[(n - 1) + (n - 1) * ld] = sh.pr;
+    if (cx) Ai[(n - 1) + (n - 1) * ld] = sh.pi;
   }
-  // the row interchanges of the factorisation as one permutation: row k of
-  // P x is x[sig[k]]
-  __shared__ int sig[D_MAX];
-  __shared__ double yr[D_MAX], yi[D_MAX];
+  __syncthreads();
+}
+
+// Row k of P y is y[sig[k]]: the exchanges of the factorisation composed.
+__device__ void iv_perm(const int* perm, int n, int* sig) {
   if (threadIdx.x == 0) {
     for (int k = 0; k < n; ++k) sig[k] = k;
     for (int k = 0; k < n; ++k) {
@@ -1096,123 +1133,356 @@ __global__ void __launch_bounds__(512) k_ce_invit(WS ws) {
       sig[p] = t;
     }
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) { xr[i] = 1.0; xi[i] = 0.0; }
-  __syncthreads();
-  // The triangular solves: thread t owns row t (n <= D_MAX <= blockDim.x)
-  // and keeps the next PF entries of its row of L (or U) in flight, so the
-  // L2 latency of the factors stays off the column-by-column chain; one
-  // barrier of the first nb threads per column.
-  constexpr int PF = 4;
+}
+
+// Solve L U y = (yr, yi) in place (y already permuted) with the first
+// nb = 32 ceil(n / 32) threads: thread t owns row t and loads the next
+// column's factor entry of its row ahead of time; the value of column k
+// passes through shared memory (alternating slots) with one named barrier of
+// those threads per column.  (udr, udi): reciprocals of U's diagonal; slot:
+// 8 floats of shared memory.
+__device__ void iv_solve(const float* Ar, const float* Ai, int ld, int n, bool cx, float* yr, float* yi,
+                         const float* udr, const float* udi, float* slot) {
   const int t = threadIdx.x;
+  const int nb = (n + 31) & ~31;
+  if (t >= nb) return;
   const bool own = t < n;
-  const int nb = (n + 31) / 32 * 32;
-  const bool inb = t < nb;
-  for (int it = 0; it < 3; ++it) {
-    if (own) {
-      yr[t] = xr[sig[t]];
-      yi[t] = xi[sig[t]];
+  float vr = own ? yr[t] : 0.f, vi = (own && cx) ? yi[t] : 0.f;
+  // L y = b: at column k, y_k is final; rows t > k subtract L(t, k) y_k
+  float fr = (own && t > 0) ? Ar[t] : 0.f, fi = (own && t > 0 && cx) ? Ai[t] : 0.f;
+  for (int k = 0; k < n; ++k) {
+    const bool nx = own && t > k + 1;
+    const float gr = nx ? Ar[t + (k + 1) * ld] : 0.f, gi = (nx && cx) ? Ai[t + (k + 1) * ld] : 0.f;
+    float* sl = slot + 2 * (k & 1);
+    if (t == k) {
+      sl[0] = vr;
+      sl[1] = vi;
     }
-    __syncthreads();
-    if (inb) {
-      // L y = P x (unit lower): at column k, rows t > k take y_k
-      cplx lp[PF];
-#pragma unroll
-      for (int u = 0; u < PF; ++u)
-        lp[u] = (own && u < t) ? cplx{Ar[t + (int64_t)u * LDD], cx ? Ai[t + (int64_t)u * LDD] : 0.0} : cplx{0.0, 0.0};
-      for (int k0 = 0; k0 < n; k0 += PF) {
-#pragma unroll
-        for (int u = 0; u < PF; ++u) {
-          const int k = k0 + u;
-          if (k < n) {
-            if (own && t > k) {
-              const cplx v = csub(cplx{yr[t], yi[t]}, cmul(lp[u], cplx{yr[k], yi[k]}));
-              yr[t] = v.re;
-              yi[t] = v.im;
-            }
-            const int kn = k + PF;
-            lp[u] = (own && kn < t) ? cplx{Ar[t + (int64_t)kn * LDD], cx ? Ai[t + (int64_t)kn * LDD] : 0.0}
-                                    : cplx{0.0, 0.0};
-            asm volatile("bar.sync 2, %0;" ::"r"(nb) : "memory");
-          }
-        }
-      }
-      // U x = y (upper), columns from the last: x_k = y_k / u_kk, then rows t < k
-      cplx up[PF];
-#pragma unroll
-      for (int u = 0; u < PF; ++u) {
-        const int kk = n - 1 - u;
-        up[u] = (own && kk > t) ? cplx{Ar[t + (int64_t)kk * LDD], cx ? Ai[t + (int64_t)kk * LDD] : 0.0}
-                                : cplx{0.0, 0.0};
-      }
-      for (int k0 = n - 1; k0 >= 0; k0 -= PF) {
-#pragma unroll
-        for (int u = 0; u < PF; ++u) {
-          const int k = k0 - u;
-          if (k >= 0) {
-            const cplx xk = cmul(cplx{yr[k], yi[k]}, cplx{udr[k], udi[k]});
-            if (own && t < k) {
-              const cplx v = csub(cplx{yr[t], yi[t]}, cmul(up[u], xk));
-              yr[t] = v.re;
-              yi[t] = v.im;
-            }
-            if (t == k) {
-              xr[k] = xk.re;
-              xi[k] = xk.im;
-            }
-            const int kn = k - PF;
-            up[u] = (own && kn > t && kn >= 0)
-                        ? cplx{Ar[t + (int64_t)kn * LDD], cx ? Ai[t + (int64_t)kn * LDD] : 0.0}
-                        : cplx{0.0, 0.0};
-            asm volatile("bar.sync 2, %0;" ::"r"(nb) : "memory");
-          }
-        }
-      }
+    asm volatile("bar.sync 2, %0;" ::"r"(nb) : "memory");
+    const float yk_r = sl[0], yk_i = sl[1];
+    if (cx) {
+      vr -= fr * yk_r - fi * yk_i;
+      vi -= fr * yk_i + fi * yk_r;
+    } else {
+      vr = fmaf(-fr, yk_r, vr);
     }
-    __syncthreads();
-    // normalise by the entry of largest |re| + |im| (ties: lowest index)
-    unsigned long long key = 0ull;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const double a = fabs(xr[i]) + fabs(xi[i]);
-      const unsigned long long kk =
-          ((unsigned long long)__double_as_longlong(a) & ~0x3FFull) | (unsigned long long)(0x3FF - i);
-      key = kk > key ? kk : key;
-    }
-    key = block_max_u64(key, redu);
-    const int bi = 0x3FF - (int)(key & 0x3FF);
-    const cplx piv{xr[bi], xi[bi]};
-    const cplx inv = (piv.re == 0.0 && piv.im == 0.0) ? cplx{1.0, 0.0} : crecip(piv);
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const cplx v = cmul(cplx{xr[i], xi[i]}, inv);
-      xr[i] = v.re;
-      xi[i] = cx ? v.im : 0.0;
-    }
-    __syncthreads();
+    fr = gr;
+    fi = gi;
   }
-  // Rayleigh quotient mu = x^H M x / x^H x
-  double nr = 0.0, ni = 0.0, dd = 0.0;
+  // U x = y: x_k = y_k / U(k, k), then rows t < k subtract U(t, k) x_k (its
+  // own pair of slots, so that no write races a read of the last L column)
+  slot += 4;
+  fr = (own && t < n - 1) ? Ar[t + (n - 1) * ld] : 0.f;
+  fi = (own && t < n - 1 && cx) ? Ai[t + (n - 1) * ld] : 0.f;
+  for (int k = n - 1; k >= 0; --k) {
+    const bool nx = own && k >= 1 && t < k - 1;
+    const float gr = nx ? Ar[t + (k - 1) * ld] : 0.f, gi = (nx && cx) ? Ai[t + (k - 1) * ld] : 0.f;
+    float* sl = slot + 2 * (k & 1);
+    if (t == k) {
+      const float xr = cx ? vr * udr[k] - vi * udi[k] : vr * udr[k];
+      const float xi = cx ? vr * udi[k] + vi * udr[k] : 0.f;
+      vr = xr;
+      vi = xi;
+      sl[0] = xr;
+      sl[1] = xi;
+    }
+    asm volatile("bar.sync 2, %0;" ::"r"(nb) : "memory");
+    const float xk_r = sl[0], xk_i = sl[1];
+    if (cx) {
+      vr -= fr * xk_r - fi * xk_i;
+      vi -= fr * xk_i + fi * xk_r;
+    } else {
+      vr = fmaf(-fr, xk_r, vr);
+    }
+    fr = gr;
+    fi = gi;
+  }
+  if (own) {
+    yr[t] = vr;
+    if (cx) yi[t] = vi;
+  }
+}
+
+// (M x)_i for a row i of M (global, column-major, ld LDD) and x = xr + i xi in
+// shared memory; the loads of M run eight columns ahead of the FMAs.
+__device__ __forceinline__ void iv_row_dot(const double* __restrict__ M, int n, int i, const double* xr,
+                                           const double* xi, double& sr, double& si) {
+  constexpr int G = 8;
+  sr = 0.0;
+  si = 0.0;
+  const double* __restrict__ row = M + i;
+  int j = 0;
+  for (; j + G <= n; j += G) {
+    double mv[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) mv[u] = __ldg(row + (int64_t)(j + u) * LDD);
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      sr = fma(mv[u], xr[j + u], sr);
+      si = fma(mv[u], xi[j + u], si);
+    }
+  }
+  for (; j < n; ++j) {
+    const double m = __ldg(row + (int64_t)j * LDD);
+    sr = fma(m, xr[j], sr);
+    si = fma(m, xi[j], si);
+  }
+}
+
+// (rr, ri) = lambda x - M x in FP64; returns max_i max(|re r_i|, |im r_i|) to
+// every thread.
+__device__ double iv_residual(const double* __restrict__ M, int n, double lr, double li, const double* xr,
+                              const double* xi, double* rr, double* ri, unsigned long long* redu) {
+  unsigned long long mb = 0ull;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double yr = 0.0, yi = 0.0;
-    for (int j = 0; j < n; ++j) {
-      const double mij = M[i + (int64_t)j * LDD];
-      yr = fma(mij, xr[j], yr);
-      yi = fma(mij, xi[j], yi);
-    }
-    // conj(x_i) * y_i
-    nr += xr[i] * yr + xi[i] * yi;
-    ni += xr[i] * yi - xi[i] * yr;
-    dd += xr[i] * xr[i] + xi[i] * xi[i];
+    double sr, si;
+    iv_row_dot(M, n, i, xr, xi, sr, si);
+    const double a = fma(lr, xr[i], fma(-li, xi[i], -sr));
+    const double b = fma(lr, xi[i], fma(li, xr[i], -si));
+    rr[i] = a;
+    ri[i] = b;
+    const unsigned long long u = abs_bits(a), v = abs_bits(b);
+    const unsigned long long w = u > v ? u : v;
+    mb = w > mb ? w : mb;
   }
-  nr = block_sum(nr, red);
-  ni = block_sum(ni, red);
-  dd = block_sum(dd, red);
+  mb = block_max_u64(mb, redu);
+  return __longlong_as_double((long long)mb);
+}
+
+// 2^(1022 - e) for a biased exponent e of a positive value v: v 2^(1022 - e)
+// lies in [0.5, 1).  1 when e is out of the range where that is a normal double.
+__device__ __forceinline__ double iv_pow2_scale(int e) {
+  return e >= 1 && e <= 2043 ? __longlong_as_double((long long)((unsigned long long)(2045 - e) << 52)) : 1.0;
+}
+
+size_t ce_invit_smem() {
+  return (size_t)2 * D_MAX * (D_MAX + 1) * sizeof(float) + 4 * D_MAX * sizeof(float) +
+         6 * D_MAX * sizeof(double) + 2 * D_MAX * sizeof(int);
+}
+
+__global__ void __launch_bounds__(IV_T, 1) k_ce_invit(WS ws) {
+  Ctl* c = ws.ctl;
+  if (c->jf <= 0) return;
+  const int n = c->ell;
+  CeLayout L = ce_layout(ws.dscr);
+  const int idx = blockIdx.x;
+  if (n <= 0 || idx >= L.cnt[0]) return;
+  extern __shared__ __align__(16) unsigned char iv_smem[];
+  double* xr = (double*)iv_smem;  // the eigenvector (FP64)
+  double* xi = xr + D_MAX;
+  double* rr = xi + D_MAX;        // residual
+  double* ri = rr + D_MAX;
+  double* br = ri + D_MAX;        // the best pair so far
+  double* bi = br + D_MAX;
+  float* yr = (float*)(bi + D_MAX);  // FP32 solve vector
+  float* yi = yr + D_MAX;
+  float* udr = yi + D_MAX;           // reciprocals of U's diagonal
+  float* udi = udr + D_MAX;
+  int* perm = (int*)(udi + D_MAX);
+  int* sig = perm + D_MAX;
+  const int ld = n + 1;
+  float* Ar = (float*)(sig + D_MAX);
+  float* Ai = Ar + (size_t)ld * n;
+  __shared__ IvShared sh;
+  __shared__ float iv_slot[8];
+  __shared__ unsigned long long redu[32];
+  __shared__ double red[32];
+  __shared__ double lam_s[2];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* __restrict__ M = L.M;
+  const double mu_r = L.cmu[2 * idx], mu_i = L.cmu[2 * idx + 1];
+  const bool cx = mu_i != 0.0;
+  // the power-of-two scale of M (loads of a column issued together)
+  unsigned long long mb = 0ull;
+  for (int j = wid; j < n; j += nw) {
+    double v[IV_NQ];
+#pragma unroll
+    for (int q = 0; q < IV_NQ; ++q) {
+      const int i = lane + 32 * q;
+      v[q] = i < n ? __ldg(M + i + (int64_t)j * LDD) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < IV_NQ; ++q) {
+      const unsigned long long u = abs_bits(v[q]);
+      mb = u > mb ? u : mb;
+    }
+  }
+  mb = block_max_u64(mb, redu);
+  const double sc = iv_pow2_scale(bexp_of_bits(mb));  // max |M sc| in [0.5, 1)
+  const float tiny = 5.9604645e-8f * (float)n;         // 2^-24 n, against entries of order one
+  // ---- 1. inverse iteration with the FP32 LU of (M - mu0 I) sc ----
+  for (int j = wid; j < n; j += nw) {
+    double v[IV_NQ];
+#pragma unroll
+    for (int q = 0; q < IV_NQ; ++q) {
+      const int i = lane + 32 * q;
+      v[q] = i < n ? __ldg(M + i + (int64_t)j * LDD) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < IV_NQ; ++q) {
+      const int i = lane + 32 * q;
+      if (i < n) {
+        Ar[i + j * ld] = (float)(i == j ? (v[q] - mu_r) * sc : v[q] * sc);
+        if (cx) Ai[i + j * ld] = i == j ? (float)(-mu_i * sc) : 0.f;
+      }
+    }
+  }
+  __syncthreads();
+  iv_lu(Ar, Ai, ld, n, cx, perm, tiny, sh);
+  iv_perm(perm, n, sig);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const cf r = cf_recip(cf{Ar[k + k * ld], cx ? Ai[k + k * ld] : 0.f});
+    udr[k] = r.re;
+    udi[k] = r.im;
+    yr[k] = 1.f;
+    yi[k] = 0.f;
+  }
+  __syncthreads();
+  for (int it = 0; it < IV_STEPS; ++it) {
+    // permute, solve, and scale the result to a largest |re| + |im| of one
+    {
+      const int t = threadIdx.x;
+      const float tr = t < n ? yr[sig[t]] : 0.f, ti = t < n ? yi[sig[t]] : 0.f;
+      __syncthreads();
+      if (t < n) {
+        yr[t] = tr;
+        yi[t] = ti;
+      }
+      __syncthreads();
+    }
+    iv_solve(Ar, Ai, ld, n, cx, yr, yi, udr, udi, iv_slot);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      float best = -1.f;
+      int bix = 0;
+      for (int i = lane; i < n; i += 32) {
+        const float a = fabsf(yr[i]) + fabsf(yi[i]);
+        if (a > best) {
+          best = a;
+          bix = i;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bix, o);
+        if (ob > best || (ob == best && oi < bix)) {
+          best = ob;
+          bix = oi;
+        }
+      }
+      const cf inv = best > 0.f && isfinite(best) ? cf_recip(cf{yr[bix], yi[bix]}) : cf{1.f, 0.f};
+      __syncwarp();
+      for (int i = lane; i < n; i += 32) {
+        const cf v = cf_mul(cf{yr[i], yi[i]}, inv);
+        yr[i] = v.re;
+        yi[i] = cx ? v.im : 0.f;
+      }
+      if (it == IV_STEPS - 1 && lane == 0) sh.p = bix;
+    }
+    __syncthreads();
+  }
+  // ---- 2. x0 with x0(s) = 1, lambda0 = Rayleigh quotient ----
+  const int s = sh.p;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    xr[i] = i == s ? 1.0 : (double)yr[i];
+    xi[i] = (i == s || !cx) ? 0.0 : (double)yi[i];
+  }
+  __syncthreads();
+  {
+    double nr = 0.0, ni = 0.0, dd = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double sr, si;
+      iv_row_dot(M, n, i, xr, xi, sr, si);
+      nr += xr[i] * sr + xi[i] * si;  // conj(x_i) (M x)_i
+      ni += xr[i] * si - xi[i] * sr;
+      dd += xr[i] * xr[i] + xi[i] * xi[i];
+    }
+    nr = block_sum(nr, red);
+    ni = block_sum(ni, red);
+    dd = block_sum(dd, red);
+    if (threadIdx.x == 0) {
+      lam_s[0] = nr / dd;
+      lam_s[1] = cx ? ni / dd : 0.0;
+    }
+    __syncthreads();
+  }
+  double lr = lam_s[0], li = lam_s[1];
+  // ---- 3. B = (M - lambda0 I) sc with column s replaced by -x0 sc, in FP32 ----
+  for (int j = wid; j < n; j += nw) {
+    double v[IV_NQ];
+#pragma unroll
+    for (int q = 0; q < IV_NQ; ++q) {
+      const int i = lane + 32 * q;
+      v[q] = (i < n && j != s) ? __ldg(M + i + (int64_t)j * LDD) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < IV_NQ; ++q) {
+      const int i = lane + 32 * q;
+      if (i >= n) continue;
+      if (j == s) {
+        Ar[i + j * ld] = (float)(-xr[i] * sc);
+        if (cx) Ai[i + j * ld] = (float)(-xi[i] * sc);
+      } else {
+        Ar[i + j * ld] = (float)(i == j ? (v[q] - lr) * sc : v[q] * sc);
+        if (cx) Ai[i + j * ld] = i == j ? (float)(-li * sc) : 0.f;
+      }
+    }
+  }
+  __syncthreads();
+  iv_lu(Ar, Ai, ld, n, cx, perm, tiny, sh);
+  iv_perm(perm, n, sig);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const cf r = cf_recip(cf{Ar[k + k * ld], cx ? Ai[k + k * ld] : 0.f});
+    udr[k] = r.re;
+    udi[k] = r.im;
+  }
+  __syncthreads();
+  double best = INFINITY;
+  double blr = lr, bli = li;  // the pair kept when no residual is finite: x0, lambda0
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    br[i] = xr[i];
+    bi[i] = xi[i];
+  }
+  for (int it = 0; it <= DMW_STEPS; ++it) {
+    const double rmax = iv_residual(M, n, lr, li, xr, xi, rr, ri, redu);
+    if (rmax < best) {  // uniform: every thread holds the same rmax
+      best = rmax;
+      blr = lr;
+      bli = li;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        br[i] = xr[i];
+        bi[i] = xi[i];
+      }
+    }
+    if (it == DMW_STEPS || !(rmax > 0.0) || !isfinite(rmax)) break;
+    // B z = r, with r scaled by a power of two to a largest entry of order one
+    const double rs = iv_pow2_scale(bexp_of_bits((unsigned long long)__double_as_longlong(rmax)));
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      yr[i] = (float)(rr[sig[i]] * rs);
+      yi[i] = cx ? (float)(ri[sig[i]] * rs) : 0.f;
+    }
+    __syncthreads();
+    iv_solve(Ar, Ai, ld, n, cx, yr, yi, udr, udi, iv_slot);
+    __syncthreads();
+    // z = y sc / rs (B was scaled by sc, r by rs)
+    const double zs = sc / rs;
+    const double dlr = (double)yr[s] * zs, dli = cx ? (double)yi[s] * zs : 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if (i == s) continue;
+      xr[i] += (double)yr[i] * zs;
+      if (cx) xi[i] += (double)yi[i] * zs;
+    }
+    lr += dlr;
+    li += dli;
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    L.cref[2 * idx] = nr / dd;
-    L.cref[2 * idx + 1] = cx ? ni / dd : 0.0;
+    L.cref[2 * idx] = blr;
+    L.cref[2 * idx + 1] = cx ? bli : 0.0;
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    L.cvec[i + (int64_t)(2 * idx) * LDD] = xr[i];
-    L.cvec[i + (int64_t)(2 * idx + 1) * LDD] = xi[i];
+    L.cvec[i + (int64_t)(2 * idx) * LDD] = br[i];
+    L.cvec[i + (int64_t)(2 * idx + 1) * LDD] = bi[i];
   }
 }
 
@@ -1406,6 +1676,8 @@ cudaError_t launch_cycle_end_part(int part, const WS& ws, int kh, int ucur, cons
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_ce_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ce_eig_smem());
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_ce_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ce_invit_smem());
+    if (e != cudaSuccess) return e;
     attr = true;
   }
   const int dmax_now = kh + ws.m;
@@ -1438,7 +1710,7 @@ cudaError_t launch_cycle_end_part(int part, const WS& ws, int kh, int ucur, cons
       break;
     }
     case 4: k_ce_eig<<<1, 512, ce_eig_smem(), st>>>(ws); break;
-    case 5: k_ce_invit<<<KC, 512, 0, st>>>(ws); break;
+    case 5: k_ce_invit<<<KC, IV_T, ce_invit_smem(), st>>>(ws); break;
     case 6: k_ce_select<<<1, 256, 0, st>>>(ws); break;
     case 7: k_ce_finish<<<1, 512, 0, st>>>(ws, kh, ucur); break;
     case 8: k_ce_sketch_update<<<K_MAX, 512, 0, st>>>(ws, kh, SU, SAU, SUn, SAUn); break;
