@@ -98,8 +98,8 @@ class SubsampledDCT:
     S = sqrt(N / s) P F E with E a diagonal of random signs, F the orthonormal
     DCT (type II; scipy's transform serves as the library step) and P the
     selection of s distinct rows drawn uniformly at random.  E ||S x||^2 =
-    ||x||^2.  Not part of the GPU path (whose sketch is the sparse sign above):
-    it lets the oracle run the paper's experiments with the paper's operator.
+    ||x||^2.  The second sketch family, beside the sparse sign above: it runs
+    the paper's experiments with the paper's operator.
     The random signs and rows come from numpy's PCG64 seeded [seed, n, s]."""
 
     def __init__(self, seed: int, n: int, s: int):

@@ -35,6 +35,8 @@ struct CeLayout {
   int* sel;   // [K_MAX] eigenvalue index per inverse iteration
   int* zcol;  // [K_MAX] first Z column of that eigenvalue
   int* cnt;   // [0] number of inverse iterations
+  int* ivfail;  // [KC] candidate left to the FP64 fallback
+  double* lu;   // KC blocks of 2*LDD*LDD (the fallback's complex LU)
 };
 
 __host__ __device__ inline CeLayout ce_layout(double* base) {
@@ -59,12 +61,14 @@ __host__ __device__ inline CeLayout ce_layout(double* base) {
   L.cmu = L.misc + 64 + 3 * K_MAX;
   L.cref = L.cmu + 2 * KC;
   L.cvec = L.cref + 2 * KC;
+  L.ivfail = L.cnt + K_MAX;  // inside the 3 K_MAX doubles reserved after misc (6 K_MAX ints, KC <= 3 K_MAX)
+  L.lu = L.cvec + (int64_t)2 * KC * LDD;
   return L;
 }
 
 size_t ce_scratch_doubles() {
   return (size_t)6 * LDD * LDD + 3 * LDD + 2 * (size_t)LDD * K_MAX + 2 * LDD + 64 + 3 * K_MAX + 4 * KC +
-         (size_t)2 * KC * LDD + 64;
+         (size_t)2 * KC * LDD + (size_t)KC * 2 * LDD * LDD + 64;
 }
 
 // Column l of S[U V] / SAW (sketched basis / sketched image).
@@ -968,7 +972,10 @@ size_t ce_eig_smem() { return ((size_t)(D_MAX + 1) * D_MAX + 2 * D_MAX + 64) * s
 //     (lambda0, x0) and factored once in FP32.  Each step computes the FP64
 //     residual r = lambda x - M x, solves B z = r with the FP32 factors and
 //     sets x(i) += z(i) (i != s), lambda += z(s); the FP64 residual carries
-//     the accuracy.  The pair with the smallest max |r| seen is kept.
+//     the accuracy.  The pair with the smallest max |r| seen is kept; if
+//     its residual is not at the FP64 level (slow or no contraction, which
+//     happens when M is too ill-conditioned for FP32 factors), the
+//     candidate is flagged for the FP64 fallback below.
 // M is scaled by a power of two 2^-e (exact) before rounding to FP32.
 // ---------------------------------------------------------------------------
 constexpr int IV_T = 512;
@@ -1479,10 +1486,284 @@ __global__ void __launch_bounds__(IV_T, 1) k_ce_invit(WS ws) {
   if (threadIdx.x == 0) {
     L.cref[2 * idx] = blr;
     L.cref[2 * idx + 1] = cx ? bli : 0.0;
+    // converged: the best residual at the level of its own FP64 rounding (n eps max|M| max|x|,
+    // with max|x| about one), with a margin of 256; else the FP64 fallback takes the candidate
+    const double mmax = __longlong_as_double((long long)mb);
+    L.ivfail[idx] = (best <= 256.0 * (double)n * 2.220446049250313e-16 * mmax) ? 0 : 1;
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     L.cvec[i + (int64_t)(2 * idx) * LDD] = br[i];
     L.cvec[i + (int64_t)(2 * idx + 1) * LDD] = bi[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The fallback for a candidate whose refinement above did not reach FP64
+// accuracy (flagged in ivfail): FP64 eigenpair of M by LU with partial
+// pivoting of M - mu0 I (complex when Im mu0 != 0), three steps of inverse
+// iteration, and the Rayleigh quotient mu = x^H M x / x^H x.  One CTA per
+// candidate; the others return at once.  Slow on this GPU (its pivot chain
+// is FP64), but its accuracy does not depend on the conditioning of M, which
+// the FP32 factors of the refinement do: on the truncated-SVD path M can be
+// too ill-conditioned for them.
+// ---------------------------------------------------------------------------
+struct cplx { double re, im; };
+__device__ inline cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ inline cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+// 1 / d for a complex d: conj(d) / |d|^2 with |d|^2 scaled into range by a
+// power of two and its reciprocal from an FP32 estimate refined by two Newton
+// steps r <- r (2 - q r) (an FP64 division is a long instruction sequence on
+// this GPU; these are a few dependent FMAs).
+__device__ inline cplx crecip(cplx d) {
+  const double m = fmax(fabs(d.re), fabs(d.im));
+  if (!(m > 0.0) || !isfinite(m)) return cplx{0.0, 0.0};
+  const int e = (int)(((unsigned long long)__double_as_longlong(m) >> 52) & 0x7FF) - 1023;
+  const int ec = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+  const double sc = __longlong_as_double((long long)((unsigned long long)(1023 - ec) << 52));  // 2^-ec
+  const double ar = d.re * sc, ai = d.im * sc;          // |scaled| in [1, 2)
+  const double q = fma(ar, ar, ai * ai);                 // in [1, 8)
+  double r = (double)__frcp_rn((float)q);
+  r = r * fma(-q, r, 2.0);
+  r = r * fma(-q, r, 2.0);
+  r = r * fma(-q, r, 2.0);
+  // 1/d = conj(d_s) / q * sc
+  return cplx{ar * r * sc, -ai * r * sc};
+}
+
+
+__global__ void __launch_bounds__(512) k_ce_invit64(WS ws) {
+  Ctl* c = ws.ctl;
+  if (c->jf <= 0) return;
+  const int n = c->ell;
+  CeLayout L = ce_layout(ws.dscr);
+  const int idx = blockIdx.x;
+  if (n <= 0 || idx >= L.cnt[0] || !L.ivfail[idx]) return;
+  const cplx mu0{L.cmu[2 * idx], L.cmu[2 * idx + 1]};
+  const bool cx = mu0.im != 0.0;
+  double* Ar = L.lu + (int64_t)idx * 2 * LDD * LDD;  // column-major n x n
+  double* Ai = Ar + (int64_t)LDD * LDD;
+  __shared__ double xr[D_MAX], xi[D_MAX];
+  __shared__ int perm[D_MAX];
+  __shared__ double red[32];
+  __shared__ double bc[4];
+  __shared__ unsigned long long redu[32];
+  const double* M = L.M;
+  double mnorm = 0.0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    const double v = M[i + (int64_t)j * LDD];
+    Ar[i + (int64_t)j * LDD] = v - (i == j ? mu0.re : 0.0);
+    Ai[i + (int64_t)j * LDD] = (i == j) ? -mu0.im : 0.0;
+    mnorm = fmax(mnorm, fabs(v));
+  }
+  {  // block max via the u64 bit pattern of a non-negative double
+    unsigned long long b = (unsigned long long)__double_as_longlong(mnorm);
+    b = block_max_u64(b, redu);
+    mnorm = __longlong_as_double((long long)b);
+  }
+  const double tiny = fmax(mnorm, 1e-300) * 2.220446049250313e-16 * (double)n;
+  __syncthreads();
+  // LU with partial pivoting (pivot by |re| + |im|)
+  for (int k = 0; k < n; ++k) {
+    unsigned long long best = 0ull;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      const double a = fabs(Ar[i + (int64_t)k * LDD]) + (cx ? fabs(Ai[i + (int64_t)k * LDD]) : 0.0);
+      // pack (magnitude bits, row) so that the max picks the largest, ties the lowest row
+      const unsigned long long key = ((unsigned long long)__double_as_longlong(a) & ~0x3FFull) |
+                                     (unsigned long long)(0x3FF - i);
+      best = key > best ? key : best;
+    }
+    best = block_max_u64(best, redu);
+    const int p = 0x3FF - (int)(best & 0x3FF);
+    if (threadIdx.x == 0) perm[k] = p;
+    if (p != k) {
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double t = Ar[k + (int64_t)j * LDD];
+        Ar[k + (int64_t)j * LDD] = Ar[p + (int64_t)j * LDD];
+        Ar[p + (int64_t)j * LDD] = t;
+        if (cx) {
+          t = Ai[k + (int64_t)j * LDD];
+          Ai[k + (int64_t)j * LDD] = Ai[p + (int64_t)j * LDD];
+          Ai[p + (int64_t)j * LDD] = t;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      cplx d{Ar[k + (int64_t)k * LDD], cx ? Ai[k + (int64_t)k * LDD] : 0.0};
+      if (d.re == 0.0 && d.im == 0.0) {
+        d.re = tiny;
+        Ar[k + (int64_t)k * LDD] = tiny;
+      }
+      const cplx inv = crecip(d);
+      bc[0] = inv.re;
+      bc[1] = inv.im;
+    }
+    __syncthreads();
+    const cplx inv{bc[0], bc[1]};
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      if (cx) {
+        const cplx l = cmul(cplx{Ar[i + (int64_t)k * LDD], Ai[i + (int64_t)k * LDD]}, inv);
+        Ar[i + (int64_t)k * LDD] = l.re;
+        Ai[i + (int64_t)k * LDD] = l.im;
+      } else {
+        Ar[i + (int64_t)k * LDD] *= inv.re;
+      }
+    }
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = k + 1 + e % m, j = k + 1 + e / m;
+      if (cx) {
+        const cplx l{Ar[i + (int64_t)k * LDD], Ai[i + (int64_t)k * LDD]};
+        const cplx u{Ar[k + (int64_t)j * LDD], Ai[k + (int64_t)j * LDD]};
+        const cplx a = csub(cplx{Ar[i + (int64_t)j * LDD], Ai[i + (int64_t)j * LDD]}, cmul(l, u));
+        Ar[i + (int64_t)j * LDD] = a.re;
+        Ai[i + (int64_t)j * LDD] = a.im;
+      } else {
+        Ar[i + (int64_t)j * LDD] = fma(-Ar[i + (int64_t)k * LDD], Ar[k + (int64_t)j * LDD], Ar[i + (int64_t)j * LDD]);
+      }
+    }
+    __syncthreads();
+  }
+  // inverse iteration from x = (1, ..., 1); the reciprocals of U's diagonal
+  // are formed once, in parallel, so the back substitution only multiplies
+  __shared__ double udr[D_MAX], udi[D_MAX];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const cplx inv = crecip(cplx{Ar[k + (int64_t)k * LDD], cx ? Ai[k + (int64_t)k * LDD] : 0.0});
+    udr[k] = inv.re;
+    udi[k] = inv.im;
+  }
+  // the row interchanges of the factorisation as one permutation: row k of
+  // P x is x[sig[k]]
+  __shared__ int sig[D_MAX];
+  __shared__ double yr[D_MAX], yi[D_MAX];
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < n; ++k) sig[k] = k;
+    for (int k = 0; k < n; ++k) {
+      const int p = perm[k];
+      const int t = sig[k];
+      sig[k] = sig[p];
+      sig[p] = t;
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { xr[i] = 1.0; xi[i] = 0.0; }
+  __syncthreads();
+  // The triangular solves: thread t owns row t (n <= D_MAX <= blockDim.x)
+  // and keeps the next PF entries of its row of L (or U) in flight, so the
+  // L2 latency of the factors stays off the column-by-column chain; one
+  // barrier of the first nb threads per column.
+  constexpr int PF = 4;
+  const int t = threadIdx.x;
+  const bool own = t < n;
+  const int nb = (n + 31) / 32 * 32;
+  const bool inb = t < nb;
+  for (int it = 0; it < 3; ++it) {
+    if (own) {
+      yr[t] = xr[sig[t]];
+      yi[t] = xi[sig[t]];
+    }
+    __syncthreads();
+    if (inb) {
+      // L y = P x (unit lower): at column k, rows t > k take y_k
+      cplx lp[PF];
+#pragma unroll
+      for (int u = 0; u < PF; ++u)
+        lp[u] = (own && u < t) ? cplx{Ar[t + (int64_t)u * LDD], cx ? Ai[t + (int64_t)u * LDD] : 0.0} : cplx{0.0, 0.0};
+      for (int k0 = 0; k0 < n; k0 += PF) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+          const int k = k0 + u;
+          if (k < n) {
+            if (own && t > k) {
+              const cplx v = csub(cplx{yr[t], yi[t]}, cmul(lp[u], cplx{yr[k], yi[k]}));
+              yr[t] = v.re;
+              yi[t] = v.im;
+            }
+            const int kn = k + PF;
+            lp[u] = (own && kn < t) ? cplx{Ar[t + (int64_t)kn * LDD], cx ? Ai[t + (int64_t)kn * LDD] : 0.0}
+                                    : cplx{0.0, 0.0};
+            asm volatile("bar.sync 2, %0;" ::"r"(nb) : "memory");
+          }
+        }
+      }
+      // U x = y (upper), columns from the last: x_k = y_k / u_kk, then rows t < k
+      cplx up[PF];
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int kk = n - 1 - u;
+        up[u] = (own && kk > t) ? cplx{Ar[t + (int64_t)kk * LDD], cx ? Ai[t + (int64_t)kk * LDD] : 0.0}
+                                : cplx{0.0, 0.0};
+      }
+      for (int k0 = n - 1; k0 >= 0; k0 -= PF) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+          const int k = k0 - u;
+          if (k >= 0) {
+            const cplx xk = cmul(cplx{yr[k], yi[k]}, cplx{udr[k], udi[k]});
+            if (own && t < k) {
+              const cplx v = csub(cplx{yr[t], yi[t]}, cmul(up[u], xk));
+              yr[t] = v.re;
+              yi[t] = v.im;
+            }
+            if (t == k) {
+              xr[k] = xk.re;
+              xi[k] = xk.im;
+            }
+            const int kn = k - PF;
+            up[u] = (own && kn > t && kn >= 0)
+                        ? cplx{Ar[t + (int64_t)kn * LDD], cx ? Ai[t + (int64_t)kn * LDD] : 0.0}
+                        : cplx{0.0, 0.0};
+            asm volatile("bar.sync 2, %0;" ::"r"(nb) : "memory");
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // normalise by the entry of largest |re| + |im| (ties: lowest index)
+    unsigned long long key = 0ull;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double a = fabs(xr[i]) + fabs(xi[i]);
+      const unsigned long long kk =
+          ((unsigned long long)__double_as_longlong(a) & ~0x3FFull) | (unsigned long long)(0x3FF - i);
+      key = kk > key ? kk : key;
+    }
+    key = block_max_u64(key, redu);
+    const int bi = 0x3FF - (int)(key & 0x3FF);
+    const cplx piv{xr[bi], xi[bi]};
+    const cplx inv = (piv.re == 0.0 && piv.im == 0.0) ? cplx{1.0, 0.0} : crecip(piv);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const cplx v = cmul(cplx{xr[i], xi[i]}, inv);
+      xr[i] = v.re;
+      xi[i] = cx ? v.im : 0.0;
+    }
+    __syncthreads();
+  }
+  // Rayleigh quotient mu = x^H M x / x^H x
+  double nr = 0.0, ni = 0.0, dd = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double yr = 0.0, yi = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double mij = M[i + (int64_t)j * LDD];
+      yr = fma(mij, xr[j], yr);
+      yi = fma(mij, xi[j], yi);
+    }
+    // conj(x_i) * y_i
+    nr += xr[i] * yr + xi[i] * yi;
+    ni += xr[i] * yi - xi[i] * yr;
+    dd += xr[i] * xr[i] + xi[i] * xi[i];
+  }
+  nr = block_sum(nr, red);
+  ni = block_sum(ni, red);
+  dd = block_sum(dd, red);
+  if (threadIdx.x == 0) {
+    L.cref[2 * idx] = nr / dd;
+    L.cref[2 * idx + 1] = cx ? ni / dd : 0.0;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    L.cvec[i + (int64_t)(2 * idx) * LDD] = xr[i];
+    L.cvec[i + (int64_t)(2 * idx + 1) * LDD] = xi[i];
   }
 }
 
@@ -1710,7 +1991,10 @@ cudaError_t launch_cycle_end_part(int part, const WS& ws, int kh, int ucur, cons
       break;
     }
     case 4: k_ce_eig<<<1, 512, ce_eig_smem(), st>>>(ws); break;
-    case 5: k_ce_invit<<<KC, IV_T, ce_invit_smem(), st>>>(ws); break;
+    case 5:
+      k_ce_invit<<<KC, IV_T, ce_invit_smem(), st>>>(ws);
+      k_ce_invit64<<<KC, 512, 0, st>>>(ws);  // the candidates the refinement left, if any
+      break;
     case 6: k_ce_select<<<1, 256, 0, st>>>(ws); break;
     case 7: k_ce_finish<<<1, 512, 0, st>>>(ws, kh, ucur); break;
     case 8: k_ce_sketch_update<<<K_MAX, 512, 0, st>>>(ws, kh, SU, SAU, SUn, SAUn); break;
