@@ -54,9 +54,11 @@ UNIT = "ms/system"
 # whenever it runs in the same process.
 STEP_EQUIV_PER_SYSTEM = 400
 # DRAM bytes (read + write) per row of one k_spmv_dots launch, from an ncu capture of that
-# kernel at 96^3 (dram__bytes_read.sum + dram__bytes_write.sum, 110.6 MB per launch at
-# 884,736 rows); set to None when the kernel changes until it is captured again.
-SPMV_DRAM_BYTES_PER_ROW = (106.546e6 + 4.053e6) / 884736
+# kernel at 96^3 (dram__bytes_read.sum + dram__bytes_write.sum over three launches: 106.55 MB
+# read and 0.78 to 4.23 MB written per launch, mean 108.6 MB, at 884,736 rows; the write
+# share depends on when L2 writes w back); set to None when the kernel changes until it is
+# captured again.
+SPMV_DRAM_BYTES_PER_ROW = (106.552e6 + 2.058e6) / 884736
 
 
 def peaks():

@@ -979,6 +979,7 @@ size_t ce_eig_smem() { return ((size_t)(D_MAX + 1) * D_MAX + 2 * D_MAX + 64) * s
 // M is scaled by a power of two 2^-e (exact) before rounding to FP32.
 // ---------------------------------------------------------------------------
 constexpr int IV_T = 512;
+static_assert(IV_T >= D_MAX && IV_T % 32 == 0, "the solves give each row of M its own thread");
 constexpr int IV_STEPS = 2;   // inverse-iteration solves before the refinement
 constexpr int DMW_STEPS = 3;  // refinement steps
 constexpr int IV_NQ = (D_MAX + 31) / 32;  // rows per lane in the LU update
@@ -1009,12 +1010,17 @@ struct IvShared {
 // dimension ld, in shared memory: unit lower L below the diagonal, U on and
 // above it, rows exchanged across the whole matrix (L included) and perm[k]
 // the row exchanged with row k at step k.  A zero pivot is replaced by tiny.
-// Block-wide, two barriers per step.  Warp 0 stores the previous step's
-// multipliers (its registers) and pivot, and finds the pivot of column k;
-// then every warp forms the multipliers of its lanes' rows i = k + 1 + lane +
-// 32 q from column k, exchanges rows k and p on its columns j = wid (mod nw)
-// and updates them column by column, over the row strips below k only.
-__device__ void iv_lu(float* Ar, float* Ai, int ld, int n, bool cx, int* perm, float tiny, IvShared& sh) {
+// Kept out of line (as is iv_solve): inlined into k_ce_invit, whose FP64
+// values stay live across it, the loops below picked up FP64 instructions
+// (about 30,000 per factorisation, measured), each holding a sub-partition's
+// FP64 pipe for tens of cycles; out of line the factorisation runs without
+// them and takes 0.25 ms instead of 0.40 ms at n = 121.
+// Block-wide, two or three barriers per step.  Warp 0 stores the previous
+// step's multipliers (its registers) and pivot, and finds the pivot of column
+// k; every warp forms the multipliers of its lanes' rows i = k + 1 + lane +
+// 32 q from column k; the block exchanges rows k and p; then warp w updates
+// its columns j = w (mod nw) one by one, over the row strips below k only.
+__device__ __noinline__ void iv_lu(float* Ar, float* Ai, int ld, int n, bool cx, int* perm, float tiny, IvShared& sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   cf l[IV_NQ];
 #pragma unroll
@@ -1085,9 +1091,10 @@ __device__ void iv_lu(float* Ar, float* Ai, int ld, int n, bool cx, int* perm, f
         l[q] = cf{0.f, 0.f};
       }
     }
-    // row exchange on this warp's columns (one lane per column), then the update
+    // row exchange, one thread per column (consecutive columns, an odd ld: no bank
+    // conflicts), then the update
     if (p != k) {
-      for (int j = wid + nw * lane; j < n; j += 32 * nw) {
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
         if (j == k) continue;
         float t = Ar[k + j * ld];
         Ar[k + j * ld] = Ar[p + j * ld];
@@ -1098,8 +1105,8 @@ __device__ void iv_lu(float* Ar, float* Ai, int ld, int n, bool cx, int* perm, f
           Ai[p + j * ld] = t;
         }
       }
+      __syncthreads();
     }
-    __syncwarp();
     int j = wid;
     while (j <= k) j += nw;  // this warp's first column right of k
     for (; j < n; j += nw) {
@@ -1142,13 +1149,13 @@ __device__ void iv_perm(const int* perm, int n, int* sig) {
   }
 }
 
-// Solve L U y = (yr, yi) in place (y already permuted) with the first
+// Solve L U y = (yr, yi) in place (y already permuted; out of line, as iv_lu) with the first
 // nb = 32 ceil(n / 32) threads: thread t owns row t and loads the next
 // column's factor entry of its row ahead of time; the value of column k
 // passes through shared memory (alternating slots) with one named barrier of
 // those threads per column.  (udr, udi): reciprocals of U's diagonal; slot:
 // 8 floats of shared memory.
-__device__ void iv_solve(const float* Ar, const float* Ai, int ld, int n, bool cx, float* yr, float* yi,
+__device__ __noinline__ void iv_solve(const float* Ar, const float* Ai, int ld, int n, bool cx, float* yr, float* yi,
                          const float* udr, const float* udi, float* slot) {
   const int t = threadIdx.x;
   const int nb = (n + 31) & ~31;
@@ -1287,7 +1294,7 @@ __global__ void __launch_bounds__(IV_T, 1) k_ce_invit(WS ws) {
   float* udi = udr + D_MAX;
   int* perm = (int*)(udi + D_MAX);
   int* sig = perm + D_MAX;
-  const int ld = n + 1;
+  const int ld = n | 1;  // odd: a row walk across columns hits every bank once
   float* Ar = (float*)(sig + D_MAX);
   float* Ai = Ar + (size_t)ld * n;
   __shared__ IvShared sh;
@@ -1298,7 +1305,8 @@ __global__ void __launch_bounds__(IV_T, 1) k_ce_invit(WS ws) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double* __restrict__ M = L.M;
   const double mu_r = L.cmu[2 * idx], mu_i = L.cmu[2 * idx + 1];
-  const bool cx = mu_i != 0.0;
+  // Complex candidate: Im mu0 != 0, tested on its bits (no FP64 instruction).
+  const bool cx = ((unsigned long long)__double_as_longlong(mu_i) << 1) != 0ull;
   // the power-of-two scale of M (loads of a column issued together)
   unsigned long long mb = 0ull;
   for (int j = wid; j < n; j += nw) {
