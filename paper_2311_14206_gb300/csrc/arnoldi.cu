@@ -12,6 +12,8 @@
 // Basis columns are stored unnormalised (v_hat); alpha_c = 1/||v_hat_c|| lives
 // in the control block and is folded into every coefficient that touches a
 // column, which saves a normalisation pass per step.
+#include <type_traits>
+
 #include "launch.cuh"
 #include "eidot.cuh"
 
@@ -667,21 +669,55 @@ cudaError_t launch_sketch_col(const WS& ws, const T* x, int j, cudaStream_t st) 
 // Arnoldi step j, part 2: v_hat_{j+1} = a_0 w - sum_i a_i v_hat_i, with
 // ||v_hat_{j+1}||^2, its dots with the t-1 newest window vectors and its max
 // magnitude as per-CTA partials (part2).  Pure streaming: many rows per thread.
+// In FP64 the update itself takes three FP64 operations per row; the squared
+// norm and the window dots run on the integer pipe instead (eidot.cuh): each
+// row's v_hat_{j+1} is rounded to 52 bits of the bound the SpMV recorded for
+// it (|v_hat_{j+1}| < 2^E, E = vtop[j+1] - win_bits - 2), each window entry to
+// 52 bits of its column's maximum, and the products are summed exactly; the
+// thread's sums are rounded to FP64 once every UPD_FLUSH rows.  A non-finite
+// v_hat_{j+1} makes the CTA's norm partial NaN (the column is then a breakdown).
 // ---------------------------------------------------------------------------
+constexpr int UPD_FLUSH = 1024;  // rows per exact integer run (Acc3 holds 2048 terms)
+
+// q52 for a value that may break the vector's bound (a non-finite one): 0 then;
+// the caller flags non-finite values through the maximum.
+__device__ __forceinline__ Q52 q52_safe(double x, int emax) {
+  const int ex = bexp(x);
+  if (ex > emax) return Q52{0, 0u};
+  return q52(x, emax, 0);
+}
+
 template <typename T, int NW, int NC>  // NW window vectors, NC = t - 1 dots kept for the next window
 __global__ void __launch_bounds__(256) k_update(WS ws, Win<T> win, T* __restrict__ vnext, int j) {
   Ctl* c = ws.ctl;
   if (arnoldi_stopped(c, j)) return;
   __shared__ double buf[256];
   __shared__ unsigned long long redu[32];
+  constexpr bool kExact = std::is_same<T, double>::value;
   T cf[NW + 1];
 #pragma unroll
   for (int a = 0; a <= NW; ++a) cf[a] = (T)c->coef[a];
   const T* __restrict__ w = (const T*)ws.Wv;
+  constexpr int NCX = NC > 0 ? NC : 1;
+  double nrm_d = 0.0, cr_d[NCX];
   T nrm = 0;
-  T cr[NC > 0 ? NC : 1];
+  T cr[NCX];
 #pragma unroll
-  for (int q = 0; q < (NC > 0 ? NC : 1); ++q) cr[q] = 0;
+  for (int q = 0; q < NCX; ++q) {
+    cr[q] = 0;
+    cr_d[q] = 0.0;
+  }
+  // fixed-point exponents (biased): v_hat_{j+1} against its bound, window columns
+  // against their maxima
+  const int ev = c->vtop[j + 1] - ws.win_bits - 2 + 1022;
+  int ew[NCX];
+#pragma unroll
+  for (int q = 0; q < NCX; ++q) ew[q] = (q < NC && q < NW) ? bexp_of_bits(c->vmax[win.lo + NW - 1 - q]) : 0;
+  Acc3 an, ac[NCX];
+  an.zero();
+#pragma unroll
+  for (int q = 0; q < NCX; ++q) ac[q].zero();
+  int run = 0;
   unsigned long long vm = 0ull;
   const int64_t n = ws.n, stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
@@ -692,21 +728,49 @@ __global__ void __launch_bounds__(256) k_update(WS ws, Win<T> win, T* __restrict
 #pragma unroll
     for (int a = 0; a < NW; ++a) v = fma(-cf[1 + a], wv[a], v);
     vnext[r] = v;
-    nrm = fma(v, v, nrm);
+    if constexpr (kExact) {
+      const Q52 qv = q52_safe((double)v, ev);
+      an.mac(qv, qv);
 #pragma unroll
-    for (int q = 0; q < NC; ++q)
-      if (q < NW) cr[q] = fma(v, wv[NW - 1 - q], cr[q]);
+      for (int q = 0; q < NC; ++q)
+        if (q < NW) ac[q].mac(qv, q52_safe((double)wv[NW - 1 - q], ew[q]));
+      if (++run == UPD_FLUSH) {
+        nrm_d += acc_to_double(an, 2 * (ev - 1073));
+        an.zero();
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          cr_d[q] += acc_to_double(ac[q], (ev - 1073) + (ew[q] - 1073));
+          ac[q].zero();
+        }
+        run = 0;
+      }
+    } else {
+      nrm = fma(v, v, nrm);
+#pragma unroll
+      for (int q = 0; q < NC; ++q)
+        if (q < NW) cr[q] = fma(v, wv[NW - 1 - q], cr[q]);
+    }
     const unsigned long long u = abs_bits((double)v);
     vm = u > vm ? u : vm;
   }
-  const double nrm_b = block_sum_lean((double)nrm, buf);
-  double cr_b[NC > 0 ? NC : 1];
+  if constexpr (kExact) {
+    nrm_d += acc_to_double(an, 2 * (ev - 1073));
 #pragma unroll
-  for (int q = 0; q < NC; ++q) cr_b[q] = block_sum_lean((double)cr[q], buf);
+    for (int q = 0; q < NC; ++q) cr_d[q] += acc_to_double(ac[q], (ev - 1073) + (ew[q] - 1073));
+  } else {
+    nrm_d = (double)nrm;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) cr_d[q] = (double)cr[q];
+  }
+  const double nrm_b = block_sum_lean(nrm_d, buf);
+  double cr_b[NCX];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) cr_b[q] = block_sum_lean(cr_d[q], buf);
   vm = block_max_u64(vm, redu);
   if (threadIdx.x == 0) {
     double* pp = ws.part2 + blockIdx.x * NPART;
-    pp[0] = nrm_b;
+    // a non-finite entry (its magnitude bits at or above those of Inf) poisons the norm
+    pp[0] = vm >= 0x7FF0000000000000ull ? __longlong_as_double(0x7FF8000000000000ll) : nrm_b;
 #pragma unroll
     for (int q = 0; q < NC; ++q) pp[1 + q] = cr_b[q];
     pp[T_MAX] = __longlong_as_double((long long)vm);
