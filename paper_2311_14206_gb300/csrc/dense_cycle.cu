@@ -879,22 +879,39 @@ __global__ void __launch_bounds__(512, 1) k_ce_eig(WS ws) {
       tau_s = tau;
     }
     __syncthreads();
-    // left: each thread owns a column jj >= col+1
-    for (int jj = col + 1 + threadIdx.x; jj < n; jj += blockDim.x) {
-      float w = HF(H, ldh, col + 1, jj);
-      for (int i = col + 2; i < n; ++i) w += HF(H, ldh, i, col) * HF(H, ldh, i, jj);
-      w *= tau_s;
-      HF(H, ldh, col + 1, jj) -= w;
-      for (int i = col + 2; i < n; ++i) HF(H, ldh, i, jj) -= w * HF(H, ldh, i, col);
+    // left: four threads per column jj >= col+1, each a quarter of the rows
+    // (interleaved), the dot reduced over the four lanes by shuffles
+    for (int base = 4 * (col + 1); base < 4 * n; base += blockDim.x) {
+      const int g = base + threadIdx.x, jj = g >> 2, sub = g & 3;
+      const bool on = jj < n;
+      float w = 0.f;
+      const float h1 = on ? HF(H, ldh, col + 1, jj) : 0.f;  // read before the shuffles: sub 0 writes it after
+      if (on)
+        for (int i = col + 2 + sub; i < n; i += 4) w += HF(H, ldh, i, col) * HF(H, ldh, i, jj);
+      w += __shfl_xor_sync(0xffffffffu, w, 1);
+      w += __shfl_xor_sync(0xffffffffu, w, 2);
+      if (on) {
+        w = (w + h1) * tau_s;
+        if (sub == 0) HF(H, ldh, col + 1, jj) -= w;
+        for (int i = col + 2 + sub; i < n; i += 4) HF(H, ldh, i, jj) -= w * HF(H, ldh, i, col);
+      }
     }
     __syncthreads();
-    // right: each thread owns a row i
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      float w = HF(H, ldh, i, col + 1);
-      for (int jj = col + 2; jj < n; ++jj) w += HF(H, ldh, i, jj) * HF(H, ldh, jj, col);
-      w *= tau_s;
-      HF(H, ldh, i, col + 1) -= w;
-      for (int jj = col + 2; jj < n; ++jj) HF(H, ldh, i, jj) -= w * HF(H, ldh, jj, col);
+    // right: four threads per row i, each a quarter of the columns (interleaved)
+    for (int base = 0; base < 4 * n; base += blockDim.x) {
+      const int g = base + threadIdx.x, i = g >> 2, sub = g & 3;
+      const bool on = i < n;
+      float w = 0.f;
+      const float h1 = on ? HF(H, ldh, i, col + 1) : 0.f;  // read before the shuffles: sub 0 writes it after
+      if (on)
+        for (int jj = col + 2 + sub; jj < n; jj += 4) w += HF(H, ldh, i, jj) * HF(H, ldh, jj, col);
+      w += __shfl_xor_sync(0xffffffffu, w, 1);
+      w += __shfl_xor_sync(0xffffffffu, w, 2);
+      if (on) {
+        w = (w + h1) * tau_s;
+        if (sub == 0) HF(H, ldh, i, col + 1) -= w;
+        for (int jj = col + 2 + sub; jj < n; jj += 4) HF(H, ldh, i, jj) -= w * HF(H, ldh, jj, col);
+      }
     }
     __syncthreads();
   }
