@@ -592,7 +592,8 @@ def run_form_paper_cd(args):
     n = 500, alpha = 0, 5, 20, b = ones, 80 Arnoldi steps + 20 recycled, at most
     10 restarts, target 1e-2 relative) through the C ABI: exact recycling, the
     inexact variant and the inexact variant with the stale-SAU rule, with the
-    sparse sign and with the paper's subsampled DCT (s = 480).  Reports products
+    sparse sign and with the paper's subsampled DCT (s = 480), and the paper's
+    own configuration (the DCT at s = 640).  Reports products
     with A (Arnoldi steps + true-residual checks + the k products of each exact
     recycle, counted as the paper counts matrix-vector products) and the time
     per problem, beside the oracle's counts for the same runs."""
@@ -607,21 +608,23 @@ def run_form_paper_cd(args):
     mats = [P.CSRDevice.from_numpy(A) for A in As]
     b = torch.ones(N, dtype=torch.float64, device="cuda")
     gold = {}
-    for sk, fname in (("sparse_sign", "paper_cd_sparse_sign_s480.json"), ("dct", "paper_cd_dct_s480.json")):
+    sketches = (("sparse_sign", 0, 480, "paper_cd_sparse_sign_s480.json"), ("dct", 1, 480, "paper_cd_dct_s480.json"),
+                ("dct_s640", 1, 640, "paper_cd_dct_s640.json"))
+    for sk, _, _, fname in sketches:
         path = os.path.join(ROOT, "tests", "golden", fname)
         if os.path.exists(path):
             with open(path) as f:
                 gold[sk] = json.load(f)["variants"]
     runs = {}
-    for sk in ("sparse_sign", "dct"):
+    for sk, kind, s_, _ in sketches:
         for variant in ("exact", "inexact", "inexact_stale_check"):
-            if sk == "dct" and variant == "inexact_stale_check":
+            if kind == 1 and variant == "inexact_stale_check":
                 continue
-            solver = P.Solver(N, cfg["m"], cfg["k"], cfg["t"], cfg["s"], cfg["zeta"], cfg["seed"], cfg["rel_tol"],
+            solver = P.Solver(N, cfg["m"], cfg["k"], cfg["t"], s_, cfg["zeta"], cfg["seed"], cfg["rel_tol"],
                               max_cycles=cfg["max_cycles"], stale_check=variant == "inexact_stale_check",
-                              sketch_kind=1 if sk == "dct" else 0)
-            if sk == "dct":
-                solver.set_sketch_draws(*W.dct_draws(cfg["seed"], N, cfg["s"]))
+                              sketch_kind=kind)
+            if kind == 1:
+                solver.set_sketch_draws(*W.dct_draws(cfg["seed"], N, s_))
             probs, total_mv, total_ms = [], 0, 0.0
             for rep in range(2):  # the first pass captures the cycle graphs
                 probs, total_mv, total_ms = [], 0, 0.0
@@ -657,7 +660,8 @@ def run_form_paper_cd(args):
                     zeta=cfg["zeta"], rel_tol=cfg["rel_tol"], max_cycles=cfg["max_cycles"],
                     timing="host wall clock per problem (each solve synchronises every cycle), second pass"),
         runs=runs, paper_table_matvecs=PAPER_CD_TABLE,
-        note="the paper's counts were taken in MATLAB with a DCT sketch of s = 640; context, not a target")
+        note="the paper's counts were taken in MATLAB with a DCT sketch of s = 640 (its own draws); the "
+             "dct_s640 runs use the same sketch family and size with this repository's draws; context, not a target")
 
 
 # --------------------------------------------------------------------------- oracle arm

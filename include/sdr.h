@@ -59,7 +59,7 @@ typedef enum {
  *              (k+1)-th harmonic Ritz values form a conjugate pair. 0 <= k <= 31.
  *   t          truncation window of the Arnoldi process, 1 <= t <= 4.
  *   s, zeta    sketch rows and nonzeros per sketch column; needs
- *              m + k + 2 <= s <= 512 and 1 <= zeta <= min(s, 32).
+ *              m + k + 2 <= s <= 768 and 1 <= zeta <= min(s, 32).
  *   seed       seed of the hash that defines S (fixed for the handle's life,
  *              so that SU and SAU remain valid from one system to the next).
  *   rel_tol    stop when ||b - A x|| < rel_tol * ||b||.

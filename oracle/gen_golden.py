@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring): never imported by the
 product path.
 
-Usage: python -m oracle.gen_golden [sketch | batch | paper_cd | paper_cd_dct]
+Usage: python -m oracle.gen_golden [sketch | batch | paper_cd | paper_cd_dct | paper_cd_dct640]
 """
 import json
 import os
@@ -97,20 +97,23 @@ PAPER_CD = dict(n=500, alpha=[0.0, 5.0, 20.0], m=80, k=20, t=2, s=480, zeta=8, r
                 seed=231114206)
 
 
-def write_paper_cd(dct=False):
-    """dct: the paper's own sketch (a subsampled randomised DCT, Section 6) at
-    s = 480 instead of the sparse sign (exact and inexact variants)."""
+def write_paper_cd(dct=False, s=None):
+    """dct: the paper's own sketch (a subsampled randomised DCT, Section 6)
+    instead of the sparse sign (exact and inexact variants); s: the sketch size
+    (default 480; the paper's is 8 m_max = 640)."""
     import workloads as W
     from . import sdr as O
     from .sketch import SubsampledDCT
-    p = PAPER_CD
+    p = dict(PAPER_CD)
+    if s is not None:
+        p["s"] = s
     As = [W.make_cd_paper(p["n"], a) for a in p["alpha"]]
     N = As[0].n
     b = np.ones(N)
     S = SubsampledDCT(p["seed"], N, p["s"]) if dct else SparseSign(p["seed"], N, p["s"], p["zeta"])
     kw = dict(m=p["m"], k=p["k"], t=p["t"], rel_tol=p["rel_tol"], max_cycles=p["max_cycles"])
-    doc = dict(description="Oracle runs of the paper's Section 6.3 sequence with the %s sketch at s = 480; "
-                           "written by oracle.gen_golden." % ("subsampled DCT" if dct else "sparse-sign"),
+    doc = dict(description="Oracle runs of the paper's Section 6.3 sequence with the %s sketch at s = %d; "
+                           "written by oracle.gen_golden." % ("subsampled DCT" if dct else "sparse-sign", p["s"]),
                params=p, variants={})
     variants = (("exact", True, False), ("inexact", False, False)) if dct else \
         (("exact", True, False), ("inexact", False, False), ("inexact_stale_check", False, True))
@@ -128,7 +131,7 @@ def write_paper_cd(dct=False):
         doc["variants"][name] = dict(problems=runs, total_matvecs=int(sum(r_["matvecs"] for r_ in runs)),
                                      oracle_seconds=time.time() - t0)
         print(name, [(r_["converged"], r_["cycles"], r_["matvecs"]) for r_ in runs], flush=True)
-    name = "paper_cd_dct_s480.json" if dct else "paper_cd_sparse_sign_s480.json"
+    name = "paper_cd_%s_s%d.json" % ("dct" if dct else "sparse_sign", p["s"])
     with open(os.path.join(GOLDEN, name), "w") as f:
         json.dump(doc, f, indent=1)
 
@@ -143,3 +146,5 @@ if __name__ == "__main__":
         write_paper_cd()
     if "paper_cd_dct" in what:
         write_paper_cd(dct=True)
+    if "paper_cd_dct640" in what:
+        write_paper_cd(dct=True, s=640)

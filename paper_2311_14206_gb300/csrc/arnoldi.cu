@@ -440,7 +440,8 @@ __device__ __forceinline__ void spmv_dots_finish(const WS& ws, const Win<T>& win
 // pipes while the FP64 pipe runs the SpMV).  The last CTA finishes column j
 // and turns the dots into the MGS coefficients H(i, j).
 // ---------------------------------------------------------------------------
-template <typename T, int NW, bool SK>  // NW window vectors v_hat_lo .. v_hat_j; SK: sketch v_hat_j
+template <typename T, int NW, bool SK, int RPT>  // NW window vectors v_hat_lo .. v_hat_j; SK: sketch v_hat_j;
+                                                 // RPT sketch rows per thread (s <= RPT SK_THREADS)
 __global__ void __launch_bounds__(SK_THREADS, 3) k_spmv_dots(WS ws, CsrDev A, Win<T> win, int j, int grid2) {
   Ctl* c = ws.ctl;
   if (arnoldi_stopped(c, j)) return;
@@ -460,9 +461,9 @@ __global__ void __launch_bounds__(SK_THREADS, 3) k_spmv_dots(WS ws, CsrDev A, Wi
 #pragma unroll
   for (int a = 0; a < NW; ++a) d[a] = 0;
   unsigned long long wm = 0ull;
-  unsigned long long lo[SK_RPT], hi[SK_RPT];
+  unsigned long long lo[RPT], hi[RPT];
 #pragma unroll
-  for (int k = 0; k < SK_RPT; ++k) lo[k] = hi[k] = 0ull;
+  for (int k = 0; k < RPT; ++k) lo[k] = hi[k] = 0ull;
   const int64_t n = A.n;
   const int ntiles = (int)((n + tileR - 1) / tileR);
   // Fixed-point units of the window dots: |w_r| <= ||A||_inf max|v_hat_j| and
@@ -533,7 +534,7 @@ __global__ void __launch_bounds__(SK_THREADS, 3) k_spmv_dots(WS ws, CsrDev A, Wi
         if (ib < tileR) vals[ib] = vb_ ? (double)x[rb] : 0.0;
       }
     }
-    if (SK) tile_sketch_accumulate<SK_RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
+    if (SK) tile_sketch_accumulate<RPT>(ws, ncols, vals, ent_s, ptr_s, redu, top, lo, hi);
     // this thread's rows of the tile, summed in order, join its exact
     // fixed-point accumulators: the dots then do not depend on which CTA took
     // which tile
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(SK_THREADS, 3) k_spmv_dots(WS ws, CsrDev A, Wi
   }
   if (SK) {
 #pragma unroll
-    for (int k = 0; k < SK_RPT; ++k) {
+    for (int k = 0; k < RPT; ++k) {
       const int row = threadIdx.x + k * blockDim.x;
       if (row < ws.s) atomic_add128(ws.accV + (int64_t)j * 2 * S_MAX + 2 * row, lo[k], hi[k]);
     }
@@ -581,15 +582,22 @@ int update_grid(const WS& ws) {
 
 template <typename T, int NW, bool SK>
 static cudaError_t launch_spmv_t(const WS& ws, CsrDev A, const Win<T>& win, int j, cudaStream_t st) {
-  static bool attr = false;
-  cudaError_t e = set_smem((const void*)k_spmv_dots<T, NW, SK>, sketch_smem_bytes(ZETA_MAX), attr);
+  // the instance with two sketch rows per thread for s <= 512 (the common case; fewer
+  // registers), three otherwise
+  const bool wide = SK && ws.s > SK_RPT_SMALL * SK_THREADS;
+  static bool attr = false, attr_w = false;
+  cudaError_t e = wide ? set_smem((const void*)k_spmv_dots<T, NW, SK, SK_RPT>, sketch_smem_bytes(ZETA_MAX), attr_w)
+                       : set_smem((const void*)k_spmv_dots<T, NW, SK, SK_RPT_SMALL>, sketch_smem_bytes(ZETA_MAX), attr);
   if (e != cudaSuccess) return e;
   const size_t sm = SK ? sketch_smem_bytes(ws.zeta) : 0;
   // three CTAs per SM are resident (register budget); tiles are handed out by a counter
   int g = grid_tiles(ws, A.n);
   const int g3 = 3 * (ws.grid_max / 8);
   if (g > g3) g = g3;
-  k_spmv_dots<T, NW, SK><<<g, SK_THREADS, sm, st>>>(ws, A, win, j, update_grid(ws));
+  if (wide)
+    k_spmv_dots<T, NW, SK, SK_RPT><<<g, SK_THREADS, sm, st>>>(ws, A, win, j, update_grid(ws));
+  else
+    k_spmv_dots<T, NW, SK, SK_RPT_SMALL><<<g, SK_THREADS, sm, st>>>(ws, A, win, j, update_grid(ws));
   return cudaGetLastError();
 }
 

@@ -24,9 +24,10 @@ namespace {
 
 constexpr int NA_TILE = 1024;     // columns per tile (at most 2^12 keeps tile sums below 2^63)
 constexpr int NA_THREADS = 256;
-constexpr int NA_RPT = S_MAX / NA_THREADS;
-constexpr int SCRATCH_WORDS = 2 * S_MAX + 64;  // 128-bit accumulators, then max|x|
-constexpr int SC_MAX = 2 * S_MAX;              // word holding the bits of max |x|
+constexpr int NA_S_MAX = 512;    // sketch rows this entry point serves (its fixed scratch)
+constexpr int NA_RPT = NA_S_MAX / NA_THREADS;
+constexpr int SCRATCH_WORDS = 2 * NA_S_MAX + 64;  // 128-bit accumulators, then max|x|
+constexpr int SC_MAX = 2 * NA_S_MAX;              // word holding the bits of max |x|
 constexpr int64_t NA_MAX_N = 2147483647;       // columns are 31-bit indices
 
 // The only device memory this entry point uses.
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_sketch(const double* __restri
                                                           int zeta, uint64_t seed, int win_bits,
                                                           unsigned long long* sc) {
   __shared__ double vals[NA_TILE];
-  __shared__ unsigned long long acc_s[S_MAX];
+  __shared__ unsigned long long acc_s[NA_S_MAX];
   __shared__ unsigned long long red[32];
   const double mx = __longlong_as_double((long long)sc[SC_MAX]);
   // x == 0: the cleared accumulators already hold S x.  A NaN or an Inf in x
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_sketch(const double* __restri
   unsigned long long lo[NA_RPT], hi[NA_RPT];
 #pragma unroll
   for (int k = 0; k < NA_RPT; ++k) lo[k] = hi[k] = 0ull;
-  for (int i = threadIdx.x; i < S_MAX; i += blockDim.x) acc_s[i] = 0ull;
+  for (int i = threadIdx.x; i < NA_S_MAX; i += blockDim.x) acc_s[i] = 0ull;
   const int64_t ntiles = (n + NA_TILE - 1) / NA_TILE;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t c0 = tile * NA_TILE;
@@ -145,7 +146,7 @@ cudaError_t scratch_address(unsigned long long** out) {
 extern "C" sdr_status sdr_sketch_noalloc(const double* x, int64_t n, int32_t s, int32_t zeta, uint64_t seed,
                                          double* y, void* stream) {
   using namespace sdr;
-  if (!x || !y || n < 1 || n > NA_MAX_N || s < 1 || s > S_MAX || zeta < 1 || zeta > s || zeta > ZETA_MAX)
+  if (!x || !y || n < 1 || n > NA_MAX_N || s < 1 || s > NA_S_MAX || zeta < 1 || zeta > s || zeta > ZETA_MAX)
     return SDR_ERR_INVALID_ARG;
   unsigned long long* sc = nullptr;
   if (scratch_address(&sc) != cudaSuccess) return SDR_ERR_CUDA;

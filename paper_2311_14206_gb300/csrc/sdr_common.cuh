@@ -8,7 +8,7 @@ namespace sdr {
 constexpr int M_MAX = 128;   // Krylov columns per cycle
 constexpr int K_MAX = 32;    // recycle columns (k + 1)
 constexpr int D_MAX = M_MAX + K_MAX;  // columns of SAW
-constexpr int S_MAX = 512;   // sketch rows
+constexpr int S_MAX = 768;   // sketch rows (the paper's experiments use s = 640)
 constexpr int T_MAX = 4;     // Arnoldi truncation window
 constexpr int ZETA_MAX = 32;
 constexpr int PTR_STRIDE = S_MAX + 8;  // per-tile row-pointer stride (16-byte multiple)
@@ -280,6 +280,7 @@ inline size_t sketch_smem_bytes(int zeta) {
 }
 constexpr int SK_THREADS = 256;              // threads of the tile-sketch kernels
 constexpr int SK_RPT = S_MAX / SK_THREADS;   // sketch rows per thread
+constexpr int SK_RPT_SMALL = 2;              // the same for s <= 2 SK_THREADS (the SpMV's lighter instance)
 
 // ---------------------------------------------------------------------------
 // Block-level helpers.

@@ -37,7 +37,7 @@ def test_host_side_validation_without_gpu():
     lib = S.load_library()
     h = ctypes.c_void_p()
     bad = [S.make_params(0, 4, 2, 40, 8, 1, 1e-8), S.make_params(20, 4, 5, 40, 8, 1, 1e-8),
-           S.make_params(20, 4, 2, 20, 8, 1, 1e-8), S.make_params(20, 4, 2, 600, 8, 1, 1e-8),
+           S.make_params(20, 4, 2, 20, 8, 1, 1e-8), S.make_params(20, 4, 2, 800, 8, 1, 1e-8),
            S.make_params(20, 4, 2, 40, 0, 1, 1e-8), S.make_params(20, 40, 2, 100, 8, 1, 1e-8),
            S.make_params(20, 4, 2, 40, 8, 1, -1.0),
            S.make_params(20, 4, 2, 40, 8, 1, 1e-8, precision=7),

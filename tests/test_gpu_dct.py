@@ -5,9 +5,10 @@ SubsampledDCT with the same draws (workloads.dct_draws).
 Bars: the sketch of random vectors within 1e-13 of ||S x|| (both sides sum in
 FP64, in different orders); a solve's first-cycle sketched residuals within
 1e-8 relative and its solution within 1e-6; the paper's Section 6.3 sequence
-with this sketch at s = 480 against the oracle's runs
-(tests/golden/paper_cd_dct_s480.json): convergence, cycles within one, and
-the inexact variant's failure on the third problem."""
+with this sketch at s = 480 and at the paper's own s = 640 against the
+oracle's runs (tests/golden/paper_cd_dct_s480.json, paper_cd_dct_s640.json):
+convergence, cycles within one, and the inexact variant's failure on the
+third problem."""
 import json
 import os
 
@@ -22,7 +23,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 SEED = 231114206
-GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_cd_dct_s480.json")
+GOLDEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.fixture(scope="module")
@@ -96,8 +97,10 @@ def test_dct_handle_rejects_other_sizes_and_bad_draws(P):
 
 
 @pytest.mark.parametrize("variant", ["exact", "inexact"])
-def test_section_6_3_with_the_papers_sketch(P, variant):
-    gold = json.load(open(GOLDEN))
+@pytest.mark.parametrize("golden", ["paper_cd_dct_s480.json", "paper_cd_dct_s640.json"])
+def test_section_6_3_with_the_papers_sketch(P, variant, golden):
+    """s = 640 is the paper's own size (8 m_max, Section 6)."""
+    gold = json.load(open(os.path.join(GOLDEN_DIR, golden)))
     p = gold["params"]
     ref = gold["variants"][variant]["problems"]
     As = [W.make_cd_paper(p["n"], a) for a in p["alpha"]]

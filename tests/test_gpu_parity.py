@@ -60,7 +60,8 @@ def principal_angle(X, Y):
 
 
 # ---------------------------------------------------------------- sketch
-@pytest.mark.parametrize("n,s,zeta", [(5000, 120, 8), (4096, 480, 8), (3000, 37, 3), (2500, 100, 1)])
+@pytest.mark.parametrize("n,s,zeta", [(5000, 120, 8), (4096, 480, 8), (3000, 37, 3), (2500, 100, 1), (6000, 768, 8),
+                                      (4500, 640, 8)])
 def test_sketch_columns_bit_exact(P, n, s, zeta):
     solver = P.Solver(n, m=10, k=2, t=2, s=s, zeta=zeta, seed=SEED)
     rng = np.random.default_rng(0)
@@ -149,7 +150,7 @@ def test_cd2d_64_cycle_replay(P):
 
 
 @pytest.mark.parametrize("t,k,zeta,s", [(1, 10, 8, 120), (3, 10, 8, 120), (4, 5, 4, 90), (2, 0, 8, 100),
-                                        (2, 10, 1, 120), (2, 10, 8, 62)])
+                                        (2, 10, 1, 120), (2, 10, 8, 62), (2, 10, 8, 640), (2, 10, 8, 768)])
 def test_parameter_edges_first_cycles(P, t, k, zeta, s):
     A = W.make_cd2d(40, (20.0, 5.0))  # N = 1600
     b = W.rhs(A.n, 7)
