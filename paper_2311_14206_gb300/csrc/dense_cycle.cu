@@ -37,6 +37,7 @@ struct CeLayout {
   int* cnt;   // [0] number of inverse iterations
   int* ivfail;  // [KC] candidate left to the FP64 fallback
   double* lu;   // KC blocks of 2*LDD*LDD (the fallback's complex LU)
+  float* H32;   // LDD x LDD: k_ce_eig's FP32 Hessenberg form of M with its reflectors below the subdiagonal
 };
 
 __host__ __device__ inline CeLayout ce_layout(double* base) {
@@ -63,12 +64,13 @@ __host__ __device__ inline CeLayout ce_layout(double* base) {
   L.cvec = L.cref + 2 * KC;
   L.ivfail = L.cnt + K_MAX;  // inside the 3 K_MAX doubles reserved after misc (6 K_MAX ints, KC <= 3 K_MAX)
   L.lu = L.cvec + (int64_t)2 * KC * LDD;
+  L.H32 = (float*)(L.lu + (int64_t)KC * 2 * LDD * LDD);
   return L;
 }
 
 size_t ce_scratch_doubles() {
   return (size_t)6 * LDD * LDD + 3 * LDD + 2 * (size_t)LDD * K_MAX + 2 * LDD + 64 + 3 * K_MAX + 4 * KC +
-         (size_t)2 * KC * LDD + (size_t)KC * 2 * LDD * LDD + 64;
+         (size_t)2 * KC * LDD + (size_t)KC * 2 * LDD * LDD + (size_t)LDD * LDD / 2 + 64;
 }
 
 // Column l of S[U V] / SAW (sketched basis / sketched image).
@@ -868,7 +870,10 @@ __global__ void __launch_bounds__(512, 1) k_ce_eig(WS ws) {
     float xs = 0.f;
     for (int i = col + 2 + threadIdx.x; i < n; i += blockDim.x) xs += HF(H, ldh, i, col) * HF(H, ldh, i, col);
     xs = block_sum_f(xs, red);
-    if (xs == 0.f) continue;
+    if (xs == 0.f) {  // already reduced: the identity (tau = 0, a zero reflector below)
+      if (threadIdx.x == 0) L.tauH[col] = 0.0;
+      continue;
+    }
     const float alpha = HF(H, ldh, col + 1, col);
     const float beta = -copysignf(sqrtf(alpha * alpha + xs), alpha);
     const float tau = (beta - alpha) / beta;
@@ -877,6 +882,7 @@ __global__ void __launch_bounds__(512, 1) k_ce_eig(WS ws) {
     if (threadIdx.x == 0) {
       HF(H, ldh, col + 1, col) = beta;
       tau_s = tau;
+      L.tauH[col] = (double)tau;
     }
     __syncthreads();
     // left: four threads per column jj >= col+1, each a quarter of the rows
@@ -915,6 +921,13 @@ __global__ void __launch_bounds__(512, 1) k_ce_eig(WS ws) {
     }
     __syncthreads();
   }
+  // the Hessenberg form with its reflectors (v = (1, H(col+2:n, col)), tau) for the
+  // eigenvector starts of k_ce_invit
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx % n, jj = idx / n;
+    L.H32[i + (int64_t)jj * LDD] = HF(H, ldh, i, jj);
+  }
+  __syncthreads();
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int i = idx % n, jj = idx / n;
     if (i > jj + 1) HF(H, ldh, i, jj) = 0.f;
@@ -978,8 +991,9 @@ size_t ce_eig_smem() { return ((size_t)(D_MAX + 1) * D_MAX + 2 * D_MAX + 64) * s
 // dependent chain in FP32 and only independent row products in FP64 (a
 // full-warp FP64 instruction holds an SM sub-partition for tens of cycles on
 // this GPU, so a scalar FP64 chain, as in an FP64 LU, is slow):
-//  1. inverse iteration with the FP32 LU (partial pivoting) of M - mu0 I from
-//     x = (1, ..., 1): IV_STEPS solves give x0 to FP32 accuracy;
+//  1. inverse iteration from x = (1, ..., 1) on the FP32 Hessenberg form
+//     H = Q^T fp32(M) Q that k_ce_eig computed (an O(n^2) LU of H - mu0 I),
+//     IV_STEPS solves, then x0 = Q y to FP32 accuracy;
 //  2. x0 scaled to x0(s) = 1 at an entry s of largest magnitude, and lambda0
 //     the FP64 Rayleigh quotient x0^H M x0 / x0^H x0;
 //  3. the refinement of Dongarra, Moler and Wilkinson (Improving the accuracy
@@ -1298,6 +1312,10 @@ __global__ void __launch_bounds__(IV_T, 1) k_ce_invit(WS ws) {
   CeLayout L = ce_layout(ws.dscr);
   const int idx = blockIdx.x;
   if (n <= 0 || idx >= L.cnt[0]) return;
+  if (c->svd_path) {  // the truncated problem: M is ill-conditioned, FP32 factors do not contract;
+    if (threadIdx.x == 0) L.ivfail[idx] = 1;  // the FP64 inverse iteration takes every candidate
+    return;
+  }
   extern __shared__ __align__(16) unsigned char iv_smem[];
   double* xr = (double*)iv_smem;  // the eigenvector (FP64)
   double* xi = xr + D_MAX;
@@ -1342,26 +1360,67 @@ __global__ void __launch_bounds__(IV_T, 1) k_ce_invit(WS ws) {
   mb = block_max_u64(mb, redu);
   const double sc = iv_pow2_scale(bexp_of_bits(mb));  // max |M sc| in [0.5, 1)
   const float tiny = 5.9604645e-8f * (float)n;         // 2^-24 n, against entries of order one
-  // ---- 1. inverse iteration with the FP32 LU of (M - mu0 I) sc ----
+  // ---- 1. x0: inverse iteration on the FP32 Hessenberg form H = Q^T fp32(M) Q that
+  // k_ce_eig left in L.H32, then x0 = Q y.  The LU of H - mu0 I (pivoting between
+  // rows k and k + 1) is O(n^2); U stays in (Ar, Ai) with zeros below the diagonal,
+  // the multipliers in (rr, ri) and the exchanges in perm. ----
   for (int j = wid; j < n; j += nw) {
-    double v[IV_NQ];
-#pragma unroll
-    for (int q = 0; q < IV_NQ; ++q) {
-      const int i = lane + 32 * q;
-      v[q] = i < n ? __ldg(M + i + (int64_t)j * LDD) : 0.0;
-    }
 #pragma unroll
     for (int q = 0; q < IV_NQ; ++q) {
       const int i = lane + 32 * q;
       if (i < n) {
-        Ar[i + j * ld] = (float)(i == j ? (v[q] - mu_r) * sc : v[q] * sc);
-        if (cx) Ai[i + j * ld] = i == j ? (float)(-mu_i * sc) : 0.f;
+        const float h = i <= j + 1 ? L.H32[i + (int64_t)j * LDD] : 0.f;
+        Ar[i + j * ld] = i == j ? h - (float)mu_r : h;
+        if (cx) Ai[i + j * ld] = i == j ? (float)(-mu_i) : 0.f;
       }
     }
   }
   __syncthreads();
-  iv_lu(Ar, Ai, ld, n, cx, perm, tiny, sh);
-  iv_perm(perm, n, sig);
+  if (threadIdx.x < 32) {
+    float hmax = 0.f;  // the largest diagonal magnitude, for the zero-pivot replacement
+    for (int e = lane; e < n; e += 32) hmax = fmaxf(hmax, fabsf(Ar[e + e * ld]));
+    for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+    const float htiny = fmaxf(hmax, 1e-30f) * 5.9604645e-8f * (float)n;
+    for (int k = 0; k + 1 < n; ++k) {
+      const cf a0{Ar[k + k * ld], cx ? Ai[k + k * ld] : 0.f};
+      const cf a1{Ar[k + 1 + k * ld], cx ? Ai[k + 1 + k * ld] : 0.f};
+      const bool sw = fabsf(a1.re) + fabsf(a1.im) > fabsf(a0.re) + fabsf(a0.im);
+      __syncwarp();
+      if (sw)
+        for (int j = k + lane; j < n; j += 32) {
+          float t = Ar[k + j * ld];
+          Ar[k + j * ld] = Ar[k + 1 + j * ld];
+          Ar[k + 1 + j * ld] = t;
+          if (cx) {
+            t = Ai[k + j * ld];
+            Ai[k + j * ld] = Ai[k + 1 + j * ld];
+            Ai[k + 1 + j * ld] = t;
+          }
+        }
+      __syncwarp();
+      cf pv = sw ? a1 : a0;
+      if (pv.re == 0.f && pv.im == 0.f) pv.re = htiny;
+      const cf l = cf_mul(sw ? a0 : a1, cf_recip(pv));
+      for (int j = k + 1 + lane; j < n; j += 32) {
+        const cf u{Ar[k + j * ld], cx ? Ai[k + j * ld] : 0.f};
+        Ar[k + 1 + j * ld] -= l.re * u.re - l.im * u.im;
+        if (cx) Ai[k + 1 + j * ld] -= l.re * u.im + l.im * u.re;
+      }
+      if (lane == 0) {
+        Ar[k + k * ld] = pv.re;
+        if (cx) Ai[k + k * ld] = pv.im;
+        Ar[k + 1 + k * ld] = 0.f;
+        if (cx) Ai[k + 1 + k * ld] = 0.f;
+        rr[k] = (double)l.re;
+        ri[k] = (double)l.im;
+        perm[k] = sw ? 1 : 0;
+      }
+      __syncwarp();
+    }
+    if (lane == 0 && Ar[(n - 1) + (n - 1) * ld] == 0.f && (!cx || Ai[(n - 1) + (n - 1) * ld] == 0.f))
+      Ar[(n - 1) + (n - 1) * ld] = htiny;
+  }
+  __syncthreads();
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const cf r = cf_recip(cf{Ar[k + k * ld], cx ? Ai[k + k * ld] : 0.f});
     udr[k] = r.re;
@@ -1371,17 +1430,25 @@ __global__ void __launch_bounds__(IV_T, 1) k_ce_invit(WS ws) {
   }
   __syncthreads();
   for (int it = 0; it < IV_STEPS; ++it) {
-    // permute, solve, and scale the result to a largest |re| + |im| of one
-    {
-      const int t = threadIdx.x;
-      const float tr = t < n ? yr[sig[t]] : 0.f, ti = t < n ? yi[sig[t]] : 0.f;
-      __syncthreads();
-      if (t < n) {
-        yr[t] = tr;
-        yi[t] = ti;
+    // P L (exchanges and multipliers, in order), then U (iv_solve: its L pass finds
+    // zeros), then the scale to a largest |re| + |im| of one
+    if (threadIdx.x == 0) {
+      for (int k = 0; k + 1 < n; ++k) {
+        cf y0{yr[k], yi[k]}, y1{yr[k + 1], yi[k + 1]};
+        if (perm[k]) {
+          const cf t = y0;
+          y0 = y1;
+          y1 = t;
+        }
+        const cf l{(float)rr[k], (float)ri[k]};
+        const cf ly = cf_mul(l, y0);
+        yr[k] = y0.re;
+        yi[k] = y0.im;
+        yr[k + 1] = y1.re - ly.re;
+        yi[k + 1] = cx ? y1.im - ly.im : 0.f;
       }
-      __syncthreads();
     }
+    __syncthreads();
     iv_solve(Ar, Ai, ld, n, cx, yr, yi, udr, udi, iv_slot);
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -1409,10 +1476,63 @@ __global__ void __launch_bounds__(IV_T, 1) k_ce_invit(WS ws) {
         yr[i] = v.re;
         yi[i] = cx ? v.im : 0.f;
       }
-      if (it == IV_STEPS - 1 && lane == 0) sh.p = bix;
     }
     __syncthreads();
   }
+  // x0 = Q y: the reflectors (staged in Ar) applied in reverse order, by warp 0
+  for (int j = wid; j + 2 < n; j += nw)
+    for (int i = j + 2 + lane; i < n; i += 32) Ar[i + j * ld] = L.H32[i + (int64_t)j * LDD];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int col = n - 3; col >= 0; --col) {
+      const float tau = (float)L.tauH[col];
+      if (tau == 0.f) continue;  // uniform
+      float dr = 0.f, di = 0.f;
+      for (int i = col + 1 + lane; i < n; i += 32) {
+        const float v = i == col + 1 ? 1.f : Ar[i + col * ld];
+        dr = fmaf(v, yr[i], dr);
+        di = fmaf(v, yi[i], di);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        dr += __shfl_xor_sync(0xffffffffu, dr, o);
+        di += __shfl_xor_sync(0xffffffffu, di, o);
+      }
+      __syncwarp();
+      for (int i = col + 1 + lane; i < n; i += 32) {
+        const float v = i == col + 1 ? 1.f : Ar[i + col * ld];
+        yr[i] = fmaf(-tau * dr, v, yr[i]);
+        if (cx) yi[i] = fmaf(-tau * di, v, yi[i]);
+      }
+      __syncwarp();
+    }
+    // the entry of largest |re| + |im| (x0(s) = 1 below)
+    float best = -1.f;
+    int bix = 0;
+    for (int i = lane; i < n; i += 32) {
+      const float a = fabsf(yr[i]) + fabsf(yi[i]);
+      if (a > best) {
+        best = a;
+        bix = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bix, o);
+      if (ob > best || (ob == best && oi < bix)) {
+        best = ob;
+        bix = oi;
+      }
+    }
+    const cf inv = best > 0.f && isfinite(best) ? cf_recip(cf{yr[bix], yi[bix]}) : cf{1.f, 0.f};
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const cf v = cf_mul(cf{yr[i], yi[i]}, inv);
+      yr[i] = v.re;
+      yi[i] = cx ? v.im : 0.f;
+    }
+    if (lane == 0) sh.p = bix;
+  }
+  __syncthreads();
   // ---- 2. x0 with x0(s) = 1, lambda0 = Rayleigh quotient ----
   const int s = sh.p;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
