@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(512) k_ce_svd(WS ws, int kh) {
   __shared__ double cnorm[D_MAX];              // rank 0's copy: squared column norms at a sweep's start
   __shared__ int perm[D_MAX];                  // visiting order of the sweep (rank 0's copy, then local)
   __shared__ double wpart[16 * 3];             // per-warp partial dots of a round
-  __shared__ double rotp[16 * 3];              // per-pair rotation (cs, sn, rotate?) of a round
+  __shared__ double rotp[16 * 2];              // per-pair rotation (cs, sn) of a round
+  __shared__ int rotf[16];                     // per-pair: rotate in this round
   const int ld = ws.dmax;
   for (int idx = threadIdx.x; idx < SVD_COLS * d; idx += blockDim.x) {
     const int q = idx / d, i = idx % d;
@@ -275,11 +276,14 @@ __global__ void __launch_bounds__(512) k_ce_svd(WS ws, int kh) {
     }
     cluster.sync();
     if (rank == 0) {
+      // squared norms are >= 0, whose bit patterns order like the values (an
+      // integer compare keeps the FP64 pipe free)
+      const long long* cb = (const long long*)cnorm;
       for (int i = threadIdx.x; i < d; i += blockDim.x) {
-        const double ni = cnorm[i];
+        const long long ni = cb[i];
         int r = 0;
         for (int j2 = 0; j2 < d; ++j2) {
-          const double nj = cnorm[j2];
+          const long long nj = cb[j2];
           r += (nj > ni || (nj == ni && j2 < i)) ? 1 : 0;
         }
         perm[r] = i;
@@ -342,27 +346,43 @@ __global__ void __launch_bounds__(512) k_ce_svd(WS ws, int kh) {
           ga = fma(xa[u], xb[u], ga);
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {  // three sums interleaved (FP64 adds have a long latency here)
-        al += __shfl_xor_sync(0xffffffffu, al, o);
-        be += __shfl_xor_sync(0xffffffffu, be, o);
-        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+      // The three butterfly sums (x + partner at distances 16, 8, 4, 2, 1), packed
+      // so that lanes which would only repeat a sum work on another of the three:
+      // six FP64 adds per warp instead of fifteen (each one holds this warp's
+      // FP64 pipe for a full warp's time), with the same additions as three
+      // separate butterflies.  al ends in lane 0, ga in lane 8, be in lane 16.
+      double s16a, s16b;
+      {
+        const double own = lane < 16 ? al : be;
+        const double snd = lane < 16 ? be : al;
+        s16a = own + __shfl_xor_sync(0xffffffffu, snd, 16);  // lanes 0-15: al, 16-31: be
+        s16b = ga + __shfl_xor_sync(0xffffffffu, ga, 16);    // lanes 0-15: ga
       }
-      if (lane == 0) {
-        wpart[w * 3 + 0] = al;
-        wpart[w * 3 + 1] = be;
-        wpart[w * 3 + 2] = ga;
+      double s8;
+      {
+        const double own = (lane >= 8 && lane < 16) ? s16b : s16a;
+        const double snd = lane < 8 ? s16b : s16a;
+        s8 = own + __shfl_xor_sync(0xffffffffu, snd, 8);  // lanes 0-7: al, 8-15: ga, 16-23: be
       }
+      s8 += __shfl_xor_sync(0xffffffffu, s8, 4);
+      s8 += __shfl_xor_sync(0xffffffffu, s8, 2);
+      s8 += __shfl_xor_sync(0xffffffffu, s8, 1);
+      if (lane == 0) wpart[w * 3 + 0] = s8;
+      if (lane == 16) wpart[w * 3 + 1] = s8;
+      if (lane == 8) wpart[w * 3 + 2] = s8;
       __syncthreads();
       // the pair's first warp combines the parts and forms the rotation
       if (live && part == 0 && lane == 0) {
-        double sa = 0.0, sb = 0.0, sg = 0.0;
-        for (int t2 = 0; t2 < wpp; ++t2) {
+        double sa = wpart[w * 3 + 0], sb = wpart[w * 3 + 1], sg = wpart[w * 3 + 2];
+        for (int t2 = 1; t2 < wpp; ++t2) {
           sa += wpart[(w + t2) * 3 + 0];
           sb += wpart[(w + t2) * 3 + 1];
           sg += wpart[(w + t2) * 3 + 2];
         }
-        const bool rot = (sg * sg > tol * tol * sa * sb) && sa > negl && sb > negl;
+        // sa, sb, negl >= 0: integer compares of their bit patterns
+        const bool big = __double_as_longlong(sa) > __double_as_longlong(negl) &&
+                         __double_as_longlong(sb) > __double_as_longlong(negl);
+        const bool rot = big && (sg * sg > tol * tol * sa * sb);
         double cs = 1.0, sn = 0.0;
         if (rot) {
           // The rotation angle needs only single precision (an inexact angle
@@ -388,13 +408,13 @@ __global__ void __launch_bounds__(512) k_ce_svd(WS ws, int kh) {
           for (int it = 0; it < 3; ++it) cs = cs * fma(-0.5 * xq, cs * cs, 1.5);
           sn = cs * t;
         }
-        rotp[q * 3 + 0] = cs;
-        rotp[q * 3 + 1] = sn;
-        rotp[q * 3 + 2] = rot ? 1.0 : 0.0;
+        rotp[q * 2 + 0] = cs;
+        rotp[q * 2 + 1] = sn;
+        rotf[q] = rot ? 1 : 0;
       }
       __syncthreads();
-      if (live && rotp[q * 3 + 2] != 0.0) {
-        const double cs = rotp[q * 3 + 0], sn = rotp[q * 3 + 1];
+      if (live && rotf[q]) {
+        const double cs = rotp[q * 2 + 0], sn = rotp[q * 2 + 1];
 #pragma unroll
         for (int u = 0; u < NE; ++u) {
           const int i = part * 32 + lane + 32 * wpp * u;
@@ -444,15 +464,18 @@ __global__ void __launch_bounds__(512) k_ce_svd(WS ws, int kh) {
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    // singular values are >= 0: integer compares of their bit patterns
+    const long long* sgb = (const long long*)sig;
     for (int i = 0; i < d; ++i) order[i] = i;
     for (int i = 1; i < d; ++i) {  // insertion sort, stable
       int v = order[i], y = i - 1;
-      while (y >= 0 && sig[order[y]] < sig[v]) { order[y + 1] = order[y]; --y; }
+      while (y >= 0 && sgb[order[y]] < sgb[v]) { order[y + 1] = order[y]; --y; }
       order[y + 1] = v;
     }
     const double s1 = sig[order[0]];
+    const long long thr = __double_as_longlong(s1 * (double)d * eps);
     int ell = 0;
-    for (int i = 0; i < d; ++i) ell += sig[order[i]] > s1 * (double)d * eps ? 1 : 0;
+    for (int i = 0; i < d; ++i) ell += sgb[order[i]] > thr ? 1 : 0;
     c->ell = ell;
     if (ell == 0) c->rankfail = 1;
   }
