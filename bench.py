@@ -465,10 +465,12 @@ def run_form_adjoint(args):
                 tot = sum(v[1] for v in prof.values())
                 _, logs = P.sdr_get_history(hh)
                 sw = [g_["svd_sweeps"] for g_ in logs if g_["flags"] & 1]
+                ndep = sum(1 for g_ in logs if g_["flags"] & 8)
                 print(f"{name} solve: {pair.last_stats[name]['cycles']} cycles, "
                       f"{pair.last_stats[name]['arnoldi_steps']} steps, truncated-SVD cycles {len(sw)}, "
                       f"Jacobi sweeps {sum(sw) / max(len(sw), 1):.1f} mean / {max(sw) if sw else 0} max, "
-                      f"ell {[g_['ell'] for g_ in logs][:6]}", file=sys.stderr)
+                      f"ell {[g_['ell'] for g_ in logs][:6]}, cycles with a dependent eigenvector {ndep}",
+                      file=sys.stderr)
                 for k_, (n_, t_) in sorted(prof.items(), key=lambda kv: -kv[1][1])[:10]:
                     print(f"  {k_:16s} launches {n_:7d}  {t_:10.2f} ms  {100 * t_ / max(tot, 1e-9):5.1f}%  "
                           f"{1e3 * t_ / max(n_, 1):9.2f} us/launch", file=sys.stderr)

@@ -166,7 +166,11 @@ typedef struct {
   int32_t ell;         /* numerical rank of SAW at the cycle's end */
   int32_t kprime;      /* recycle columns produced */
   int32_t kh;          /* recycle columns used by the cycle */
-  int32_t flags;       /* bit 0: truncated-SVD path taken; bit 1: breakdown */
+  int32_t flags;       /* bit 0: truncated-SVD path taken; bit 1: breakdown;
+                          bit 2: rank lost (SAW's QR, l = 0, the eigenvalue
+                          iteration's limit, or bit 3); bit 3: a selected
+                          eigenvector was dependent on the ones before it
+                          (its Gram-Schmidt remainder below 1e-12 of its norm) */
   int32_t svd_sweeps;  /* Jacobi sweeps of the truncated-SVD path (0 when not taken) */
   double res;          /* true residual at the cycle's last check */
   double sres;         /* sketched residual at the cycle's last step */

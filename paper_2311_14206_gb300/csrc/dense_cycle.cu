@@ -1999,6 +1999,7 @@ __global__ void __launch_bounds__(512) k_ce_finish(WS ws, int kh, int ucur) {
   CeLayout L = ce_layout(ws.dscr);
   __shared__ double red[32];
   __shared__ double dts[K_MAX];
+  int zdep = 0;  // (thread 0) a selected eigenvector depends on the earlier ones
   double* Z = L.Zr;
   for (int col = 0; col < kp; ++col) {
     double* zc = Z + (int64_t)col * LDD;
@@ -2027,7 +2028,10 @@ __global__ void __launch_bounds__(512) k_ce_finish(WS ws, int kh, int ucur) {
     double nr = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) nr = fma(zc[i], zc[i], nr);
     nr = sqrt(block_sum(nr, red));
-    if (threadIdx.x == 0 && !(nr > 1e-12 * n0)) c->rankfail = 1;
+    if (threadIdx.x == 0 && !(nr > 1e-12 * n0)) {
+      c->rankfail = 1;
+      zdep = 1;
+    }
     const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) zc[i] *= inv;
     __syncthreads();
@@ -2085,7 +2089,7 @@ __global__ void __launch_bounds__(512) k_ce_finish(WS ws, int kh, int ucur) {
       g.ell = c->ell;
       g.kprime = kp;
       g.kh = kh;
-      g.flags = (c->svd_path ? 1 : 0) | (c->breakdown ? 2 : 0) | (c->rankfail ? 4 : 0);
+      g.flags = (c->svd_path ? 1 : 0) | (c->breakdown ? 2 : 0) | (c->rankfail ? 4 : 0) | (zdep ? 8 : 0);
       g.svd_sweeps = c->svd_path ? c->svd_sweeps : 0;
       g.res = c->res;
       g.sres = c->sres;
