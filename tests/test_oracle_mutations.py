@@ -123,3 +123,52 @@ def _sketch_pins(mod):
 def test_sketch_mutation_is_caught(name, old, new):
     mod = load_mutant(sketch, old, new)
     assert _sketch_pins(mod), f"no pin caught: {name}"
+
+
+# ---- the subsampled DCT (Section 6), pinned by its definition as a cosine sum
+DCT_MUTATIONS = [
+    ("DCT type III in place of II", "type=2", "type=3"),
+    ("random signs dropped", "self.signs * x", "x"),
+    ("scale sqrt(s / N)", "self.scale = np.sqrt(n / s)", "self.scale = np.sqrt(s / n)"),
+    ("unnormalised DCT", 'norm="ortho"', 'norm="backward"'),
+]
+
+
+@pytest.mark.parametrize("name,old,new", DCT_MUTATIONS, ids=[m[0] for m in DCT_MUTATIONS])
+def test_dct_mutation_is_caught(name, old, new, monkeypatch):
+    import test_oracle_sketch as T
+    mod = load_mutant(sketch, old, new)
+    monkeypatch.setattr(sketch, "SubsampledDCT", mod.SubsampledDCT)  # the pin imports it from oracle.sketch
+    assert pins_catch(mod, [lambda _m: T.test_subsampled_dct_definition_and_embedding()]), f"no pin caught: {name}"
+
+
+# ---- the rank rule for an installed SAU and the stale-SAU rule (Section 3.6)
+STALE_MUTATIONS = [
+    ("rank threshold without the factor s", "<= s * EPS * maxn", "<= EPS * maxn"),
+    ("rank test on the last pivot only", "np.any(np.abs(np.diag(R)) <= s * EPS * maxn)",
+     "np.abs(R[-1, -1]) <= s * EPS * maxn"),
+    ("non-finite SAU passes the rank test", "    if not np.all(np.isfinite(SAU)):\n        return True\n", ""),
+    ("column norms taken over rows", "np.linalg.norm(SAU, axis=0)", "np.linalg.norm(SAU, axis=1)"),
+    ("stale test with the ratio inverted", "c.checks[-1][2] > STALE_RATIO * c.checks[-1][1]",
+     "c.checks[-1][1] > STALE_RATIO * c.checks[-1][2]"),
+    ("stale refresh keeps the old SAU",
+     "SAU = S.apply_cols(csr_matmat(A, U))\n            matvecs += U.shape[1]\n            refreshes += 1",
+     "matvecs += U.shape[1]\n            refreshes += 1"),
+]
+
+
+def _stale_pins(mod):
+    import test_oracle_stale as T
+    saved = T.O
+    try:
+        T.O = mod
+        return pins_catch(mod, [lambda _m: T.test_rank_rule_closed_forms(),
+                                lambda _m: T.test_stale_rule_silent_on_exact_variant(30),
+                                lambda _m: T.test_stale_rule_rescues_inexact_variant()])
+    finally:
+        T.O = saved
+
+
+@pytest.mark.parametrize("name,old,new", STALE_MUTATIONS, ids=[m[0] for m in STALE_MUTATIONS])
+def test_stale_mutation_is_caught(name, old, new):
+    assert _stale_pins(load_mutant(sdr, old, new)), f"no pin caught: {name}"

@@ -30,6 +30,7 @@ def test_rank_rule_closed_forms():
     R = np.linalg.qr(_two_columns(1e-6), mode="r")
     assert abs(abs(R[1, 1]) - 3.0 * np.sin(1e-6)) < 1e-12  # |R_22| = ||c|| sin(theta)
     assert not O.sau_rank_deficient(_two_columns(1e-10))  # 3e-10 > s eps ||c|| = 1.3e-13
+    assert O.sau_rank_deficient(_two_columns(3e-14))      # 9e-14 <= s eps ||c||, though above eps ||c||
     assert O.sau_rank_deficient(_two_columns(1e-16))      # below the threshold
     assert O.sau_rank_deficient(_two_columns(0.0))        # duplicated columns
     rng = np.random.default_rng(1)
