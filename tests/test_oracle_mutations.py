@@ -172,3 +172,33 @@ def _stale_pins(mod):
 @pytest.mark.parametrize("name,old,new", STALE_MUTATIONS, ids=[m[0] for m in STALE_MUTATIONS])
 def test_stale_mutation_is_caught(name, old, new):
     assert _stale_pins(load_mutant(sdr, old, new)), f"no pin caught: {name}"
+
+
+# ---- the Givens-sine estimator (Section 4.5; Section 5, the augmented cycle)
+GIVENS_MUTATIONS = [
+    ("sine reported from the cosine", "sines.append(abs(s))", "sines.append(abs(c))"),
+    ("earlier rotations not applied to the new column",
+     "            Gr[k + i, col], Gr[k + i + 1, col] = c * a + s * b, -s * a + c * b\n", "            pass\n"),
+    ("right-hand side from the column before", "g = beta * R[:, k].copy()", "g = beta * R[:, k - 1].copy()"),
+    ("G without the Hessenberg block", "B[k:, k:] = H[:j + 1, :j]", "B[k:, k:] = np.eye(j + 1, j)"),
+    ("rotation normalised by |a| + |b|", "r = float(np.hypot(a, b))", "r = float(abs(a) + abs(b))"),
+]
+
+
+def _givens_pins(mod):
+    import test_oracle_givens as T
+    saved = T.G
+    try:
+        T.G = mod
+        return pins_catch(mod, [lambda _m: T.test_estimator_sres_equals_householder_least_squares(),
+                                lambda _m: T.test_identity_sketch_gives_textbook_gmres_sines(),
+                                lambda _m: T.test_sines_are_sketched_subspace_angles(),
+                                lambda _m: T.test_corollary_bound_on_true_residuals()])
+    finally:
+        T.G = saved
+
+
+@pytest.mark.parametrize("name,old,new", GIVENS_MUTATIONS, ids=[m[0] for m in GIVENS_MUTATIONS])
+def test_givens_mutation_is_caught(name, old, new):
+    from oracle import givens
+    assert _givens_pins(load_mutant(givens, old, new)), f"no pin caught: {name}"
