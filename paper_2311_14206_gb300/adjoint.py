@@ -14,7 +14,7 @@ import ctypes
 
 import torch
 
-from .sdr import CSRDevice, Solver, _check, _ptr, _stream, load_library, sdr_csr, sdr_solve
+from .sdr import CSRDevice, Solver, _check, _device_array, _ptr, _stream, load_library, sdr_csr, sdr_solve
 
 
 class AdjointPair:
@@ -23,8 +23,9 @@ class AdjointPair:
     def __init__(self, n, rowptr: torch.Tensor, col: torch.Tensor, m, k, t, s, zeta=8, seed=231114206,
                  rel_tol=1e-8, max_cycles=200):
         self.n, self.nnz = int(n), int(col.numel())
-        self.rowptr, self.col = rowptr.contiguous(), col.contiguous()
+        self.rowptr = _device_array(rowptr.contiguous(), self.n + 1, "rowptr", torch.int32)
         dev = rowptr.device
+        self.col = _device_array(col.contiguous(), self.nnz, "col", torch.int32, dev)
         self.rowptrT = torch.empty(self.n + 1, dtype=torch.int32, device=dev)
         self.colT = torch.empty(self.nnz, dtype=torch.int32, device=dev)
         self.perm = torch.empty(self.nnz, dtype=torch.int32, device=dev)
@@ -45,26 +46,29 @@ class AdjointPair:
         A = self.matrix(vals)
         if self._fwd_used:
             self.fwd.recycle(A, 0)
-        x = torch.zeros_like(b)
+        x = torch.zeros_like(b, memory_format=torch.contiguous_format)
         _, self.last_stats["forward"] = sdr_solve(self.fwd.h, A, b.contiguous(), x)
         self._fwd_used = True
         return x
 
     def solve_adjoint(self, vals: torch.Tensor, g: torch.Tensor) -> torch.Tensor:
+        vals = _device_array(vals.contiguous(), self.nnz, "vals", device=self.perm.device)
         valsT = torch.empty_like(vals)
-        _check(load_library().sdr_gather_values(_ptr(vals.contiguous()), _ptr(self.perm), self.nnz, _ptr(valsT),
+        _check(load_library().sdr_gather_values(_ptr(vals), _ptr(self.perm), self.nnz, _ptr(valsT),
                                                 _stream()), "sdr_gather_values")
         AT = CSRDevice(self.n, self.rowptrT, self.colT, valsT)
         if self._adj_used:
             self.adj.recycle(AT, 0)
-        lam = torch.zeros_like(g)
+        lam = torch.zeros_like(g, memory_format=torch.contiguous_format)
         _, self.last_stats["adjoint"] = sdr_solve(self.adj.h, AT, g.contiguous(), lam)
         self._adj_used = True
         return lam
 
     def value_gradient(self, vals, lam, x):
-        grad = torch.empty_like(vals)
         A = self.matrix(vals).c_struct()
+        lam = _device_array(lam.contiguous(), self.n, "lambda", device=self.perm.device)
+        x = _device_array(x.contiguous(), self.n, "x", device=self.perm.device)
+        grad = torch.empty_like(vals, memory_format=torch.contiguous_format)  # nnz entries: c_struct checked
         _check(load_library().sdr_value_gradient(ctypes.byref(A), _ptr(lam), _ptr(x), _ptr(grad), _stream()),
                "sdr_value_gradient")
         return grad

@@ -134,6 +134,38 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
+def _check_len(t, n, name):
+    """t is a tensor of n elements (ValueError otherwise).  The wrappers check
+    the sizes of all their arrays first, then their type and placement."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, the library uses {n}")
+
+
+def _device_array(t, n, name, dtype=torch.float64, device=None):
+    """Check t before its raw pointer reaches the library, which reads or writes
+    exactly n elements of dtype there: a tensor of n elements, contiguous, of
+    dtype, on a CUDA device (the given one, if any).  Raises ValueError or
+    TypeError."""
+    _check_len(t, n, name)
+    if t.dtype != dtype or not t.is_contiguous() or not t.is_cuda:
+        raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if device is not None and t.device != device:
+        raise TypeError(f"{name} is on {t.device}, the other arrays on {device}")
+    return t
+
+
+# The sketch size s of each handle created through this module: the library
+# writes s-element sketches into buffers the caller passes, and the ABI has no
+# call that reports s.
+_HANDLE_S = {}
+
+
+def _handle_s(h):
+    return _HANDLE_S.get(h.value if isinstance(h, ctypes.c_void_p) else h)
+
+
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -157,14 +189,20 @@ class CSRDevice:
                    val.to(torch.float32) if with_f32 else None)
 
     def c_struct(self) -> sdr_csr:
-        for t, dt in ((self.rowptr, torch.int32), (self.col, torch.int32), (self.val, torch.float64)):
-            if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
-                raise TypeError("CSR arrays must be contiguous CUDA tensors (int32, int32, float64)")
+        if not self.n >= 1:
+            raise ValueError(f"CSR order n = {self.n}")
+        nnz = int(self.val.numel())
+        _check_len(self.rowptr, self.n + 1, "rowptr")
+        _check_len(self.col, nnz, "col")
+        if self.val32 is not None:
+            _check_len(self.val32, nnz, "val32")
+        _device_array(self.rowptr, self.n + 1, "rowptr", torch.int32)
+        dev = self.rowptr.device
+        _device_array(self.col, nnz, "col", torch.int32, dev)
+        _device_array(self.val, nnz, "val", torch.float64, dev)
         v32 = 0
         if self.val32 is not None:
-            if not self.val32.is_cuda or self.val32.dtype != torch.float32 or not self.val32.is_contiguous():
-                raise TypeError("val32 must be a contiguous float32 CUDA tensor")
-            v32 = self.val32.data_ptr()
+            v32 = _device_array(self.val32, nnz, "val32", torch.float32, dev).data_ptr()
         return sdr_csr(self.n, int(self.val.numel()), self.rowptr.data_ptr(), self.col.data_ptr(),
                        self.val.data_ptr(), v32)
 
@@ -186,6 +224,7 @@ def sdr_create(params: sdr_params, n_max: int, stream=None) -> ctypes.c_void_p:
     h = ctypes.c_void_p()
     st = lib.sdr_create(ctypes.byref(params), n_max, stream if stream is not None else _stream(), ctypes.byref(h))
     _check(st, "sdr_create")
+    _HANDLE_S[h.value] = int(params.s)
     return h
 
 
@@ -194,9 +233,13 @@ def sdr_solve(h, A: CSRDevice, b: torch.Tensor, x: torch.Tensor, allow_not_conve
     OK (and NOT_CONVERGED when allow_not_converged) raise SdrError, unless
     listed in `allow` (for instance SDR_ERR_BREAKDOWN = 5)."""
     lib = load_library()
-    if b.dtype != torch.float64 or x.dtype != torch.float64 or not (b.is_cuda and x.is_cuda):
-        raise TypeError("b and x must be float64 CUDA tensors")
+    _check_len(b, A.n, "b")
+    _check_len(x, A.n, "x")
+    _device_array(b, A.n, "b")
+    _device_array(x, A.n, "x", device=b.device)
     csr = A.c_struct()
+    if A.val.device != b.device:
+        raise TypeError(f"A is on {A.val.device}, b and x on {b.device}")
     stats = sdr_stats()
     st = lib.sdr_solve(h, ctypes.byref(csr), _ptr(b), _ptr(x), ctypes.byref(stats))
     _check(st, "sdr_solve", ok=((0, 4) if allow_not_converged else (0,)) + tuple(allow))
@@ -208,11 +251,16 @@ def sdr_solve_batch(handles, As, bs, xs, allow_not_converged=True):
     recycle space each); x arrays are overwritten.  Returns (status, [stats])."""
     lib = load_library()
     cnt = len(handles)
+    if not (len(As) == len(bs) == len(xs) == cnt):
+        raise ValueError(f"{cnt} handles, {len(As)} matrices, {len(bs)} right-hand sides, {len(xs)} solutions")
+    for A, b, x in zip(As, bs, xs):
+        _check_len(b, A.n, "b")
+        _check_len(x, A.n, "x")
+    for A, b, x in zip(As, bs, xs):
+        _device_array(b, A.n, "b")
+        _device_array(x, A.n, "x", device=b.device)
     H = (ctypes.c_void_p * cnt)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
     C = (sdr_csr * cnt)(*[A.c_struct() for A in As])
-    for t in list(bs) + list(xs):
-        if t.dtype != torch.float64 or not t.is_cuda:
-            raise TypeError("b and x must be float64 CUDA tensors")
     B = (ctypes.c_void_p * cnt)(*[b.data_ptr() for b in bs])
     X = (ctypes.c_void_p * cnt)(*[x.data_ptr() for x in xs])
     S = (sdr_stats * cnt)()
@@ -224,6 +272,8 @@ def sdr_solve_batch(handles, As, bs, xs, allow_not_converged=True):
 def sdr_recycle_batch(handles, As, mode=0):
     lib = load_library()
     cnt = len(handles)
+    if As is not None and len(As) != cnt:
+        raise ValueError(f"{cnt} handles, {len(As)} matrices")
     H = (ctypes.c_void_p * cnt)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
     C = (sdr_csr * cnt)(*[A.c_struct() for A in As]) if As is not None else None
     return _check(lib.sdr_recycle_batch(cnt, H, C, mode), "sdr_recycle_batch")
@@ -236,10 +286,19 @@ def sdr_recycle(h, A_next: CSRDevice = None, mode: int = 0):
 
 
 def sdr_destroy(h):
+    _HANDLE_S.pop(h.value if isinstance(h, ctypes.c_void_p) else h, None)
     return load_library().sdr_destroy(h)
 
 
+def _check_s(h, s, where):
+    hs = _handle_s(h)
+    if hs is not None and s != hs:
+        raise ValueError(f"{where}: s = {s}, but the handle sketches to {hs} rows")
+
+
 def sdr_sketch(h, x: torch.Tensor, s: int) -> torch.Tensor:
+    _check_s(h, s, "sdr_sketch")
+    _device_array(x, x.numel(), "x")
     y = torch.empty(s, dtype=torch.float64, device=x.device)
     _check(load_library().sdr_sketch(h, _ptr(x), x.numel(), _ptr(y)), "sdr_sketch")
     return y
@@ -302,6 +361,7 @@ def sdr_recycle_dim(h) -> int:
 
 
 def sdr_recycle_export(h, n: int, s: int, device="cuda"):
+    _check_s(h, s, "sdr_recycle_export")
     kd = sdr_recycle_dim(h)
     U = torch.empty((kd, n), dtype=torch.float64, device=device)  # row c = column c (column-major n x kd)
     SU = torch.empty((kd, s), dtype=torch.float64, device=device)
@@ -313,10 +373,17 @@ def sdr_recycle_export(h, n: int, s: int, device="cuda"):
 
 def sdr_recycle_import(h, A: CSRDevice, U: torch.Tensor, SU: torch.Tensor = None, SAU: torch.Tensor = None):
     """U, SU, SAU given as (n x k), (s x k), (s x k) arrays; stored column-major."""
+    if U.dim() != 2:
+        raise ValueError("U must be an n x k array")
     n, kd = U.shape
-    Uc = U.T.contiguous()
-    SUc = SU.T.contiguous() if SU is not None else None
-    SAUc = SAU.T.contiguous() if SAU is not None else None
+    hs = _handle_s(h)
+    for name, X in (("SU", SU), ("SAU", SAU)):
+        if X is not None and (X.dim() != 2 or X.shape[1] != kd or (hs is not None and X.shape[0] != hs)):
+            raise ValueError(f"{name} has shape {tuple(X.shape)}, expected (s, {kd})"
+                             + (f" with s = {hs}" if hs is not None else ""))
+    Uc = _device_array(U.T.contiguous(), n * kd, "U")
+    SUc = _device_array(SU.T.contiguous(), SU.numel(), "SU", device=Uc.device) if SU is not None else None
+    SAUc = _device_array(SAU.T.contiguous(), SAU.numel(), "SAU", device=Uc.device) if SAU is not None else None
     csr = A.c_struct() if A is not None else None
     st = load_library().sdr_recycle_import(h, ctypes.byref(csr) if csr is not None else None, n, kd, _ptr(Uc),
                                            _ptr(SUc), _ptr(SAUc))
